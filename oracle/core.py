@@ -1,0 +1,236 @@
+"""ctypes wrapper around ``pond_oracle.c`` (test infrastructure only; see package doc)."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pond_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NPLANES = 25
+# plane layout of a state array of shape (25, ny, nx): f_0..f_8, g_0..g_8, theta, ux, uy,
+# rho, T, uhat_x, uhat_y.  Population index i = 3*jy + jx with c = j - 1.
+PL = dict(f=0, g=9, theta=18, ux=19, uy=20, rho=21, T=22, uhx=23, uhy=24)
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, OpenMP, no FMA contraction)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + ".%d.tmp" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
+                                   "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _CParams(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
+                ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("delta", C.c_double),
+                ("kappa", C.c_double), ("tau", C.c_double), ("k_cond", C.c_double),
+                ("p_floor", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
+                ("pad", C.c_int32), ("dt", C.c_double)]
+
+
+@dataclasses.dataclass
+class Params:
+    nx: int
+    ny: int
+    bc_x: int = 0
+    bc_y: int = 0
+    a: float = 2.0 / 49.0
+    b: float = 2.0 / 21.0
+    R: float = 1.0
+    delta: float = 1.0 / 3.0
+    kappa: float = 0.0
+    tau: float = 0.8
+    k_cond: float = -1.0
+    p_floor: float = 1e-3 / 6.0
+    tol: float = 1e-12
+    max_iter: int = 20
+    dt: float = 1.0
+
+    def c(self) -> _CParams:
+        return _CParams(self.nx, self.ny, self.bc_x, self.bc_y, self.a, self.b, self.R,
+                        self.delta, self.kappa, self.tau, self.k_cond, self.p_floor, self.tol,
+                        self.max_iter, 0, self.dt)
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        pp = C.POINTER(_CParams)
+        lib.orc_moment_matrix.argtypes = [dp, dp]
+        lib.orc_gauge_matrix.argtypes = [dp, dp, dp]
+        lib.orc_gauge_matrix.restype = C.c_int
+        lib.orc_lagrange4.argtypes = [C.c_double, dp]
+        lib.orc_nonlocal.argtypes = [pp, dp, dp, dp]
+        lib.orc_init.argtypes = [pp, dp, dp, dp, dp, dp]
+        lib.orc_stream_node.argtypes = [pp, dp, C.c_int, C.c_int, dp, dp, dp]
+        lib.orc_stream_node.restype = C.c_int
+        lib.orc_macro.argtypes = [pp, dp, dp, dp, C.c_double, C.c_double, C.c_double, dp]
+        lib.orc_collide.argtypes = [pp, dp, dp, dp, dp, C.c_double, C.c_double, C.c_double,
+                                    dp, dp]
+        lib.orc_collide.restype = C.c_int
+        lib.orc_step.argtypes = [pp, dp, dp, dp]
+        lib.orc_step.restype = C.c_int
+        lib.orc_step_nodes.argtypes = [pp, dp, C.POINTER(C.c_int64), C.c_int64, dp, dp]
+        lib.orc_step_nodes.restype = C.c_int
+        lib.orc_moments.argtypes = [pp, dp, dp, dp, dp, dp, dp]
+        lib.orc_num_threads.restype = C.c_int
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _d(x) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def weights() -> np.ndarray:
+    """D2Q9 weights W_i = W_jx W_jy (index i = 3*jy + jx, c = j - 1)."""
+    w1 = np.array([1 / 6, 2 / 3, 1 / 6])
+    return np.array([w1[i % 3] * w1[i // 3] for i in range(9)])
+
+
+def velocities(lam) -> tuple[np.ndarray, np.ndarray]:
+    """Shifted velocities v_i = sqrt(theta) c_i + u of gauge lam = (theta, ux, uy)."""
+    th, ux, uy = lam
+    c = np.array([(i % 3 - 1, i // 3 - 1) for i in range(9)], dtype=np.float64)
+    s = np.sqrt(th)
+    return s * c[:, 0] + ux, s * c[:, 1] + uy
+
+
+def moment_matrix(lam) -> np.ndarray:
+    out = np.zeros(81)
+    _load().orc_moment_matrix(_p(_d(lam)), _p(out))
+    return out.reshape(9, 9)
+
+
+def gauge_matrix(src, dst) -> np.ndarray:
+    out = np.zeros(81)
+    rc = _load().orc_gauge_matrix(_p(_d(src)), _p(_d(dst)), _p(out))
+    if rc:
+        raise ValueError("singular moment matrix")
+    return out.reshape(9, 9)
+
+
+def lagrange4(xi: float) -> np.ndarray:
+    out = np.zeros(4)
+    _load().orc_lagrange4(float(xi), _p(out))
+    return out
+
+
+def nonlocal_fields(P: Params, rho, T) -> np.ndarray:
+    """Lagged interface/heat-flux fields (4, ny, nx): Fx, Fy, rho E_lambda, M_0."""
+    rho = _d(rho); T = _d(T)
+    out = np.zeros((4, P.ny, P.nx))
+    cp = P.c()
+    _load().orc_nonlocal(C.byref(cp), _p(rho), _p(T), _p(out))
+    return out
+
+
+def init_state(P: Params, rho, ux, uy, T) -> np.ndarray:
+    out = np.zeros((NPLANES, P.ny, P.nx))
+    cp = P.c()
+    _load().orc_init(C.byref(cp), _p(_d(rho)), _p(_d(ux)), _p(_d(uy)), _p(_d(T)), _p(out))
+    return out
+
+
+def stream_node(P: Params, state, X: int, Y: int, lam):
+    state = _d(state)
+    ft = np.zeros(9); gt = np.zeros(9)
+    cp = P.c()
+    rc = _load().orc_stream_node(C.byref(cp), _p(state), int(X), int(Y), _p(_d(lam)),
+                                 _p(ft), _p(gt))
+    if rc:
+        raise ValueError("singular moment matrix")
+    return ft, gt
+
+
+def macro(P: Params, lam, ft, gt, Fx=0.0, Fy=0.0, rEl=0.0) -> dict:
+    out = np.zeros(11)
+    cp = P.c()
+    _load().orc_macro(C.byref(cp), _p(_d(lam)), _p(_d(ft)), _p(_d(gt)), float(Fx), float(Fy),
+                      float(rEl), _p(out))
+    keys = ["rho", "ux", "uy", "uhx", "uhy", "E", "e", "T", "p", "P", "theta"]
+    return dict(zip(keys, out.tolist())) | {"_raw": out}
+
+
+def collide(P: Params, lam, ft, gt, mac, Fx=0.0, Fy=0.0, M0=0.0):
+    fo = np.zeros(9); go = np.zeros(9)
+    raw = mac["_raw"] if isinstance(mac, dict) else _d(mac)
+    cp = P.c()
+    rc = _load().orc_collide(C.byref(cp), _p(_d(lam)), _p(_d(ft)), _p(_d(gt)), _p(_d(raw)),
+                             float(Fx), float(Fy), float(M0), _p(fo), _p(go))
+    if rc:
+        raise ValueError("singular moment matrix")
+    return fo, go
+
+
+def step(P: Params, state, n: int = 1, stats=None) -> np.ndarray:
+    """Advance the full grid by n time steps; returns the new state (25, ny, nx)."""
+    cur = _d(state).copy()
+    nxt = np.empty_like(cur)
+    st = np.zeros(4)
+    cp = P.c()
+    lib = _load()
+    for _ in range(n):
+        rc = lib.orc_step(C.byref(cp), _p(cur), _p(nxt), _p(st))
+        if rc:
+            raise FloatingPointError("oracle step failed (singular moment matrix)")
+        cur, nxt = nxt, cur
+    if stats is not None:
+        stats["streams"] = stats.get("streams", 0.0) + st[0]
+        stats["nonconv"] = stats.get("nonconv", 0.0) + st[1]
+        stats["clamped"] = stats.get("clamped", 0.0) + st[2]
+    return cur
+
+
+def step_nodes(P: Params, state, nodes, stats=None) -> np.ndarray:
+    """One step evaluated at the given flat node indices only; returns (len, 25)."""
+    state = _d(state)
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64))
+    out = np.zeros((len(nodes), NPLANES))
+    st = np.zeros(4)
+    cp = P.c()
+    rc = _load().orc_step_nodes(C.byref(cp), _p(state), nodes.ctypes.data_as(C.POINTER(C.c_int64)),
+                                len(nodes), _p(out), _p(st))
+    if rc:
+        raise FloatingPointError("oracle step failed (singular moment matrix)")
+    if stats is not None:
+        stats["streams"] = stats.get("streams", 0.0) + st[0]
+        stats["nonconv"] = stats.get("nonconv", 0.0) + st[1]
+        stats["clamped"] = stats.get("clamped", 0.0) + st[2]
+    return out
+
+
+def moments(P: Params, state) -> dict:
+    state = _d(state)
+    outs = [np.zeros((P.ny, P.nx)) for _ in range(5)]
+    cp = P.c()
+    _load().orc_moments(C.byref(cp), _p(state), *[_p(o) for o in outs])
+    return dict(zip(["rho", "ux", "uy", "T", "p"], outs))
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())

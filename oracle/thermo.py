@@ -1,0 +1,133 @@
+"""Closed-form thermodynamics of the van der Waals fluid (test infrastructure only).
+
+Used to build initial conditions of the synthetic workloads and as pins:
+  - vdW pressure, internal energy e = C_v T - a rho (Eq. SM vdW internal energy)
+  - isentropic sound speed (Eq. SM speed of sound formula, vdW form)
+  - Maxwell's equal-area rule for coexistence densities (main text, Fig. 2)
+  - Rankine-Hugoniot post-shock state in closed form (SM "Rankine-Hugoniot
+    conditions"), with the velocity formula read with the pre-shock sound speed
+    (the printed formula names the post-shock one; only the pre-shock reading
+    satisfies the jump conditions)
+  - Rankine-Hugoniot state by a direct root solve of the jump conditions (pin)
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import optimize
+
+A_VDW = 2.0 / 49.0
+B_VDW = 2.0 / 21.0
+R_GAS = 1.0
+
+
+def critical(a=A_VDW, b=B_VDW, R=R_GAS):
+    """rho_cr = 1/(3b), T_cr = 8a/(27 R b), p_cr = a/(27 b^2) (main text)."""
+    return 1.0 / (3.0 * b), 8.0 * a / (27.0 * R * b), a / (27.0 * b * b)
+
+
+def pressure(rho, T, a=A_VDW, b=B_VDW, R=R_GAS):
+    return rho * R * T / (1.0 - b * rho) - a * rho * rho
+
+
+def energy(rho, T, delta, a=A_VDW, R=R_GAS):
+    return (R / delta) * T - a * rho
+
+
+def dp_drho_T(rho, T, a=A_VDW, b=B_VDW, R=R_GAS):
+    return R * T / (1.0 - b * rho) ** 2 - 2.0 * a * rho
+
+
+def sound_speed(rho, T, delta, a=A_VDW, b=B_VDW, R=R_GAS):
+    """Isentropic vdW sound speed sqrt(R T (1 + delta)/(1 - b rho)^2 - 2 a rho)."""
+    return math.sqrt(R * T * (1.0 + delta) / (1.0 - b * rho) ** 2 - 2.0 * a * rho)
+
+
+def _helmholtz_mu(rho, T, a=A_VDW, b=B_VDW, R=R_GAS):
+    """Chemical potential up to a T-only constant: mu = f + p/rho with
+    f = -R T ln((1 - b rho)/rho) - a rho (isothermal part of the vdW free energy)."""
+    return -R * T * math.log((1.0 - b * rho) / rho) - a * rho + pressure(rho, T, a, b, R) / rho
+
+
+def maxwell(Tr: float, a=A_VDW, b=B_VDW, R=R_GAS):
+    """Coexisting (rho_v, rho_l) at T = Tr*T_cr by equal pressure and equal chemical
+    potential, which is Maxwell's equal-area rule."""
+    rc, Tc, pc = critical(a, b, R)
+    T = Tr * Tc
+    # spinodal densities bracket the roots
+    sp = np.sort(np.roots([-2.0 * a * b * b, 4.0 * a * b, -2.0 * a, R * T]).real)
+    sp = [s for s in sp if 0 < s < 1.0 / b]
+    lo, hi = sp[0], sp[-1]
+
+    def resid(x):
+        rv, rl = x
+        return [pressure(rv, T, a, b, R) - pressure(rl, T, a, b, R),
+                _helmholtz_mu(rv, T, a, b, R) - _helmholtz_mu(rl, T, a, b, R)]
+
+    guess = [rc * max(1e-3, 1.0 - 2.0 * math.sqrt(1.0 - Tr)) * 0.8, rc * (1.0 + 2.0 * math.sqrt(1.0 - Tr))]
+    guess = [min(guess[0], 0.9 * lo), max(guess[1], 1.1 * hi)]
+    sol = optimize.fsolve(resid, guess, xtol=1e-14, full_output=True)
+    rv, rl = sol[0]
+    if not (0 < rv < lo and hi < rl < 1.0 / b):
+        raise RuntimeError("Maxwell construction failed at Tr=%g" % Tr)
+    return float(rv), float(rl)
+
+
+def rh_closed_form(rho0: float, p0: float, rho1: float, delta: float,
+                   a=A_VDW, b=B_VDW, R=R_GAS):
+    """Post-shock (Mach M0 w.r.t. the pre-shock sound speed, u1, p1) for a shock moving
+    into still fluid, from the reduced closed form (SM "Rankine-Hugoniot conditions")."""
+    rc, Tc, pc = critical(a, b, R)
+    vc = 1.0 / rc
+    scale = math.sqrt(pc * vc)
+    r0, r1, pt0 = rho0 / rc, rho1 / rc, p0 / pc
+    T0 = (p0 + a * rho0 * rho0) * (1.0 - b * rho0) / (rho0 * R)
+    c0 = sound_speed(rho0, T0, delta, a, b, R) / scale
+    num = pt0 * (1.0 + delta) + r0 * r1 * (r0 + r1 + 3.0 * delta - 3.0)
+    den = r0 * (2.0 * r0 * (3.0 - r1) + 3.0 * delta * (r0 - r1))
+    M0 = math.sqrt(6.0 * r1 * num / den) / c0
+    u1 = c0 * M0 * (r1 - r0) / r1
+    p1 = pt0 + c0 * c0 * M0 * M0 * r0 * (r1 - r0) / r1
+    return M0, u1 * scale, p1 * pc
+
+
+def rh_root_solve(rho0: float, p0: float, rho1: float, delta: float,
+                  a=A_VDW, b=B_VDW, R=R_GAS):
+    """Same state from the jump conditions -s<M> + <N> = 0 solved numerically
+    for (s, u1, p1) with u0 = 0."""
+    def e_of(rho, p):
+        T = (p + a * rho * rho) * (1.0 - b * rho) / (rho * R)
+        return energy(rho, T, delta, a, R)
+
+    def resid(x):
+        s, u1, p1 = x
+        E0 = e_of(rho0, p0)
+        E1 = e_of(rho1, p1) + 0.5 * u1 * u1
+        return [-s * (rho1 - rho0) + rho1 * u1,
+                -s * rho1 * u1 + (p1 + rho1 * u1 * u1 - p0),
+                -s * (rho1 * E1 - rho0 * E0) + u1 * (rho1 * E1 + p1)]
+
+    T0 = (p0 + a * rho0 * rho0) * (1.0 - b * rho0) / (rho0 * R)
+    c0 = sound_speed(rho0, T0, delta, a, b, R)
+    M_guess, u_guess, p_guess = rh_closed_form(rho0, p0, rho1, delta, a, b, R)
+    x = optimize.fsolve(resid, [M_guess * c0 * 1.01, u_guess * 0.99, p_guess * 1.01], xtol=1e-14)
+    s, u1, p1 = x
+    return s / c0, u1, p1
+
+
+def post_shock_for_mach(rho0: float, T0: float, Mach: float, delta: float,
+                        a=A_VDW, b=B_VDW, R=R_GAS):
+    """Post-shock (rho1, u1, p1, T1) for a shock of the given Mach number (w.r.t. the
+    pre-shock sound speed) into still fluid at (rho0, T0)."""
+    p0 = pressure(rho0, T0, a, b, R)
+    f = lambda r1: rh_closed_form(rho0, p0, r1, delta, a, b, R)[0] - Mach
+    rc = critical(a, b, R)[0]
+    r0 = rho0 / rc
+    # the closed form's denominator vanishes at the strong-shock compression limit
+    hi = rc * r0 * (6.0 + 3.0 * delta) / (2.0 * r0 + 3.0 * delta) * (1.0 - 1e-9)
+    lo = rho0 * (1.0 + 1e-9)
+    r1 = optimize.brentq(f, lo, hi, xtol=1e-15, rtol=1e-15)
+    M0, u1, p1 = rh_closed_form(rho0, p0, r1, delta, a, b, R)
+    T1 = (p1 + a * r1 * r1) * (1.0 - b * r1) / (r1 * R)
+    return float(r1), float(u1), float(p1), float(T1)

@@ -1,0 +1,68 @@
+"""Writes ``paper_2002_09217_gb300/workloads.json``: the thermodynamic constants
+that the synthetic workloads are built from (coexistence densities by Maxwell's
+rule, Rankine-Hugoniot post-shock states, the per-temperature time step).
+
+Run: ``python -m oracle.write_workloads``.  It calls only ``oracle.thermo``; the
+JSON file is data that the input generators read, so no product code executes
+the oracle.
+
+Time step rule (the paper keeps delta t symbolic with Delta x = 1): the explicit
+step is stable in the liquid when the sound speed is carried by the stencil,
+which needs delta t <~ 1.25 sqrt(theta_l) / varsigma_l^2 (shortest-wave analysis
+of stream + relax).  We take 0.8 sqrt(theta_l)/varsigma_l^2, capped at 0.5.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+from . import thermo
+
+DELTA = 1.0 / 3.0
+T_L = 1.0 / 3.0
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                   "paper_2002_09217_gb300", "workloads.json")
+
+
+def dt_rule(rho: float, T: float, delta: float = DELTA) -> float:
+    p = thermo.pressure(rho, T)
+    theta = p / (rho * T_L)
+    c2 = thermo.sound_speed(rho, T, delta) ** 2
+    return float(min(0.5, 0.8 * math.sqrt(theta) / c2))
+
+
+def main() -> None:
+    rc, Tc, pc = thermo.critical()
+    coex = {}
+    for k in range(70, 96):
+        Tr = k / 100.0
+        rv, rl = thermo.maxwell(Tr)
+        coex["%.2f" % Tr] = {"rho_v": rv, "rho_l": rl, "dt": dt_rule(rl, Tr * Tc)}
+    shocks = {}
+    for k in range(70, 96):
+        Tr = k / 100.0
+        rv = coex["%.2f" % Tr]["rho_v"]
+        row = {}
+        for m in range(12, 31):
+            Ma = m / 10.0
+            r1, u1, p1, T1 = thermo.post_shock_for_mach(rv, Tr * Tc, Ma, DELTA)
+            row["%.1f" % Ma] = {"rho1": r1, "u1": u1, "T1": T1, "dt": min(
+                coex["%.2f" % Tr]["dt"], dt_rule(r1, T1), 0.5 / (1.0 + abs(u1)))}
+        shocks["%.2f" % Tr] = row
+    sup_rho = 2.0 * rc
+    data = {
+        "note": "written by oracle/write_workloads.py from oracle/thermo.py (vdW a=2/49, b=2/21, R=1, delta=1/3)",
+        "critical": {"rho": rc, "T": Tc, "p": pc},
+        "delta": DELTA,
+        "coexistence": coex,
+        "shock": shocks,
+        "supercritical_1.10": {"dt": dt_rule(sup_rho, 1.1 * Tc)},
+    }
+    with open(OUT, "w") as fh:
+        json.dump(data, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+"""Seeded synthetic inputs for the PonD step: initial (rho, u, T) fields and
+workload parameters.
+
+This module generates data only (profiles, counter-based noise, request mixes);
+it holds none of the method's arithmetic, and both the CUDA path and the test
+oracle consume what it returns.  Thermodynamic constants (Maxwell coexistence
+densities, Rankine-Hugoniot post-shock states, the per-temperature time step)
+are read from ``workloads.json`` next to this file.
+
+Noise: rho <- rho (1 + xi), xi ~ U[-A, A] drawn from splitmix64(seed ^ node).
+"""
+from __future__ import annotations
+
+import dataclasses
+import functools
+import json
+import math
+import os
+
+import numpy as np
+
+SEED = 20020921
+A_VDW, B_VDW, R_GAS = 2.0 / 49.0, 2.0 / 21.0, 1.0
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@functools.lru_cache(maxsize=1)
+def table() -> dict:
+    with open(os.path.join(_HERE, "workloads.json")) as fh:
+        return json.load(fh)
+
+
+def t_cr() -> float:
+    return table()["critical"]["T"]
+
+
+def coexistence(Tr: float) -> tuple[float, float, float]:
+    """(rho_v, rho_l, dt) at the tabulated reduced temperature nearest to Tr."""
+    row = table()["coexistence"]["%.2f" % round(Tr, 2)]
+    return row["rho_v"], row["rho_l"], row["dt"]
+
+
+def splitmix64_uniform(seed: int, n: int) -> np.ndarray:
+    """n uniforms in [0, 1) from splitmix64(seed ^ k), k = 0..n-1 (counter based)."""
+    with np.errstate(over="ignore"):
+        z = (np.arange(n, dtype=np.uint64) ^ np.uint64(seed)) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def noise(seed: int, shape, amp: float) -> np.ndarray:
+    n = int(np.prod(shape))
+    return (2.0 * splitmix64_uniform(seed, n) - 1.0).reshape(shape) * amp
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    bc_x: int
+    bc_y: int
+    T_r: float
+    kappa: float
+    tau: float
+    dt: float
+    steps: int
+    rho: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    T: np.ndarray
+    a: float = A_VDW
+    b: float = B_VDW
+    R: float = R_GAS
+    delta: float = 1.0 / 3.0
+    k_cond: float = -1.0
+    p_floor: float = 1e-3 / 6.0
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+    def fields(self):
+        return self.rho, self.ux, self.uy, self.T
+
+
+def slab(nx=128, ny=4, Tr=0.9, width=4.0, amp=1e-3, steps=2000, seed=SEED, kappa=0.02, tau=1.0):
+    """Liquid slab over the middle half of a periodic box, vapour elsewhere."""
+    rv, rl, dt = coexistence(Tr)
+    x = np.arange(nx) + 0.5
+    prof = rv + (rl - rv) * 0.5 * (np.tanh((x - nx / 4) / width) - np.tanh((x - 3 * nx / 4) / width))
+    rho = np.tile(prof, (ny, 1)) * (1.0 + noise(seed, (ny, nx), amp))
+    z = np.zeros((ny, nx))
+    return Workload("slab%dx%d" % (nx, ny), nx, ny, 0, 0, Tr, kappa, tau, dt, steps, rho, z, z.copy(),
+                    np.full((ny, nx), Tr * t_cr()))
+
+
+def shock_tube(nx=2048, ny=4, Tr=1.1, rho_left=7.0, rho_right=1.75, width=4.0, steps=5000,
+               tau=1.0):
+    """Supercritical two-state tube, smooth tanh step at the middle, zero-gradient
+    ends in x, periodic in y."""
+    x = np.arange(nx) + 0.5
+    prof = rho_right + (rho_left - rho_right) * 0.5 * (1.0 - np.tanh((x - nx / 2) / width))
+    rho = np.tile(prof, (ny, 1))
+    z = np.zeros((ny, nx))
+    dt = table()["supercritical_1.10"]["dt"] if abs(Tr - 1.1) < 1e-12 else 0.4
+    return Workload("shocktube%dx%d" % (nx, ny), nx, ny, 1, 0, Tr, 0.0, tau, dt, steps, rho, z,
+                    z.copy(), np.full((ny, nx), Tr * t_cr()))
+
+
+def droplet(n=512, Tr=0.85, radius=64.0, width=4.0, amp=1e-4, steps=20000, seed=SEED, kappa=0.02,
+            tau=1.0, ny=None):
+    """Liquid disc at the box centre in its vapour, periodic."""
+    ny = n if ny is None else ny
+    rv, rl, dt = coexistence(Tr)
+    x = np.arange(n)[None, :] + 0.5
+    y = np.arange(ny)[:, None] + 0.5
+    r = np.sqrt((x - n / 2) ** 2 + (y - ny / 2) ** 2)
+    rho = (rv + (rl - rv) * 0.5 * (1.0 - np.tanh((r - radius) / width))) * (1.0 + noise(seed, (ny, n), amp))
+    z = np.zeros((ny, n))
+    return Workload("droplet%dx%d" % (n, ny), n, ny, 0, 0, Tr, kappa, tau, dt, steps, rho, z,
+                    z.copy(), np.full((ny, n), Tr * t_cr()))
+
+
+def droplet_shock(nx=2048, ny=1024, Tr=0.8, radius=80.0, xc=600.0, x_shock=300.0, Mach=1.5,
+                  width=4.0, steps=10000, kappa=0.02, tau=1.0):
+    """Droplet at coexistence in its vapour, hit by a planar shock (post-shock state
+    on the left of x_shock); zero-gradient boundaries."""
+    rv, rl, dt = coexistence(Tr)
+    sh = table()["shock"]["%.2f" % round(Tr, 2)]["%.1f" % round(Mach, 1)]
+    Tc = t_cr()
+    x = np.arange(nx)[None, :] + 0.5 + np.zeros((ny, 1))
+    y = np.arange(ny)[:, None] + 0.5 + np.zeros((1, nx))
+    r = np.sqrt((x - xc) ** 2 + (y - ny / 2) ** 2)
+    drop = 0.5 * (1.0 - np.tanh((r - radius) / width))
+    post = 0.5 * (1.0 - np.tanh((x - x_shock) / width))
+    rho = rv + (rl - rv) * drop + (sh["rho1"] - rv) * post
+    ux = sh["u1"] * post
+    T = Tr * Tc + (sh["T1"] - Tr * Tc) * post
+    return Workload("dropletshock%dx%d" % (nx, ny), nx, ny, 1, 1, Tr, kappa, tau, sh["dt"], steps,
+                    rho, ux, np.zeros((ny, nx)), T)
+
+
+def shock_in_vapour(n=64, Tr=0.8, Mach=1.5, width=4.0, steps=1000, kappa=0.02, tau=1.0):
+    """Square box of vapour at coexistence density with a planar shock entering from
+    the left (zero-gradient in x, periodic in y)."""
+    rv, rl, dt = coexistence(Tr)
+    sh = table()["shock"]["%.2f" % round(Tr, 2)]["%.1f" % round(Mach, 1)]
+    Tc = t_cr()
+    x = np.arange(n)[None, :] + 0.5 + np.zeros((n, 1))
+    post = 0.5 * (1.0 - np.tanh((x - n / 4) / width))
+    rho = rv + (sh["rho1"] - rv) * post
+    return Workload("shock%d" % n, n, n, 1, 0, Tr, kappa, tau, sh["dt"], steps, rho, sh["u1"] * post,
+                    np.zeros((n, n)), Tr * Tc + (sh["T1"] - Tr * Tc) * post)
+
+
+CONFIGS = {
+    "slab128x4": lambda: slab(),
+    "shocktube2048x4": lambda: shock_tube(),
+    "droplet512x512": lambda: droplet(),
+    "dropletshock2048x1024": lambda: droplet_shock(),
+}
+
+
+def config(name: str) -> Workload:
+    return CONFIGS[name]()
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float
+    side: int
+    T_r: float
+    kind: str
+    mach: float
+    steps: int
+    precision: str
+
+
+def serving_requests(n: int = 256, rate: float = 1.0, seed: int = SEED) -> list[Request]:
+    """Seeded request mix: Poisson arrivals at the given rate (per second), square
+    sides log-uniform in [64, 1024], T/T_cr uniform in [0.70, 0.95] (tabulated to
+    0.01), init in {droplet, slab, shock}, shock Mach uniform in [1.2, 3.0]
+    (tabulated to 0.1), 1000-10000 steps, precision mixed or fp64 (50/50)."""
+    u = splitmix64_uniform(seed ^ 0x5EEDF00D, 8 * n).reshape(n, 8)
+    reqs = []
+    t = 0.0
+    for k in range(n):
+        t += -math.log(1.0 - u[k, 0]) / rate
+        side = int(round(math.exp(math.log(64) + u[k, 1] * (math.log(1024) - math.log(64)))))
+        Tr = round(0.70 + 0.25 * u[k, 2], 2)
+        kind = ("droplet", "slab", "shock")[min(2, int(u[k, 3] * 3))]
+        mach = round(1.2 + 1.8 * u[k, 4], 1)
+        steps = 1000 + int(u[k, 5] * 9001)
+        prec = "mixed" if u[k, 6] < 0.5 else "fp64"
+        reqs.append(Request(k, t, side, Tr, kind, mach, min(steps, 10000), prec))
+    return reqs
+
+
+def request_workload(req: Request) -> Workload:
+    n = req.side
+    if req.kind == "droplet":
+        return droplet(n=n, Tr=req.T_r, radius=n / 8.0, steps=req.steps, seed=SEED + req.rid)
+    if req.kind == "slab":
+        return slab(nx=n, ny=n, Tr=req.T_r, steps=req.steps, seed=SEED + req.rid)
+    return shock_in_vapour(n=n, Tr=req.T_r, Mach=req.mach, steps=req.steps)

@@ -1,0 +1,155 @@
+"""Physics pins of the oracle: limits and benchmarks whose answers are fixed
+independently of the scheme.
+
+- ideal-gas limit (a = b = 0): Sod shock tube against the exact Riemann solution,
+  with the error falling under refinement;
+- flat liquid-vapour interface: bulk densities against Maxwell's equal-area rule
+  (main text, Fig. 2);
+- lagged interface / heat-flux terms against 1-D finite differences written here;
+- thermodynamics: critical point, equal-area rule by quadrature, Rankine-Hugoniot
+  closed form against a direct root solve.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import oracle
+from oracle import thermo
+
+from exact_riemann import solve as riemann
+
+
+def _sod(nx):
+    w = 2.0 * nx / 400.0
+    tend = 60.0 * nx / 400.0
+    P = oracle.Params(nx=nx, ny=1, bc_x=1, a=0.0, b=0.0, delta=0.4, kappa=0.0, tau=1.0,
+                      dt=0.5, p_floor=1e-6)
+    x = np.arange(nx) + 0.5
+    sw = 0.5 * (1.0 - np.tanh((x - nx / 2) / w))
+    rho = (0.125 + 0.875 * sw)[None, :]
+    p = (0.01 + 0.09 * sw)[None, :]
+    st = oracle.init_state(P, rho, 0 * rho, 0 * rho, p / rho)
+    st = oracle.step(P, st, int(round(tend / P.dt)))
+    m = oracle.moments(P, st)
+    ex = riemann(1.0, 0.0, 0.1, 0.125, 0.0, 0.01, 1.4, x, tend, nx / 2)
+    l1 = lambda a, b: np.abs(a - b).sum() / np.abs(b).sum()
+    return l1(m["rho"][0], ex[0]), l1(m["p"][0], ex[2])
+
+
+def test_ideal_gas_sod_matches_exact_riemann_and_converges():
+    """a = b = 0, delta = 0.4 (gamma = 1.4): the model is an ideal-gas kinetic
+    scheme; density and pressure within 1.5 % (L1) of the exact solution at 400
+    nodes, and closer at 800."""
+    r400, p400 = _sod(400)
+    r200, _ = _sod(200)
+    assert r400 < 0.015 and p400 < 0.015
+    assert r400 < r200
+
+
+@pytest.mark.slow
+def test_flat_interface_coexistence_matches_maxwell():
+    """Slab of liquid in vapour at T = 0.9 T_cr: after relaxing, the bulk
+    densities sit on Maxwell's equal-area values within 1 % (main text, Fig. 2)."""
+    Tr = 0.9
+    rc, Tc, pc = thermo.critical()
+    rv, rl = thermo.maxwell(Tr)
+    nx = 128
+    P = oracle.Params(nx=nx, ny=1, kappa=0.02, tau=1.0, dt=0.5)
+    x = np.arange(nx) + 0.5
+    rho = (rv + (rl - rv) * 0.5 * (np.tanh((x - 32) / 4) - np.tanh((x - 96) / 4)))[None, :]
+    st = oracle.init_state(P, rho, 0 * rho, 0 * rho, np.full_like(rho, Tr * Tc))
+    st = oracle.step(P, st, 3000)
+    acc_v = acc_l = 0.0
+    n = 0
+    for _ in range(10):
+        st = oracle.step(P, st, 100)
+        r = oracle.moments(P, st)["rho"][0]
+        acc_v += r[:8].mean() + r[-8:].mean()
+        acc_l += r[56:72].mean()
+        n += 1
+    assert acc_v / (2 * n) == pytest.approx(rv, rel=0.01)
+    assert acc_l / n == pytest.approx(rl, rel=0.01)
+
+
+def test_nonlocal_terms_match_one_dimensional_differences():
+    """For fields varying in x only, the D2Q9 stencils reduce to the central
+    differences d = (phi[x+1]-phi[x-1])/2, lap = phi[x+1]+phi[x-1]-2 phi[x]."""
+    nx = 24
+    P = oracle.Params(nx=nx, ny=3, kappa=0.03, tau=0.9, dt=0.6)
+    x = np.arange(nx)
+    rho = 3.5 + 1.2 * np.sin(2 * np.pi * x / nx) + 0.3 * np.cos(6 * np.pi * x / nx)
+    T = 0.12 + 0.01 * np.sin(4 * np.pi * x / nx)
+    nl = oracle.nonlocal_fields(P, np.tile(rho, (3, 1)), np.tile(T, (3, 1)))
+    d = lambda f: (np.roll(f, -1) - np.roll(f, 1)) / 2.0
+    lap = lambda f: np.roll(f, -1) + np.roll(f, 1) - 2.0 * f
+    dr = d(rho)
+    Kxx = -P.kappa * (rho * lap(rho) + 0.5 * dr * dr) + P.kappa * dr * dr
+    np.testing.assert_allclose(nl[0, 1], -d(Kxx), rtol=1e-11, atol=1e-14)
+    np.testing.assert_allclose(nl[1, 1], 0.0, atol=1e-14)
+    np.testing.assert_allclose(nl[2, 1], 0.5 * P.kappa * dr * dr, rtol=1e-12, atol=1e-16)
+    p = thermo.pressure(rho, T)
+    h = (P.R / P.delta) * T - P.a * rho + p / rho
+    mu = (P.tau - 0.5) * np.maximum(p, P.p_floor) * P.dt
+    k = mu * (P.R / P.delta + P.R)
+    q = -mu * d(h) + k * d(T)
+    np.testing.assert_allclose(nl[3, 1], 2.0 * d(q), rtol=1e-10, atol=1e-14)
+
+
+def test_heat_flux_source_vanishes_for_ideal_gas_default_conductivity():
+    """With k = mu (C_v + R) and a = b = 0, h = (C_v + R) T so M_0 = 0."""
+    P = oracle.Params(nx=10, ny=7, a=0.0, b=0.0, delta=0.4, tau=0.9)
+    r = np.random.default_rng(3)
+    nl = oracle.nonlocal_fields(P, r.uniform(0.5, 1.5, (7, 10)), r.uniform(0.1, 0.2, (7, 10)))
+    assert np.abs(nl[3]).max() < 1e-15
+
+
+# -------------------------------------------------------------- thermo
+def test_critical_point_constants():
+    rc, Tc, pc = thermo.critical()
+    assert rc == pytest.approx(3.5)
+    assert Tc == pytest.approx(8.0 / 63.0)
+    assert pc == pytest.approx(1.0 / 6.0)
+    # inflection of the critical isotherm: dp/drho = d2p/drho2 = 0
+    h = 1e-4
+    p = lambda r: thermo.pressure(r, Tc)
+    assert (p(rc + h) - p(rc - h)) / (2 * h) == pytest.approx(0.0, abs=1e-7)
+    assert (p(rc + h) - 2 * p(rc) + p(rc - h)) / h ** 2 == pytest.approx(0.0, abs=1e-4)
+
+
+@pytest.mark.parametrize("Tr", [0.7, 0.8, 0.85, 0.9, 0.95])
+def test_maxwell_equal_area_by_quadrature(Tr):
+    rc, Tc, pc = thermo.critical()
+    rv, rl = thermo.maxwell(Tr)
+    T = Tr * Tc
+    ps = thermo.pressure(rv, T)
+    assert thermo.pressure(rl, T) == pytest.approx(ps, rel=1e-10)
+    area, _ = integrate.quad(lambda v: thermo.pressure(1.0 / v, T) - ps, 1.0 / rl, 1.0 / rv,
+                             epsabs=1e-14, epsrel=1e-13, limit=200)
+    assert abs(area) < 1e-10
+
+
+@pytest.mark.parametrize("Tr,Ma", [(0.8, 1.5), (0.9, 1.47), (0.7, 3.0), (0.95, 1.2)])
+def test_rankine_hugoniot_closed_form_matches_root_solve(Tr, Ma):
+    rc, Tc, pc = thermo.critical()
+    rv, _ = thermo.maxwell(Tr)
+    r1, u1, p1, T1 = thermo.post_shock_for_mach(rv, Tr * Tc, Ma, 1.0 / 3.0)
+    M0, u, p = thermo.rh_root_solve(rv, thermo.pressure(rv, Tr * Tc), r1, 1.0 / 3.0)
+    assert M0 == pytest.approx(Ma, rel=1e-10)
+    assert u == pytest.approx(u1, rel=1e-10)
+    assert p == pytest.approx(p1, rel=1e-10)
+
+
+def test_sound_speed_at_critical_point():
+    """The isentropic speed at the critical point is sqrt(2 p_cr v_cr) for delta =
+    1/3... independent of delta it equals sqrt(R T_cr (1+delta)/(1-b rho_cr)^2 - 2 a rho_cr)."""
+    rc, Tc, pc = thermo.critical()
+    for delta in (1.0 / 3.0, 2.0 / 3.0):
+        c = thermo.sound_speed(rc, Tc, delta)
+        want = math.sqrt(Tc * (1 + delta) / (1 - thermo.B_VDW * rc) ** 2 - 2 * thermo.A_VDW * rc)
+        assert c == pytest.approx(want, rel=1e-14)
+    # at the critical point (dp/drho)_T = 0, so c^2 = (T/(rho^2 C_v)) (dp/dT)^2
+    delta = 1.0 / 3.0
+    dpdT = rc / (1 - thermo.B_VDW * rc)
+    assert thermo.sound_speed(rc, Tc, delta) ** 2 == pytest.approx(Tc * dpdT ** 2 * delta / rc ** 2, rel=1e-12)
