@@ -1,0 +1,164 @@
+/*
+ * pond.h -- C ABI of libpond: the GB300 (sm_103a) time step of the two-population
+ * "Particles on Demand" (PonD) kinetic model of a van der Waals fluid
+ * (Reyhanian, Dorschner & Karlin, "Thermokinetic model of compressible multiphase
+ * flows", arXiv:2002.09217).
+ *
+ * One time step per node (all on the GPU, no CPU fallback):
+ *   1. frame search: predictor = the node's previous gauge lambda = (theta, u);
+ *      corrector = re-stream with theta = max(p, p_floor)/(rho T_L) and u from the
+ *      streamed moments (shifted velocities v_i = sqrt(theta) c_i + u, Eq. particle
+ *      velocity) until the relative change is <= tol or max_iter streams were done;
+ *   2. semi-Lagrangian streaming of f and g from x - v_i dt (Eqs. f/g streaming):
+ *      each stencil neighbour's populations are carried into the arrival gauge by the
+ *      moment-matching transfer matrix (SM "Transfer matrix") and combined with the
+ *      4x4 cubic Lagrange stencil (SM "Reconstruction");
+ *   3. moments rho, rho u, 2 rho E (moments Eq.), e -> T by the vdW energy
+ *      e = C_v T - a rho, and the BGK collision of f and g with the Korteweg force
+ *      source S_i, the heat-flux correction and the forced g equilibrium
+ *      (Eqs. f/g collision, S-i, korteweg, gtilde, new geq).
+ * The non-local terms (force F = -div K, interface energy, heat-flux source M_0)
+ * use the previous step's density and temperature.
+ *
+ * Conventions
+ *   - Lattice D2Q9 (the only one): c = (cx, cy), cx, cy in {-1, 0, 1}; population
+ *     index i = 3*(cy+1) + (cx+1); W = W_cx W_cy with W_0 = 2/3, W_+-1 = 1/6; T_L = 1/3.
+ *   - Grids are nx * ny nodes, Delta x = 1, row-major with x fastest: node = y*nx + x.
+ *   - Host arrays are always caller-owned; they are read or written during the call
+ *     only.  Device memory is owned by the context; it is taken from the caller's
+ *     allocator callbacks when given (e.g. PyTorch's caching allocator), else from
+ *     cudaMalloc.
+ *   - All work is enqueued on the context's stream (opts.stream, NULL = the legacy
+ *     default stream).  Calls that return host data synchronise that stream.
+ *   - Errors are returned as pond_status; pond_last_error() gives a message.  Device
+ *     conditions (non-converged frame search, pressure floor hit, NaN) are counted on
+ *     the device and reported by pond_stats().  There is no CPU fallback: a missing
+ *     or unusable GPU is POND_ECUDA.
+ *   - A context is not thread safe; distinct contexts may be used concurrently.
+ */
+#ifndef POND_H
+#define POND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pond_ctx pond_ctx;
+
+typedef enum {
+    POND_OK = 0,
+    POND_EINVAL = 1,    /* invalid argument or parameter out of range             */
+    POND_ENOMEM = 2,    /* device allocation failed                               */
+    POND_ECUDA = 3,     /* CUDA runtime error (message in pond_last_error)         */
+    POND_ENONCONV = 4,  /* reserved: frame search did not converge somewhere       */
+    POND_ETHETA = 5,    /* reserved: pressure floor was hit                       */
+    POND_ENAN = 6,      /* a NaN/Inf appeared in the state (see pond_stats)        */
+    POND_ETIMEOUT = 7   /* reserved for bounded device waits                      */
+} pond_status;
+
+enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
+enum { POND_D2Q9 = 0 };                            /* lattice                         */
+enum { POND_VDW = 0, POND_IDEAL = 1 };             /* EoS: IDEAL forces a = b = 0     */
+enum { POND_FP64 = 0, POND_MIXED = 1 };            /* arithmetic / storage form       */
+
+/* Grid: nx, ny >= 1; bc_x, bc_y: POND_PERIODIC, or POND_ZEROGRAD (index clamp). */
+typedef struct { int32_t nx, ny; int32_t bc_x, bc_y; } pond_grid;
+
+typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9               */
+
+/* van der Waals EoS p = rho R T/(1 - b rho) - a rho^2 with e = (R/delta) T - a rho
+ * (main text; SM "Thermodynamics"); 0 < delta <= 2/3. */
+typedef struct { int32_t kind; double a, b, R, delta; } pond_eos;
+
+/* Options.  precision: POND_FP64 (all FP64) or POND_MIXED (FP32 populations and
+ * streaming/collision arithmetic; FP64 e->T, EoS, frame residual and sums).
+ * dt: time step (Delta x = 1), 0 < dt <= 1.  tol / max_iter: frame search stop rule.
+ * k_cond: conductivity; < 0 selects k = mu (C_v + R), mu = (tau - 1/2) P dt.
+ * p_floor: pressure floor of the gauge temperature theta = max(p, p_floor)/(rho T_L).
+ * stream: a cudaStream_t (NULL = default stream).
+ * dalloc/dfree/alloc_ctx: optional device allocator (both or neither). */
+typedef struct {
+    int32_t precision;
+    int32_t max_iter;
+    double tol;
+    double dt;
+    double k_cond;
+    double p_floor;
+    void *stream;
+    void *(*dalloc)(size_t bytes, void *alloc_ctx);
+    void (*dfree)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
+} pond_opts;
+
+/* Device counters accumulated since the last pond_stats() call that reset them. */
+typedef struct {
+    int64_t steps;         /* time steps taken by this context                  */
+    int64_t node_updates;  /* nx*ny*steps                                       */
+    int64_t streams;       /* streaming passes (frame-search iterations) summed */
+    int64_t nonconverged;  /* node updates whose frame search hit max_iter      */
+    int64_t clamped;       /* node updates with p < p_floor                     */
+    int64_t nonfinite;     /* node updates that produced NaN/Inf                */
+} pond_stats_t;
+
+/* Create a context and allocate its device state (two state buffers of 25 planes
+ * plus scratch).  kappa >= 0: Korteweg coefficient (Eq. korteweg); tau > 1/2: BGK
+ * relaxation time, omega = 1/tau.  On success *out owns the context. */
+pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, const pond_eos *eos,
+                        double kappa, double tau, const pond_opts *opts, pond_ctx **out);
+
+/* Equilibrium initial state from host fields rho, ux, uy, T (nx*ny doubles each):
+ * f_i = rho W_i, g_i = the co-moving g equilibrium (Eq. geq) including the interface
+ * energy kappa |grad rho|^2 / 2, gauge theta = max(p, p_floor)/(rho T_L).
+ * Requires rho > 0, b rho < 1, T > 0 everywhere (POND_EINVAL otherwise). */
+pond_status pond_init_fields(pond_ctx *ctx, const double *rho, const double *ux,
+                             const double *uy, const double *T);
+
+/* Same with device pointers (nx*ny doubles each, read on the context stream). */
+pond_status pond_init_fields_device(pond_ctx *ctx, const double *d_rho, const double *d_ux,
+                                    const double *d_uy, const double *d_T);
+
+/* Advance n >= 0 time steps (asynchronous on the context stream). */
+pond_status pond_step(pond_ctx *ctx, int64_t n);
+
+/* Macroscopic fields to host arrays (nx*ny doubles each, NULL skips a field):
+ * rho, fluid velocity uhat = u + F dt/(2 rho), T, p (vdW EoS).  Synchronises. */
+pond_status pond_moments(pond_ctx *ctx, double *rho, double *ux, double *uy, double *T,
+                         double *p);
+
+/* Same into device arrays (asynchronous). */
+pond_status pond_moments_device(pond_ctx *ctx, double *d_rho, double *d_ux, double *d_uy,
+                                double *d_T, double *d_p);
+
+/* Global sums in FP64 with compensated summation: out = {sum rho, sum rho uhat_x,
+ * sum rho uhat_y, sum_nodes sum_i g_i / 2 (total energy)}.  Synchronises. */
+pond_status pond_conservation(pond_ctx *ctx, double out[4]);
+
+/* Full state as 25 host planes of nx*ny doubles: f_0..f_8, g_0..g_8, theta, u_x,
+ * u_y (the gauge the populations are stored in), rho, T, uhat_x, uhat_y.
+ * pond_get_state synchronises; pond_set_state replaces the current state. */
+pond_status pond_get_state(pond_ctx *ctx, double *state);
+pond_status pond_set_state(pond_ctx *ctx, const double *state);
+
+/* Read (and, if reset != 0, zero) the device counters.  Synchronises. */
+pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);
+
+/* Bytes of device memory the context holds (state + scratch). */
+size_t pond_device_bytes(const pond_ctx *ctx);
+
+/* Destroy the context and release its device memory (NULL is a no-op). */
+void pond_destroy(pond_ctx *ctx);
+
+/* Last error message of the context (never NULL; "" after success). */
+const char *pond_last_error(const pond_ctx *ctx);
+
+/* Library version string. */
+const char *pond_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POND_H */

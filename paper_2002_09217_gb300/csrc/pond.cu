@@ -1,0 +1,380 @@
+// pond.cu -- host side of libpond: the C ABI declared in include/pond.h.
+//
+// A context owns two 25-plane state buffers (ping-pong), 9 scratch planes for the
+// non-local terms, a 5-plane FP64 staging buffer for host <-> device field copies and
+// a small block of device counters.  Every call enqueues on the context stream.
+#include "pond.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pond_kernels.cuh"
+
+using namespace pond;
+
+struct pond_ctx {
+    pond_grid grid{};
+    pond_eos eos{};
+    pond_opts opts{};
+    double kappa = 0.0, tau = 1.0;
+    int device = 0;
+    size_t N = 0, esize = 0;
+    void *state[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *scratch = nullptr;       // NSC planes of R
+    double *stage = nullptr;       // 5 planes of double
+    double *part = nullptr;        // conservation partials (nblk * 8) + out[4]
+    int red_blocks = 0;
+    DevStats *dstats = nullptr;
+    cudaStream_t stream = nullptr;
+    int64_t steps = 0;
+    bool initialised = false;
+    std::string err;
+    size_t bytes = 0;
+    DevParams dp{};
+};
+
+namespace {
+
+pond_status fail(pond_ctx *c, pond_status st, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return st;
+}
+
+pond_status cuda_fail(pond_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, POND_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                 \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+void *dev_alloc(pond_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (c->opts.dalloc) {
+        p = c->opts.dalloc(bytes, c->opts.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        p = nullptr;
+    }
+    if (p) c->bytes += bytes;
+    return p;
+}
+
+void dev_free(pond_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->opts.dfree) c->opts.dfree(p, c->opts.alloc_ctx);
+    else cudaFree(p);
+}
+
+inline unsigned blocks_for(size_t n, unsigned bs) { return (unsigned)((n + bs - 1) / bs); }
+
+bool mixed(const pond_ctx *c) { return c->opts.precision == POND_MIXED; }
+
+template <typename R>
+pond_status launch_step(pond_ctx *c)
+{
+    const R *in = (const R *)c->state[c->cur];
+    R *out = (R *)c->state[1 - c->cur];
+    R *sc = (R *)c->scratch;
+    const unsigned nb = blocks_for(c->N, 256), nb128 = blocks_for(c->N, 128);
+    k_nonlocal1<R><<<nb, 256, 0, c->stream>>>(c->dp, in, sc);
+    k_nonlocal2<R><<<nb, 256, 0, c->stream>>>(c->dp, sc);
+    k_step<R><<<nb128, 128, 0, c->stream>>>(c->dp, in, out, sc, c->dstats);
+    c->cur = 1 - c->cur;
+    return POND_OK;
+}
+
+template <typename R>
+void launch_init(pond_ctx *c, const double *rho, const double *ux, const double *uy, const double *T)
+{
+    k_init<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, rho, ux, uy, T,
+                                                             (R *)c->state[c->cur], c->dstats);
+}
+
+template <typename R>
+void launch_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T, double *p)
+{
+    k_moments<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur],
+                                                                rho, ux, uy, T, p);
+}
+
+template <typename R>
+void launch_conserve(pond_ctx *c)
+{
+    k_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
+    k_conserve2<<<1, 32, 0, c->stream>>>(c->part, c->red_blocks, c->part + 8 * c->red_blocks);
+}
+
+pond_status check_ctx(pond_ctx *c)
+{
+    if (!c) return POND_EINVAL;
+    c->err.clear();
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return POND_OK;
+}
+
+pond_status init_common(pond_ctx *c, const double *d_rho, const double *d_ux, const double *d_uy,
+                        const double *d_T)
+{
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream), "cudaMemsetAsync");
+    if (mixed(c)) launch_init<float>(c, d_rho, d_ux, d_uy, d_T);
+    else launch_init<double>(c, d_rho, d_ux, d_uy, d_T);
+    CK(cudaGetLastError(), "k_init launch");
+    DevStats hs{};
+    CK(cudaMemcpyAsync(&hs, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream), "cudaMemsetAsync");
+    if (hs.bad_init)
+        return fail(c, POND_EINVAL, "init fields need rho > 0, b*rho < 1 and T > 0 at every node ("
+                                        + std::to_string(hs.bad_init) + " nodes violate it)");
+    c->initialised = true;
+    c->steps = 0;
+    return POND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pond_version(void) { return "pond-gb300 0.1 (sm_103a)"; }
+
+const char *pond_last_error(const pond_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t pond_device_bytes(const pond_ctx *ctx) { return ctx ? ctx->bytes : 0; }
+
+pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, const pond_eos *eos,
+                        double kappa, double tau, const pond_opts *opts, pond_ctx **out)
+{
+    if (!out) return POND_EINVAL;
+    *out = nullptr;
+    if (!grid || !lattice || !eos || !opts) return POND_EINVAL;
+    if (grid->nx < 1 || grid->ny < 1) return POND_EINVAL;
+    if ((grid->bc_x != POND_PERIODIC && grid->bc_x != POND_ZEROGRAD) ||
+        (grid->bc_y != POND_PERIODIC && grid->bc_y != POND_ZEROGRAD))
+        return POND_EINVAL;
+    if (lattice->kind != POND_D2Q9) return POND_EINVAL;
+    if (eos->kind != POND_VDW && eos->kind != POND_IDEAL) return POND_EINVAL;
+    if (!(eos->R > 0.0) || !(eos->delta > 0.0) || !(eos->delta <= 2.0 / 3.0 + 1e-12)) return POND_EINVAL;
+    if (eos->kind == POND_VDW && (!(eos->a >= 0.0) || !(eos->b >= 0.0))) return POND_EINVAL;
+    if (!(kappa >= 0.0) || !(tau > 0.5) || !std::isfinite(tau) || !std::isfinite(kappa)) return POND_EINVAL;
+    if (opts->precision != POND_FP64 && opts->precision != POND_MIXED) return POND_EINVAL;
+    if (!(opts->dt > 0.0) || !(opts->dt <= 1.0)) return POND_EINVAL;
+    if (!(opts->tol > 0.0) || opts->max_iter < 1 || opts->max_iter > 1000) return POND_EINVAL;
+    if (!(opts->p_floor > 0.0)) return POND_EINVAL;
+    if ((opts->dalloc == nullptr) != (opts->dfree == nullptr)) return POND_EINVAL;
+
+    pond_ctx *c = new pond_ctx();
+    c->grid = *grid;
+    c->eos = *eos;
+    if (eos->kind == POND_IDEAL) { c->eos.a = 0.0; c->eos.b = 0.0; }
+    c->opts = *opts;
+    c->kappa = kappa;
+    c->tau = tau;
+    c->stream = (cudaStream_t)opts->stream;
+    c->N = (size_t)grid->nx * (size_t)grid->ny;
+    c->esize = opts->precision == POND_MIXED ? sizeof(float) : sizeof(double);
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        std::string m = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
+        delete c;
+        (void)m;
+        return POND_ECUDA;
+    }
+    DevParams &d = c->dp;
+    d.nx = grid->nx; d.ny = grid->ny; d.bcx = grid->bc_x; d.bcy = grid->bc_y;
+    d.N = (long long)c->N;
+    d.a = c->eos.a; d.b = c->eos.b; d.R = c->eos.R; d.delta = c->eos.delta; d.cv = c->eos.R / c->eos.delta;
+    d.kappa = kappa; d.tau = tau; d.omega = 1.0 / tau; d.dt = opts->dt; d.k_cond = opts->k_cond;
+    d.p_floor = opts->p_floor; d.tol = opts->tol; d.max_iter = opts->max_iter;
+
+    c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
+    size_t sb = (size_t)NPL * c->N * c->esize;
+    c->state[0] = dev_alloc(c, sb);
+    c->state[1] = dev_alloc(c, sb);
+    c->scratch = dev_alloc(c, (size_t)NSC * c->N * c->esize);
+    c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
+    c->part = (double *)dev_alloc(c, (8 * (size_t)c->red_blocks + 8) * sizeof(double));
+    c->dstats = (DevStats *)dev_alloc(c, sizeof(DevStats));
+    if (!c->state[0] || !c->state[1] || !c->scratch || !c->stage || !c->part || !c->dstats) {
+        pond_destroy(c);
+        return POND_ENOMEM;
+    }
+    if (cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream) != cudaSuccess) {
+        pond_destroy(c);
+        return POND_ECUDA;
+    }
+    *out = c;
+    return POND_OK;
+}
+
+void pond_destroy(pond_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    dev_free(c, c->state[0]);
+    dev_free(c, c->state[1]);
+    dev_free(c, c->scratch);
+    dev_free(c, c->stage);
+    dev_free(c, c->part);
+    dev_free(c, c->dstats);
+    delete c;
+}
+
+pond_status pond_init_fields(pond_ctx *c, const double *rho, const double *ux, const double *uy,
+                             const double *T)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!rho || !ux || !uy || !T) return fail(c, POND_EINVAL, "null field pointer");
+    size_t bytes = c->N * sizeof(double);
+    const double *src[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        CK(cudaMemcpyAsync(c->stage + k * c->N, src[k], bytes, cudaMemcpyHostToDevice, c->stream),
+           "cudaMemcpyAsync H2D");
+    return init_common(c, c->stage, c->stage + c->N, c->stage + 2 * c->N, c->stage + 3 * c->N);
+}
+
+pond_status pond_init_fields_device(pond_ctx *c, const double *d_rho, const double *d_ux,
+                                    const double *d_uy, const double *d_T)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!d_rho || !d_ux || !d_uy || !d_T) return fail(c, POND_EINVAL, "null field pointer");
+    return init_common(c, d_rho, d_ux, d_uy, d_T);
+}
+
+pond_status pond_step(pond_ctx *c, int64_t n)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (n < 0) return fail(c, POND_EINVAL, "negative step count");
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    for (int64_t k = 0; k < n; ++k) {
+        if (mixed(c)) launch_step<float>(c);
+        else launch_step<double>(c);
+    }
+    CK(cudaGetLastError(), "step launch");
+    c->steps += n;
+    return POND_OK;
+}
+
+pond_status pond_moments_device(pond_ctx *c, double *rho, double *ux, double *uy, double *T, double *p)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    if (mixed(c)) launch_moments<float>(c, rho, ux, uy, T, p);
+    else launch_moments<double>(c, rho, ux, uy, T, p);
+    CK(cudaGetLastError(), "k_moments launch");
+    return POND_OK;
+}
+
+pond_status pond_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T, double *p)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    double *host[5] = {rho, ux, uy, T, p};
+    double *dev[5];
+    for (int k = 0; k < 5; ++k) dev[k] = host[k] ? c->stage + k * c->N : nullptr;
+    st = pond_moments_device(c, dev[0], dev[1], dev[2], dev[3], dev[4]);
+    if (st) return st;
+    for (int k = 0; k < 5; ++k)
+        if (host[k])
+            CK(cudaMemcpyAsync(host[k], dev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+               "cudaMemcpyAsync D2H");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return POND_OK;
+}
+
+pond_status pond_conservation(pond_ctx *c, double out[4])
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!out) return fail(c, POND_EINVAL, "null output");
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    if (mixed(c)) launch_conserve<float>(c);
+    else launch_conserve<double>(c);
+    CK(cudaGetLastError(), "conservation launch");
+    CK(cudaMemcpyAsync(out, c->part + 8 * c->red_blocks, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream), "cudaMemcpyAsync D2H");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return POND_OK;
+}
+
+pond_status pond_get_state(pond_ctx *c, double *state)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!state) return fail(c, POND_EINVAL, "null output");
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    size_t total = (size_t)NPL * c->N;
+    if (!mixed(c)) {
+        CK(cudaMemcpyAsync(state, c->state[c->cur], total * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream), "cudaMemcpyAsync D2H");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        return POND_OK;
+    }
+    std::vector<float> tmp(total);
+    CK(cudaMemcpyAsync(tmp.data(), c->state[c->cur], total * sizeof(float), cudaMemcpyDeviceToHost,
+                       c->stream), "cudaMemcpyAsync D2H");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    for (size_t k = 0; k < total; ++k) state[k] = (double)tmp[k];
+    return POND_OK;
+}
+
+pond_status pond_set_state(pond_ctx *c, const double *state)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!state) return fail(c, POND_EINVAL, "null input");
+    size_t total = (size_t)NPL * c->N;
+    if (!mixed(c)) {
+        CK(cudaMemcpyAsync(c->state[c->cur], state, total * sizeof(double), cudaMemcpyHostToDevice,
+                           c->stream), "cudaMemcpyAsync H2D");
+    } else {
+        std::vector<float> tmp(total);
+        for (size_t k = 0; k < total; ++k) tmp[k] = (float)state[k];
+        CK(cudaMemcpyAsync(c->state[c->cur], tmp.data(), total * sizeof(float), cudaMemcpyHostToDevice,
+                           c->stream), "cudaMemcpyAsync H2D");
+    }
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    c->initialised = true;
+    return POND_OK;
+}
+
+pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!out) return fail(c, POND_EINVAL, "null output");
+    DevStats hs{};
+    CK(cudaMemcpyAsync(&hs, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream),
+       "cudaMemcpyAsync D2H");
+    if (reset) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream), "cudaMemsetAsync");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    out->steps = c->steps;
+    out->node_updates = c->steps * (int64_t)c->N;
+    out->streams = (int64_t)hs.streams;
+    out->nonconverged = (int64_t)hs.nonconv;
+    out->clamped = (int64_t)hs.clamped;
+    out->nonfinite = (int64_t)hs.nonfinite;
+    return hs.nonfinite ? fail(c, POND_ENAN, "non-finite values in the state") : POND_OK;
+}
+
+}  // extern "C"

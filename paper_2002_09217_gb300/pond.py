@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libpond (``include/pond.h``): argument marshalling only.
+
+Every step of the time step runs in the CUDA kernels of ``libpond.so``; there is
+no CPU fallback.  If the library cannot be loaded, or no GPU is usable, the calls
+raise.  PyTorch is used for device memory (the caching allocator backs the
+library's device buffers) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build_lib
+
+POND_PERIODIC, POND_ZEROGRAD = 0, 1
+POND_D2Q9 = 0
+POND_VDW, POND_IDEAL = 0, 1
+POND_FP64, POND_MIXED = 0, 1
+NPLANES = 25
+STATUS = {0: "POND_OK", 1: "POND_EINVAL", 2: "POND_ENOMEM", 3: "POND_ECUDA", 4: "POND_ENONCONV",
+          5: "POND_ETHETA", 6: "POND_ENAN", 7: "POND_ETIMEOUT"}
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32)]
+
+
+class Lattice(C.Structure):
+    _fields_ = [("kind", C.c_int32)]
+
+
+class Eos(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
+                ("delta", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("dt", C.c_double), ("k_cond", C.c_double), ("p_floor", C.c_double),
+                ("stream", C.c_void_p), ("dalloc", _ALLOC), ("dfree", _FREE),
+                ("alloc_ctx", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("node_updates", C.c_int64), ("streams", C.c_int64),
+                ("nonconverged", C.c_int64), ("clamped", C.c_int64), ("nonfinite", C.c_int64)]
+
+
+class PondError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load() -> C.CDLL:
+    """Load libpond.so (building it with nvcc first if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(build_lib.LIB):
+            build_lib.build()
+        lib = C.CDLL(build_lib.LIB)
+        P = C.c_void_p
+        dp = C.POINTER(C.c_double)
+        lib.pond_create.argtypes = [C.POINTER(Grid), C.POINTER(Lattice), C.POINTER(Eos), C.c_double,
+                                    C.c_double, C.POINTER(Opts), C.POINTER(P)]
+        for name, args in [("pond_init_fields", [P, dp, dp, dp, dp]),
+                           ("pond_init_fields_device", [P, P, P, P, P]),
+                           ("pond_step", [P, C.c_int64]),
+                           ("pond_moments", [P, dp, dp, dp, dp, dp]),
+                           ("pond_moments_device", [P, P, P, P, P, P]),
+                           ("pond_conservation", [P, dp]),
+                           ("pond_get_state", [P, dp]),
+                           ("pond_set_state", [P, dp]),
+                           ("pond_stats", [P, C.POINTER(Stats), C.c_int32])]:
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        lib.pond_create.restype = C.c_int
+        lib.pond_destroy.argtypes = [P]
+        lib.pond_destroy.restype = None
+        lib.pond_last_error.argtypes = [P]
+        lib.pond_last_error.restype = C.c_char_p
+        lib.pond_device_bytes.argtypes = [P]
+        lib.pond_device_bytes.restype = C.c_size_t
+        lib.pond_version.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise PondError(3, "no CUDA device available (libpond has no CPU path)")
+    return torch
+
+
+class Simulation:
+    """One PonD simulation on the current CUDA device (see include/pond.h).
+
+    precision: "mixed" (FP32 populations + FP64 EoS/residual) or "fp64".
+    """
+
+    def __init__(self, nx: int, ny: int, *, bc_x: int = POND_PERIODIC, bc_y: int = POND_PERIODIC,
+                 a: float = 2.0 / 49.0, b: float = 2.0 / 21.0, R: float = 1.0,
+                 delta: float = 1.0 / 3.0, kappa: float = 0.0, tau: float = 1.0,
+                 precision: str = "mixed", dt: float = 0.5, tol: float | None = None,
+                 max_iter: int = 20, k_cond: float = -1.0, p_floor: float = 1e-3 / 6.0,
+                 stream=None, torch_alloc: bool = True, ideal: bool = False):
+        torch = _torch()
+        self._lib = load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.N = self.nx * self.ny
+        self.precision = precision
+        if precision not in ("mixed", "fp64"):
+            raise ValueError("precision must be 'mixed' or 'fp64'")
+        if tol is None:
+            tol = 1e-6 if precision == "mixed" else 1e-12
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        self._device = self._stream.device
+        self._blocks = {}
+        if torch_alloc:
+            dev, strm = self._device, self._stream
+
+            def _alloc(nbytes, _ctx):
+                try:
+                    ptr = torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+                except RuntimeError:
+                    return None
+                self._blocks[ptr] = nbytes
+                return ptr
+
+            def _free(ptr, _ctx):
+                if ptr in self._blocks:
+                    del self._blocks[ptr]
+                    torch.cuda.caching_allocator_delete(ptr)
+
+            self._cb_alloc, self._cb_free = _ALLOC(_alloc), _FREE(_free)
+        else:
+            self._cb_alloc, self._cb_free = _ALLOC(), _FREE()
+        grid = Grid(self.nx, self.ny, bc_x, bc_y)
+        lat = Lattice(POND_D2Q9)
+        eos = Eos(POND_IDEAL if ideal else POND_VDW, a, b, R, delta)
+        opts = Opts(POND_MIXED if precision == "mixed" else POND_FP64, max_iter, tol, dt, k_cond,
+                    p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None)
+        self.params = dict(nx=nx, ny=ny, bc_x=bc_x, bc_y=bc_y, a=a, b=b, R=R, delta=delta,
+                           kappa=kappa, tau=tau, precision=precision, dt=dt, tol=tol,
+                           max_iter=max_iter, k_cond=k_cond, p_floor=p_floor)
+        ctx = C.c_void_p()
+        with torch.cuda.device(self._device):
+            st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos), kappa, tau,
+                                       C.byref(opts), C.byref(ctx))
+        if st != 0:
+            raise PondError(st, "pond_create failed")
+        self._ctx = ctx
+
+    # -- helpers ---------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            raise PondError(st, self._lib.pond_last_error(self._ctx).decode())
+
+    def _host(self, x) -> np.ndarray:
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), (self.ny, self.nx)))
+        return a
+
+    # -- API ---------------------------------------------------------------
+    def init_fields(self, rho, ux, uy, T):
+        """Host numpy arrays (ny, nx) or CUDA float64 tensors."""
+        if hasattr(rho, "is_cuda") and rho.is_cuda:
+            ts = [t.contiguous() for t in (rho, ux, uy, T)]
+            self._check(self._lib.pond_init_fields_device(self._ctx, *[C.c_void_p(t.data_ptr()) for t in ts]))
+            return
+        arrs = [self._host(v) for v in (rho, ux, uy, T)]
+        self._check(self._lib.pond_init_fields(self._ctx, *[_dptr(a) for a in arrs]))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.pond_step(self._ctx, int(n)))
+
+    def moments(self) -> dict:
+        outs = [np.empty((self.ny, self.nx)) for _ in range(5)]
+        self._check(self._lib.pond_moments(self._ctx, *[_dptr(o) for o in outs]))
+        return dict(zip(("rho", "ux", "uy", "T", "p"), outs))
+
+    def moments_device(self, out: dict):
+        """Write rho, ux, uy, T, p into given CUDA float64 tensors (keys may be absent)."""
+        ptrs = [C.c_void_p(out[k].data_ptr()) if k in out else C.c_void_p() for k in
+                ("rho", "ux", "uy", "T", "p")]
+        self._check(self._lib.pond_moments_device(self._ctx, *ptrs))
+
+    def conservation(self) -> np.ndarray:
+        out = np.zeros(4)
+        self._check(self._lib.pond_conservation(self._ctx, _dptr(out)))
+        return out
+
+    def get_state(self) -> np.ndarray:
+        out = np.empty((NPLANES, self.ny, self.nx))
+        self._check(self._lib.pond_get_state(self._ctx, _dptr(out)))
+        return out
+
+    def set_state(self, state):
+        s = np.ascontiguousarray(np.asarray(state, dtype=np.float64).reshape(NPLANES, self.ny, self.nx))
+        self._check(self._lib.pond_set_state(self._ctx, _dptr(s)))
+
+    def stats(self, reset: bool = False) -> dict:
+        s = Stats()
+        st = self._lib.pond_stats(self._ctx, C.byref(s), 1 if reset else 0)
+        d = {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+        if st not in (0, 6):
+            self._check(st)
+        d["status"] = STATUS.get(st, st)
+        return d
+
+    def device_bytes(self) -> int:
+        return int(self._lib.pond_device_bytes(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.pond_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def from_workload(w, precision: str = "mixed", **kw) -> Simulation:
+    """Simulation for an ``inputs.Workload`` (parameters only; call init_fields)."""
+    return Simulation(w.nx, w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R, delta=w.delta,
+                      kappa=w.kappa, tau=w.tau, precision=precision, dt=w.dt, k_cond=w.k_cond,
+                      p_floor=w.p_floor, **kw)

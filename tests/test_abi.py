@@ -1,0 +1,75 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function that include/pond.h declares; the product path refuses to run without a
+GPU instead of falling back to the CPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2002_09217_gb300 import build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if hdr.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", hdr)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"\b(pond_\w+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = build_lib.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("pond_create", "pond_init_fields", "pond_step", "pond_moments", "pond_destroy",
+                     "pond_conservation", "pond_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_version_string(lib):
+    lib.pond_version.restype = ctypes.c_char_p
+    assert b"sm_103a" in lib.pond_version()
+
+
+def test_invalid_parameters_are_rejected_on_the_host(lib):
+    """Parameter checks run before any device call, so they work without a GPU."""
+    from paper_2002_09217_gb300 import pond
+    L = pond.load()
+    g = pond.Grid(0, 4, 0, 0)
+    lat = pond.Lattice(0)
+    eos = pond.Eos(0, 2 / 49, 2 / 21, 1.0, 1 / 3)
+    opts = pond.Opts(1, 20, 1e-6, 0.5, -1.0, 1e-4, None, pond._ALLOC(), pond._FREE(), None)
+    out = ctypes.c_void_p()
+    assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(eos), 0.0, 1.0,
+                         ctypes.byref(opts), ctypes.byref(out)) == 1
+    g = pond.Grid(8, 8, 0, 0)
+    assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(eos), 0.0, 0.5,
+                         ctypes.byref(opts), ctypes.byref(out)) == 1      # tau must exceed 1/2
+    bad = pond.Eos(0, 2 / 49, 2 / 21, 1.0, 0.9)                           # delta > 2/3
+    assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(bad), 0.0, 1.0,
+                         ctypes.byref(opts), ctypes.byref(out)) == 1
+    assert not out.value
+    L.pond_destroy(None)
+
+
+def test_no_cpu_fallback_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2002_09217_gb300 import pond
+    with pytest.raises(pond.PondError):
+        pond.Simulation(8, 8)

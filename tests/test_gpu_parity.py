@@ -1,0 +1,183 @@
+"""GPU time step (libpond through its C ABI) against the FP64 oracle.
+
+Element-by-element parity on seeded inputs at sizes the oracle finishes in
+seconds (several 128-node launch tiles plus a ragged tail), on the full
+128x4 slab for its 2000 steps, and on the other full-size workloads through
+one-step checks at sampled nodes (the oracle steps those nodes from the GPU's
+own previous state).  Bars: FP64 <= 1e-11, mixed FP32/FP64 <= 1e-5 relative
+L-infinity per field (rho, uhat_x, uhat_y, T, p).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_09217_gb300 import inputs
+
+from parity_util import TOL, oracle_run, params_of, rel_linf, sample_nodes, state_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pond():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2002_09217_gb300 import pond as mod
+    mod.load()
+    return mod
+
+
+def gpu_run(pond, w, precision, steps=None, **kw):
+    with pond.from_workload(w, precision=precision, **kw) as sim:
+        sim.init_fields(*w.fields())
+        sim.step(w.steps if steps is None else steps)
+        return sim.moments(), sim.stats()
+
+
+def small_cases():
+    yield "slab40x6", inputs.slab(nx=40, ny=6, Tr=0.9, steps=25)
+    yield "droplet24x20", inputs.droplet(n=24, ny=20, Tr=0.9, radius=5.0, steps=20)
+    yield "shock36x10_zerograd", inputs.shock_in_vapour(n=36, Tr=0.8, Mach=1.5, steps=15)
+    yield "tube60x3_zerograd", inputs.shock_tube(nx=60, ny=3, width=2.0, steps=30)
+    yield "column1x33", inputs.slab(nx=1, ny=33, Tr=0.9, steps=10)
+    yield "single_node", inputs.slab(nx=1, ny=1, Tr=0.9, steps=5)
+    yield "strong_shock_Tr0.7_Ma3", inputs.shock_in_vapour(n=20, Tr=0.7, Mach=3.0, steps=12)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", [c[0] for c in small_cases()])
+def test_small_grids_match_oracle(pond, case, precision):
+    w = dict(small_cases())[case]
+    P, st, ostats = oracle_run(w)
+    ref = oracle.moments(P, st)
+    got, gstats = gpu_run(pond, w, precision)
+    err = rel_linf(got, ref)
+    assert max(err.values()) <= TOL[precision], err
+    assert gstats["nonfinite"] == 0
+    if precision == "fp64":
+        # same frame-search work up to nodes sitting at the tolerance boundary
+        assert abs(gstats["streams"] - ostats["streams"]) <= 0.01 * ostats["streams"] + 2
+
+
+def test_ideal_gas_limit_matches_oracle(pond):
+    nx = 64
+    x = np.arange(nx) + 0.5
+    sw = 0.5 * (1.0 - np.tanh((x - nx / 2) / 2.0))
+    rho = np.tile(0.125 + 0.875 * sw, (2, 1))
+    T = np.tile((0.01 + 0.09 * sw), (2, 1)) / rho
+    w = inputs.Workload("sod64x2", nx, 2, 1, 0, 0.0, 0.0, 1.0, 0.5, 40, rho, 0 * rho, 0 * rho, T,
+                        a=0.0, b=0.0, delta=0.4, p_floor=1e-6)
+    P, st, _ = oracle_run(w)
+    ref = oracle.moments(P, st)
+    for prec in ("fp64", "mixed"):
+        got, _ = gpu_run(pond, w, prec)
+        err = rel_linf(got, ref)
+        assert max(err.values()) <= TOL[prec], (prec, err)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_slab128x4_full_run(pond, precision):
+    """The 128x4 quasi-1D slab at T = 0.9 T_cr with seeded noise, all 2000 steps."""
+    w = inputs.slab()
+    P, st, _ = oracle_run(w)
+    ref = oracle.moments(P, st)
+    got, gstats = gpu_run(pond, w, precision)
+    err = rel_linf(got, ref)
+    assert max(err.values()) <= TOL[precision], err
+    assert gstats["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shocktube_reduced_full_run(pond, precision):
+    """The supercritical tube recipe at 256x4 for 600 steps (waves reach the walls)."""
+    w = inputs.shock_tube(nx=256, ny=4, steps=600)
+    P, st, _ = oracle_run(w)
+    ref = oracle.moments(P, st)
+    got, _ = gpu_run(pond, w, precision)
+    err = rel_linf(got, ref)
+    assert max(err.values()) <= TOL[precision], err
+
+
+def one_step_sampled(pond, w, precision, steps, nsample=64):
+    """Run the GPU to `steps`, then compare its next step at sampled nodes with the
+    oracle stepping those nodes from the GPU's own state."""
+    with pond.from_workload(w, precision=precision) as sim:
+        sim.init_fields(*w.fields())
+        sim.step(steps)
+        prev = sim.get_state()
+        sim.step(1)
+        nxt = sim.get_state().reshape(25, -1)
+        st = sim.stats()
+    P = params_of(w, tol=(1e-12 if precision == "fp64" else 1e-6))
+    nodes = sample_nodes(w.nx, w.ny, nsample)
+    rows = oracle.step_nodes(P, prev, nodes)
+    got = state_fields(P, nxt[:, nodes].T)
+    ref = state_fields(P, rows)
+    return rel_linf(got, ref), st
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_shocktube2048x4_sampled_at_full_steps(pond, precision):
+    w = inputs.shock_tube()
+    err, st = one_step_sampled(pond, w, precision, w.steps - 1)
+    assert max(err.values()) <= TOL[precision], err
+    assert st["nonfinite"] == 0
+
+
+def test_droplet512_sampled(pond):
+    w = inputs.droplet()
+    err, st = one_step_sampled(pond, w, "mixed", 1000)
+    assert max(err.values()) <= TOL["mixed"], err
+    assert st["nonfinite"] == 0
+
+
+def test_dropletshock2048x1024_sampled(pond):
+    w = inputs.droplet_shock()
+    err, st = one_step_sampled(pond, w, "mixed", 200)
+    assert max(err.values()) <= TOL["mixed"], err
+
+
+def test_conservation_sums_match_oracle_state(pond):
+    w = inputs.droplet(n=48, ny=40, Tr=0.9, radius=10.0, steps=30)
+    P, st, _ = oracle_run(w)
+    flat = st.reshape(25, -1)
+    want = [flat[21].sum(), (flat[21] * flat[23]).sum(), (flat[21] * flat[24]).sum(),
+            0.5 * flat[9:18].sum()]
+    with pond.from_workload(w, precision="fp64") as sim:
+        sim.init_fields(*w.fields())
+        sim.step(w.steps)
+        got = sim.conservation()
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12)
+
+
+def test_device_pointer_paths_equal_host_paths(pond):
+    import torch
+    w = inputs.slab(nx=40, ny=6, steps=5)
+    dev = [torch.tensor(a, device="cuda", dtype=torch.float64) for a in w.fields()]
+    with pond.from_workload(w, precision="mixed") as a, pond.from_workload(w, precision="mixed") as b:
+        a.init_fields(*w.fields())
+        b.init_fields(*dev)
+        a.step(5)
+        b.step(5)
+        ha = a.moments()
+        out = {k: torch.empty((w.ny, w.nx), device="cuda", dtype=torch.float64) for k in ha}
+        b.moments_device(out)
+        torch.cuda.synchronize()
+        for k in ha:
+            np.testing.assert_array_equal(ha[k], out[k].cpu().numpy())
+
+
+def test_state_round_trip_and_invalid_init(pond):
+    w = inputs.slab(nx=16, ny=4, steps=3)
+    with pond.from_workload(w, precision="fp64") as sim:
+        sim.init_fields(*w.fields())
+        sim.step(3)
+        s = sim.get_state()
+        sim.set_state(s)
+        np.testing.assert_array_equal(sim.get_state(), s)
+        bad = w.rho.copy()
+        bad[1, 2] = -1.0
+        with pytest.raises(pond.PondError) as ei:
+            sim.init_fields(bad, w.ux, w.uy, w.T)
+        assert ei.value.status == 1
