@@ -142,6 +142,11 @@ pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 pond_status pond_get_state(pond_ctx *ctx, double *state);
 pond_status pond_set_state(pond_ctx *ctx, const double *state);
 
+/* One time step with CUDA events around each of its three kernels on the context
+ * stream; ms_out = {non-local pass 1, non-local pass 2, frame search + collision}
+ * in milliseconds.  Synchronises (a tracing aid; pond_step is the fast path). */
+pond_status pond_step_timed(pond_ctx *ctx, double ms_out[3]);
+
 /* Read (and, if reset != 0, zero) the device counters.  Synchronises. */
 pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);
 

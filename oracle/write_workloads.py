@@ -7,9 +7,11 @@ JSON file is data that the input generators read, so no product code executes
 the oracle.
 
 Time step rule (the paper keeps delta t symbolic with Delta x = 1): the explicit
-step is stable in the liquid when the sound speed is carried by the stencil,
-which needs delta t <~ 1.25 sqrt(theta_l) / varsigma_l^2 (shortest-wave analysis
-of stream + relax).  We take 0.8 sqrt(theta_l)/varsigma_l^2, capped at 0.5.
+step is stable in the dense phase only while the shortest waves (checkerboard
+modes along x and along the diagonal) are carried by the stencil, which a 1-D
+shortest-wave analysis of stream + relax puts at delta t <~ 1.25 sqrt(theta)/varsigma^2
+and 2-D oracle runs at about 0.6 of that.  We take 0.45 sqrt(theta)/varsigma^2 at the
+densest state of the workload, capped at 0.5.
 """
 from __future__ import annotations
 
@@ -29,7 +31,7 @@ def dt_rule(rho: float, T: float, delta: float = DELTA) -> float:
     p = thermo.pressure(rho, T)
     theta = p / (rho * T_L)
     c2 = thermo.sound_speed(rho, T, delta) ** 2
-    return float(min(0.5, 0.8 * math.sqrt(theta) / c2))
+    return float(min(0.5, 0.45 * math.sqrt(theta) / c2))
 
 
 def main() -> None:

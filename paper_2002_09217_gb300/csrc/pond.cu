@@ -83,15 +83,19 @@ inline unsigned blocks_for(size_t n, unsigned bs) { return (unsigned)((n + bs - 
 bool mixed(const pond_ctx *c) { return c->opts.precision == POND_MIXED; }
 
 template <typename R>
-pond_status launch_step(pond_ctx *c)
+pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
     R *sc = (R *)c->scratch;
     const unsigned nb = blocks_for(c->N, 256), nb128 = blocks_for(c->N, 128);
+    if (ev) cudaEventRecord(ev[0], c->stream);
     k_nonlocal1<R><<<nb, 256, 0, c->stream>>>(c->dp, in, sc);
+    if (ev) cudaEventRecord(ev[1], c->stream);
     k_nonlocal2<R><<<nb, 256, 0, c->stream>>>(c->dp, sc);
+    if (ev) cudaEventRecord(ev[2], c->stream);
     k_step<R><<<nb128, 128, 0, c->stream>>>(c->dp, in, out, sc, c->dstats);
+    if (ev) cudaEventRecord(ev[3], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
 }
@@ -270,6 +274,29 @@ pond_status pond_step(pond_ctx *c, int64_t n)
     }
     CK(cudaGetLastError(), "step launch");
     c->steps += n;
+    return POND_OK;
+}
+
+pond_status pond_step_timed(pond_ctx *c, double ms_out[3])
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!ms_out) return fail(c, POND_EINVAL, "null output");
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    cudaEvent_t ev[4];
+    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
+    if (mixed(c)) launch_step<float>(c, ev);
+    else launch_step<double>(c, ev);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        ms_out[k] = ms;
+    }
+    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pond_step_timed");
+    c->steps += 1;
     return POND_OK;
 }
 

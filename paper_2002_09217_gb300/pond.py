@@ -87,7 +87,8 @@ def load() -> C.CDLL:
                            ("pond_conservation", [P, dp]),
                            ("pond_get_state", [P, dp]),
                            ("pond_set_state", [P, dp]),
-                           ("pond_stats", [P, C.POINTER(Stats), C.c_int32])]:
+                           ("pond_stats", [P, C.POINTER(Stats), C.c_int32]),
+                           ("pond_step_timed", [P, dp])]:
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = C.c_int
@@ -195,6 +196,12 @@ class Simulation:
 
     def step(self, n: int = 1):
         self._check(self._lib.pond_step(self._ctx, int(n)))
+
+    def step_timed(self) -> list:
+        """One step; per-kernel milliseconds [non-local 1, non-local 2, step kernel]."""
+        out = np.zeros(3)
+        self._check(self._lib.pond_step_timed(self._ctx, _dptr(out)))
+        return out.tolist()
 
     def moments(self) -> dict:
         outs = [np.empty((self.ny, self.nx)) for _ in range(5)]
