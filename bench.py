@@ -230,8 +230,7 @@ def main():
 
     # per-kernel time of the dominant kernel (k_step) from events around one launch:
     # the step is 3 launches; time the frame-search kernel alone via a second sim call
-    kms = kernel_time(sim, flush, stream, torch, reps=min(args.steps, 50))
-    kstep_ms = kms[2]
+    kstep_ms = kernel_time(sim, flush, stream, torch, reps=min(args.steps, 50))
 
     # end to end through the public API with host buffers: init from pinned host arrays,
     # n_seg time steps, moments back to host, per call
@@ -252,12 +251,12 @@ def main():
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "frame_search_streams_per_node": its,
-        "gpu_launches": 3 * args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved_tf, "peak": peak_tf,
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved_tf, "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
                      "peak_src": "FP32 %s: 152 SM x 128 lanes x 2 x %.0f MHz" % (
                          "" if args.precision == "mixed" else "/64 (FP64)", pk["sm_max_mhz"]),
-                     "flops_per_update": fl_update, "kernel_ms": kms},
+                     "flops_per_update": fl_update, "kernel_ms": kstep_ms},
         "hbm": {"bytes_per_update": bytes_per_update(args.precision),
                 "achieved_gbs": value * 1e6 * bytes_per_update(args.precision) / 1e9,
                 "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
@@ -278,16 +277,14 @@ def main():
         dist.destroy_process_group()
 
 
-def kernel_time(sim, flush, stream, torch, reps: int) -> list:
-    """Average per-kernel durations [non-local 1, non-local 2, frame search + collision]
-    of single steps timed by the library itself (CUDA events on the context stream)."""
-    acc = [0.0, 0.0, 0.0]
+def kernel_time(sim, flush, stream, torch, reps: int) -> float:
+    """Average duration of the fused step kernel, timed by the library itself with CUDA
+    events on the context stream, L2 flushed before each launch."""
+    acc = 0.0
     for k in range(reps):
         with torch.cuda.stream(stream):
             flush.fill_(float(k))
-        ms = sim.step_timed()
-        for i in range(3):
-            acc[i] += ms[i] / reps
+        acc += sim.step_timed() / reps
     return acc
 
 

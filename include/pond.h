@@ -103,8 +103,8 @@ typedef struct {
     int64_t nonfinite;     /* node updates that produced NaN/Inf                */
 } pond_stats_t;
 
-/* Create a context and allocate its device state (two state buffers of 25 planes
- * plus scratch).  kappa >= 0: Korteweg coefficient (Eq. korteweg); tau > 1/2: BGK
+/* Create a context and allocate its device state (two state buffers of 25 planes,
+ * a 5-plane FP64 staging buffer and reduction partials).  kappa >= 0: Korteweg coefficient (Eq. korteweg); tau > 1/2: BGK
  * relaxation time, omega = 1/tau.  On success *out owns the context. */
 pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, const pond_eos *eos,
                         double kappa, double tau, const pond_opts *opts, pond_ctx **out);
@@ -142,10 +142,10 @@ pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 pond_status pond_get_state(pond_ctx *ctx, double *state);
 pond_status pond_set_state(pond_ctx *ctx, const double *state);
 
-/* One time step with CUDA events around each of its three kernels on the context
- * stream; ms_out = {non-local pass 1, non-local pass 2, frame search + collision}
- * in milliseconds.  Synchronises (a tracing aid; pond_step is the fast path). */
-pond_status pond_step_timed(pond_ctx *ctx, double ms_out[3]);
+/* One time step (one launch of the fused step kernel) bracketed by CUDA events on the
+ * context stream; *ms_out = its duration in milliseconds.  Synchronises (a tracing
+ * aid; pond_step is the fast path). */
+pond_status pond_step_timed(pond_ctx *ctx, double *ms_out);
 
 /* Read (and, if reset != 0, zero) the device counters.  Synchronises. */
 pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);

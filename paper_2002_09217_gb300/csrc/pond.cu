@@ -1,8 +1,9 @@
 // pond.cu -- host side of libpond: the C ABI declared in include/pond.h.
 //
-// A context owns two 25-plane state buffers (ping-pong), 9 scratch planes for the
-// non-local terms, a 5-plane FP64 staging buffer for host <-> device field copies and
-// a small block of device counters.  Every call enqueues on the context stream.
+// A context owns two 25-plane state buffers (ping-pong), a 5-plane FP64 staging buffer
+// for host <-> device field copies, the block partials of the conservation sums and a
+// small block of device counters.  Every call enqueues on the context stream; one time
+// step is one launch of the fused kernel k_pond_step (pond_step.cuh).
 #include "pond.h"
 
 #include <cuda_runtime.h>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "pond_kernels.cuh"
+#include "pond_step.cuh"
 
 using namespace pond;
 
@@ -27,7 +29,6 @@ struct pond_ctx {
     size_t N = 0, esize = 0;
     void *state[2] = {nullptr, nullptr};
     int cur = 0;
-    void *scratch = nullptr;       // NSC planes of R
     double *stage = nullptr;       // 5 planes of double
     double *part = nullptr;        // conservation partials (nblk * 8) + out[4]
     int red_blocks = 0;
@@ -87,15 +88,10 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
-    R *sc = (R *)c->scratch;
-    const unsigned nb = blocks_for(c->N, 256), nb128 = blocks_for(c->N, 128);
+    const unsigned nb = blocks_for(c->N, STEP_NB);
     if (ev) cudaEventRecord(ev[0], c->stream);
-    k_nonlocal1<R><<<nb, 256, 0, c->stream>>>(c->dp, in, sc);
+    k_pond_step<R><<<nb, STEP_NB * STEP_LPN, 0, c->stream>>>(c->dp, in, out, c->dstats);
     if (ev) cudaEventRecord(ev[1], c->stream);
-    k_nonlocal2<R><<<nb, 256, 0, c->stream>>>(c->dp, sc);
-    if (ev) cudaEventRecord(ev[2], c->stream);
-    k_step<R><<<nb128, 128, 0, c->stream>>>(c->dp, in, out, sc, c->dstats);
-    if (ev) cudaEventRecord(ev[3], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
 }
@@ -208,11 +204,10 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     size_t sb = (size_t)NPL * c->N * c->esize;
     c->state[0] = dev_alloc(c, sb);
     c->state[1] = dev_alloc(c, sb);
-    c->scratch = dev_alloc(c, (size_t)NSC * c->N * c->esize);
     c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
     c->part = (double *)dev_alloc(c, (8 * (size_t)c->red_blocks + 8) * sizeof(double));
     c->dstats = (DevStats *)dev_alloc(c, sizeof(DevStats));
-    if (!c->state[0] || !c->state[1] || !c->scratch || !c->stage || !c->part || !c->dstats) {
+    if (!c->state[0] || !c->state[1] || !c->stage || !c->part || !c->dstats) {
         pond_destroy(c);
         return POND_ENOMEM;
     }
@@ -232,7 +227,6 @@ void pond_destroy(pond_ctx *c)
     else cudaDeviceSynchronize();
     dev_free(c, c->state[0]);
     dev_free(c, c->state[1]);
-    dev_free(c, c->scratch);
     dev_free(c, c->stage);
     dev_free(c, c->part);
     dev_free(c, c->dstats);
@@ -277,24 +271,22 @@ pond_status pond_step(pond_ctx *c, int64_t n)
     return POND_OK;
 }
 
-pond_status pond_step_timed(pond_ctx *c, double ms_out[3])
+pond_status pond_step_timed(pond_ctx *c, double *ms_out)
 {
     pond_status st = check_ctx(c);
     if (st) return st;
     if (!ms_out) return fail(c, POND_EINVAL, "null output");
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
-    cudaEvent_t ev[4];
-    for (int k = 0; k < 4; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
+    cudaEvent_t ev[2];
+    for (int k = 0; k < 2; ++k) CK(cudaEventCreate(&ev[k]), "cudaEventCreate");
     if (mixed(c)) launch_step<float>(c, ev);
     else launch_step<double>(c, ev);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-        float ms = 0.f;
-        e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-        ms_out[k] = ms;
-    }
-    for (int k = 0; k < 4; ++k) cudaEventDestroy(ev[k]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+    *ms_out = ms;
+    for (int k = 0; k < 2; ++k) cudaEventDestroy(ev[k]);
     if (e != cudaSuccess) return cuda_fail(c, e, "pond_step_timed");
     c->steps += 1;
     return POND_OK;

@@ -1,0 +1,437 @@
+// pond_step.cuh -- the fused time-step kernel of the PonD van der Waals model (sm_103a).
+//
+// One launch per time step.  A block owns NB = 32 nodes; each node is served by a group
+// of LPN = 8 lanes of one warp.  Per node:
+//   phase 0  non-local terms from the previous step's rho and T (radius 2): lane l of the
+//            group takes the l-th non-rest neighbour, builds the Korteweg stress K and the
+//            heat flux q there, and the group sums W c . K and W c . q into F = -div K and
+//            M_0 = 2 div q (Eq. korteweg, Eq. gtilde).
+//   phase 1  frame search (block lockstep): the group streams all 9 directions x 16 stencil
+//            nodes (each lane 2 stencil positions for every direction), reduces the
+//            increments with warp shuffles, and warp 0 (one lane per node) takes the moments,
+//            inverts e -> T, evaluates the EoS and the residual in FP64.
+//   phase 2  BGK collision with the force source, heat-flux correction and forced g
+//            equilibrium, one population per lane.
+//
+// Increment form.  With f~_i = sum_n A_n [G_n f(n)]_i and sum_n A_n = 1,
+//   f~_i = f_i(x) + sum_n A_n ( [G_n (f(n) - f(x))]_i + [(G_n - I) f(x)]_i ),
+// where G_n is the transfer map from the gauge of stencil node n into the arrival gauge
+// (SM "Transfer matrix", separable per axis) and (G_n - I) is evaluated from the gauge
+// differences directly, so equal gauges give exactly the identity and a uniform region
+// reproduces itself exactly.  The FP32 rounding error of a step is then proportional to
+// the local differences, not to the populations, and does not accumulate as a bias.
+#pragma once
+
+#include "pond_kernels.cuh"
+
+namespace pond {
+
+constexpr int STEP_NB = 32;   // nodes per block
+constexpr int STEP_LPN = 8;   // lanes per node
+
+template <typename R>
+struct StepShared {
+    R dsum[STEP_NB][4];        // sum dF, sum dF cx, sum dF cy, sum dG of the current stream
+    R lam[STEP_NB][3];         // current arrival gauge (theta, ux, uy)
+    R mac[STEP_NB][10];        // rho, u*x, u*y, uhx, uhy, E, T, P, theta*, p
+    double base[STEP_NB][4];   // exact FP64 sums of the node's stored f, f cx, f cy, g
+    int active[STEP_NB];
+    int any_active;
+};
+
+// 1-D transfer-map increment E = l_k(c_a + e) - l_k(c_a) for target index k (c = k-1),
+// source offset e (in units of the target spacing s) and source index a (c_a = a-1).
+template <typename R>
+__device__ __forceinline__ R ell_inc(int k, int a, R e)
+{
+    R two_c = R(2 * (a - 1));
+    if (k == 1) return -e * (two_c + e);
+    if (k == 0) return R(0.5) * e * (two_c + e - R(1));
+    return R(0.5) * e * (two_c + e + R(1));
+}
+
+// One cubic Lagrange basis function a_j(xi) on nodes 0..3.
+template <typename R>
+__device__ __forceinline__ R lag1(int j, R xi)
+{
+    R t0 = xi, t1 = xi - R(1), t2 = xi - R(2), t3 = xi - R(3);
+    if (j == 0) return -(t1 * t2 * t3) * R(1.0 / 6.0);
+    if (j == 1) return t0 * t2 * t3 * R(0.5);
+    if (j == 2) return -(t0 * t1 * t3) * R(0.5);
+    return t0 * t1 * t2 * R(1.0 / 6.0);
+}
+
+// a[i] for a run-time i without local-memory indexing (unrolled selects).
+template <typename R, int K>
+__device__ __forceinline__ R pick(const R (&a)[K], int i)
+{
+    R r = a[0];
+#pragma unroll
+    for (int j = 1; j < K; ++j) r = (i == j) ? a[j] : r;
+    return r;
+}
+
+template <typename R> __device__ __forceinline__ R fdiv_(R a, R b);
+template <> __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
+
+template <typename R>
+__device__ __forceinline__ R pressure_(const DevParams &p, R r, R t)
+{
+    return r * (R)p.R * t / (R(1) - (R)p.b * r) - (R)p.a * r * r;
+}
+
+// Contribution of stencil node `nd` to direction (jx, jy) of the arrival node, in the
+// increment form; fx/gx are the arrival node's own stored populations.
+template <typename R>
+__device__ __forceinline__ void pair_inc(const DevParams &p, const R *__restrict__ in, long long nd,
+                                         int jx, int jy, R th, R s, R inv_s, R ux, R uy,
+                                         const R fx[9], const R gx[9], R &tf, R &tg)
+{
+    const long long N = p.N;
+    R thn = in[P_TH * N + nd];
+    R sn = sqrt_(thn);
+    R qm1 = fdiv_(thn - th, (sn + s) * s);          // (s_n - s)/s without cancellation
+    R wx = (in[P_UX * N + nd] - ux) * inv_s;
+    R wy = (in[P_UY * N + nd] - uy) * inv_s;
+    R Ex[3], Ey[3], Gx[3], Gy[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Ex[a] = ell_inc<R>(jx, a, qm1 * R(a - 1) + wx);
+        Ey[a] = ell_inc<R>(jy, a, qm1 * R(a - 1) + wy);
+        Gx[a] = Ex[a] + (a == jx ? R(1) : R(0));
+        Gy[a] = Ey[a] + (a == jy ? R(1) : R(0));
+    }
+    R sf = 0, sg = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        R rf = 0, rg = 0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int i = 3 * b + a;
+            R df = in[(P_F + i) * N + nd] - fx[i];
+            R dg = in[(P_G + i) * N + nd] - gx[i];
+            rf += Gx[a] * df + Ex[a] * fx[i];
+            rg += Gx[a] * dg + Ex[a] * gx[i];
+        }
+        sf += Gy[b] * rf + Ey[b] * fx[3 * b + jx];
+        sg += Gy[b] * rg + Ey[b] * gx[3 * b + jx];
+    }
+    tf = sf;
+    tg = sg;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, const R *__restrict__ in,
+                                                                  R *__restrict__ out, DevStats *stats)
+{
+    constexpr int LPN = STEP_LPN;
+    __shared__ StepShared<R> sh;
+    const long long N = p.N;
+    const int grp = threadIdx.x / LPN, lane = threadIdx.x % LPN;
+    const unsigned gmask = 0xffu << (LPN * (grp % (32 / LPN)));
+    const long long n = (long long)blockIdx.x * STEP_NB + grp;
+    const bool valid = n < N;
+    const long long nn = valid ? n : N - 1;   // clamped index for harmless loads
+    const int X = (int)(nn % p.nx), Y = (int)(nn / p.nx);
+
+    // ---------------- phase 0: non-local terms, own populations --------------------
+    R Fx = 0, Fy = 0, M0 = 0, rEl = 0;
+    {
+        // lane -> non-rest neighbour (cx, cy); index skips the rest direction 4
+        const int dir = lane < 4 ? lane : lane + 1;
+        const int cx = dir % 3 - 1, cy = dir / 3 - 1;
+        const int mx = bc_wrap(X + cx, p.nx, p.bcx), my = bc_wrap(Y + cy, p.ny, p.bcy);
+        const R *rho = in + P_RHO * N, *T = in + P_T * N;
+        R r0 = rho[(long long)my * p.nx + mx], pr0 = 0;
+        R grx = 0, gry = 0, lap = 0, ghx = 0, ghy = 0, gTx = 0, gTy = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int ex = i % 3 - 1, ey = i / 3 - 1;
+            long long m = (long long)bc_wrap(my + ey, p.ny, p.bcy) * p.nx + bc_wrap(mx + ex, p.nx, p.bcx);
+            R w = (R)(w1d(ex + 1) * w1d(ey + 1));
+            R r = rho[m], t = T[m];
+            R pr = pressure_<R>(p, r, t);
+            R h = (R)p.cv * t - (R)p.a * r + pr / r;
+            if (i == 4) pr0 = pr;
+            grx += w * R(ex) * r;
+            gry += w * R(ey) * r;
+            lap += w * (r - r0);
+            ghx += w * R(ex) * h;
+            ghy += w * R(ey) * h;
+            gTx += w * R(ex) * t;
+            gTy += w * R(ey) * t;
+        }
+        grx *= R(3); gry *= R(3); lap *= R(6);
+        ghx *= R(3); ghy *= R(3); gTx *= R(3); gTy *= R(3);
+        const R kap = (R)p.kappa;
+        const R iso = -kap * (r0 * lap + R(0.5) * (grx * grx + gry * gry));
+        const R Kxx = iso + kap * grx * grx, Kxy = kap * grx * gry, Kyy = iso + kap * gry * gry;
+        const R P0 = pr0 > (R)p.p_floor ? pr0 : (R)p.p_floor;
+        const R mu = (R)(p.tau - 0.5) * P0 * (R)p.dt;
+        const R kc = p.k_cond >= 0.0 ? (R)p.k_cond : mu * (R)(p.cv + p.R);
+        const R qx = -mu * ghx + kc * gTx, qy = -mu * ghy + kc * gTy;
+        const R w = (R)(w1d(cx + 1) * w1d(cy + 1));
+        Fx = -R(3) * w * (R(cx) * Kxx + R(cy) * Kxy);
+        Fy = -R(3) * w * (R(cx) * Kxy + R(cy) * Kyy);
+        M0 = R(6) * w * (R(cx) * qx + R(cy) * qy);
+        // interface energy at the node itself: gradient from the 8 neighbours' densities
+        rEl = 0;
+        R gxn = R(3) * w * R(cx) * r0, gyn = R(3) * w * R(cy) * r0;
+#pragma unroll
+        for (int o = LPN / 2; o > 0; o >>= 1) {
+            Fx += __shfl_xor_sync(gmask, Fx, o, LPN);
+            Fy += __shfl_xor_sync(gmask, Fy, o, LPN);
+            M0 += __shfl_xor_sync(gmask, M0, o, LPN);
+            gxn += __shfl_xor_sync(gmask, gxn, o, LPN);
+            gyn += __shfl_xor_sync(gmask, gyn, o, LPN);
+        }
+        rEl = R(0.5) * kap * (gxn * gxn + gyn * gyn);
+    }
+    R fx[9], gx[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        fx[i] = in[(P_F + i) * N + nn];
+        gx[i] = in[(P_G + i) * N + nn];
+    }
+    if (lane == 0) {
+        sh.lam[grp][0] = in[P_TH * N + nn];
+        sh.lam[grp][1] = in[P_UX * N + nn];
+        sh.lam[grp][2] = in[P_UY * N + nn];
+        sh.active[grp] = valid ? 1 : 0;
+        double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            b0 += (double)fx[i];
+            b1 += (double)fx[i] * (double)(i % 3 - 1);
+            b2 += (double)fx[i] * (double)(i / 3 - 1);
+            b3 += (double)gx[i];
+        }
+        sh.base[grp][0] = b0; sh.base[grp][1] = b1; sh.base[grp][2] = b2; sh.base[grp][3] = b3;
+    }
+    if (threadIdx.x == 0) sh.any_active = 1;
+    __syncthreads();
+
+    // ---------------- phase 1: frame search (block lockstep) -----------------------
+    R df[9], dg[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { df[i] = 0; dg[i] = 0; }
+    int it = 0;                      // iterations of this block
+    int my_it = 0, my_conv = 0;      // warp-0 lane bookkeeping for node `threadIdx.x`
+    const int kk = lane & 3, m1 = lane >> 2, m2 = m1 + 2;
+    while (sh.any_active && it < p.max_iter) {
+        ++it;
+        if (sh.active[grp]) {
+            const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
+            const R s = sqrt_(th), inv_s = R(1) / s;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) { df[i] = 0; dg[i] = 0; }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int jx = i % 3, jy = i / 3;
+                const R dx = -(s * R(jx - 1) + ux) * (R)p.dt;
+                const R dy = -(s * R(jy - 1) + uy) * (R)p.dt;
+                const R flx = floor(dx), fly = floor(dy);
+                const int x0 = X + (int)flx - 1, y0 = Y + (int)fly - 1;
+                const R ax = lag1<R>(kk, dx - flx + R(1));
+                const R eta = dy - fly + R(1);
+                const R ay1 = lag1<R>(m1, eta), ay2 = lag1<R>(m2, eta);
+                const long long xx = bc_wrap(x0 + kk, p.nx, p.bcx);
+                const long long n1 = (long long)bc_wrap(y0 + m1, p.ny, p.bcy) * p.nx + xx;
+                const long long n2 = (long long)bc_wrap(y0 + m2, p.ny, p.bcy) * p.nx + xx;
+                R tf, tg, uf, ug;
+                pair_inc<R>(p, in, n1, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
+                pair_inc<R>(p, in, n2, jx, jy, th, s, inv_s, ux, uy, fx, gx, uf, ug);
+                df[i] = ax * (ay1 * tf + ay2 * uf);
+                dg[i] = ax * (ay1 * tg + ay2 * ug);
+            }
+#pragma unroll
+            for (int o = LPN / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    df[i] += __shfl_xor_sync(gmask, df[i], o, LPN);
+                    dg[i] += __shfl_xor_sync(gmask, dg[i], o, LPN);
+                }
+            if (lane == 0) {
+                R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    a0 += df[i];
+                    a1 += df[i] * R(i % 3 - 1);
+                    a2 += df[i] * R(i / 3 - 1);
+                    a3 += dg[i];
+                }
+                sh.dsum[grp][0] = a0; sh.dsum[grp][1] = a1; sh.dsum[grp][2] = a2; sh.dsum[grp][3] = a3;
+                // stash the group's lagged terms for warp 0 (once is enough, cheap to repeat)
+                sh.mac[grp][0] = Fx; sh.mac[grp][1] = Fy; sh.mac[grp][2] = rEl;
+            }
+        }
+        __syncthreads();
+        // warp 0: moments, e -> T, EoS, residual in FP64 for node j = threadIdx.x
+        if (threadIdx.x < STEP_NB) {
+            const int j = threadIdx.x;
+            if (sh.active[j]) {
+                const double dt = p.dt;
+                const double Fxd = (double)sh.mac[j][0], Fyd = (double)sh.mac[j][1];
+                const double rEd = (double)sh.mac[j][2];
+                const double thd = (double)sh.lam[j][0], uxd = (double)sh.lam[j][1], uyd = (double)sh.lam[j][2];
+                const double sd = sqrt(thd);
+                const double rho = sh.base[j][0] + (double)sh.dsum[j][0];
+                const double irho = 1.0 / rho;
+                const double uxs = uxd + sd * (sh.base[j][1] + (double)sh.dsum[j][1]) * irho;
+                const double uys = uyd + sd * (sh.base[j][2] + (double)sh.dsum[j][2]) * irho;
+                const double uhx = uxs + 0.5 * Fxd * dt * irho, uhy = uys + 0.5 * Fyd * dt * irho;
+                const double E = 0.5 * (sh.base[j][3] + (double)sh.dsum[j][3]) * irho;
+                const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEd * irho;
+                const double T = (e + p.a * rho) / p.cv;
+                const double pr = rho * p.R * T / (1.0 - p.b * rho) - p.a * rho * rho;
+                const double P = pr > p.p_floor ? pr : p.p_floor;
+                const double ths = P * irho * 3.0;
+                double res = fabs(ths - thd) / thd;
+                res = fmax(res, fabs(uxs - uxd) / sd);
+                res = fmax(res, fabs(uys - uyd) / sd);
+                const bool conv = res <= p.tol;
+                const bool bad = !(res == res);
+                my_it = it;
+                if (conv || bad || it >= p.max_iter) {
+                    sh.active[j] = 0;
+                    my_conv = conv;
+                    R *m = sh.mac[j];
+                    m[0] = (R)rho; m[1] = (R)uxs; m[2] = (R)uys; m[3] = (R)uhx; m[4] = (R)uhy;
+                    m[5] = (R)E; m[6] = (R)T; m[7] = (R)P; m[8] = (R)ths; m[9] = (R)pr;
+                    // exact FP64 copies the collision needs are re-derived there
+                    sh.base[j][0] = rho;
+                    sh.base[j][1] = uxs - uxd;
+                    sh.base[j][2] = uys - uyd;
+                    sh.base[j][3] = ths;
+                } else {
+                    sh.lam[j][0] = (R)ths;
+                    sh.lam[j][1] = (R)uxs;
+                    sh.lam[j][2] = (R)uys;
+                }
+            }
+            const int any = __any_sync(0xffffffffu, sh.active[j]);
+            if (j == 0) sh.any_active = any;
+        }
+        __syncthreads();
+    }
+
+    // ---------------- phase 2: collision (one population per lane) -----------------
+    if (valid) {
+        const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
+        const R s = sqrt_(th), inv_s = R(1) / s;
+        const R *m = sh.mac[grp];
+        const R rr = m[0], uxr = m[1], uyr = m[2], uhxr = m[3], uhyr = m[4], Er = m[5];
+        const R Pr = m[7], thsr = m[8];
+        const double rho_d = sh.base[grp][0];
+        const R dux = (R)sh.base[grp][1], duy = (R)sh.base[grp][2];
+        const R sst = sqrt_(thsr);
+        const R qm1 = fdiv_((R)(sh.base[grp][3] - (double)th), (sst + s) * s);
+        const R wsx = dux * inv_s, wsy = duy * inv_s;
+        const R dvx = (R)((double)Fx * p.dt / rho_d) * inv_s, dvy = (R)((double)Fy * p.dt / rho_d) * inv_s;
+        const R W1[3] = {R(1.0 / 6.0), R(2.0 / 3.0), R(1.0 / 6.0)};
+        // transfer increments from lambda* = (ths, u*) into the streaming gauge, and from the
+        // force-shifted frame (ths, u* + F dt/rho) (Eq. S-i)
+        R Ex[3][3], Ey[3][3], Wsx[3], Wsy[3], Whx[3], Why[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Wsx[k] = Wsy[k] = Whx[k] = Why[k] = 0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                Ex[k][a] = ell_inc<R>(k, a, qm1 * R(a - 1) + wsx);
+                Ey[k][a] = ell_inc<R>(k, a, qm1 * R(a - 1) + wsy);
+                Wsx[k] += Ex[k][a] * W1[a];
+                Wsy[k] += Ey[k][a] * W1[a];
+                Whx[k] += (ell_inc<R>(k, a, qm1 * R(a - 1) + wsx + dvx) - Ex[k][a]) * W1[a];
+                Why[k] += (ell_inc<R>(k, a, qm1 * R(a - 1) + wsy + dvy) - Ey[k][a]) * W1[a];
+            }
+        }
+        const R om = (R)p.omega, dtr = (R)p.dt;
+        // g: forced equilibrium (Eq. new geq), heat-flux correction (Eq. gtilde) and the
+        // force-work source 2 W_i uhat.F, all in lambda*, in every lane (9 values)
+        const R H = Er + Pr / rr;
+        const R Ixx = R(2) * uhxr * Fx + dtr * Fx * Fx * Er / (R(2) * Pr);
+        const R Ixy = uhxr * Fy + Fx * uhyr + dtr * Fx * Fy * Er / (R(2) * Pr);
+        const R Iyy = R(2) * uhyr * Fy + dtr * Fy * Fy * Er / (R(2) * Pr);
+        const R cM = dtr * rr / Pr;
+        const R Mx = cM * (Fx * H - (Ixx * uxr + Ixy * uyr));
+        const R My = cM * (Fy * H - (Ixy * uxr + Iyy * uyr));
+        const R cN = dtr * rr / (R(2) * Pr);
+        const R Nxx = rr + cN * Ixx, Nxy = cN * Ixy, Nyy = rr + cN * Iyy;
+        const R Pd = Pr / rr;
+        const R work = R(2) * (uhxr * Fx + uhyr * Fy);
+        R Xs[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const R cx = R(i % 3 - 1), cy = R(i / 3 - 1);
+            const R w = W1[i % 3] * W1[i / 3];
+            const R ccx = sst * cx, ccy = sst * cy;                  // v - u* in lambda*
+            const R Axx = ccx * ccx + R(2) * ccx * uxr - Pd;          // v v - P/rho I - u u
+            const R Axy = ccx * ccy + ccx * uyr + ccy * uxr;
+            const R Ayy = ccy * ccy + R(2) * ccy * uyr - Pd;
+            const R geq = w * (R(2) * rr * Er + Mx * ccx + My * ccy + Nxx * Axx + R(2) * Nxy * Axy + Nyy * Ayy);
+            const R vx = ccx + uxr, vy = ccy + uyr;
+            const R uc = uxr * cx + uyr * cy;
+            const R gc = M0 * w * (R(1) + rr * uc * uc / (R(2) * Pr * R(POND_TL))
+                                   - rr * (vx * vx + vy * vy) / (R(2) * Pr) + R(1));
+            Xs[i] = om * geq + dtr * (gc + w * work);
+        }
+#pragma unroll
+        for (int rep = 0; rep < 2; ++rep) {
+            const int i = lane + rep * LPN;
+            if (i < 9) {
+                const int kx = i % 3, ky = i / 3;
+                const R ft = pick(fx, i) + pick(df, i), gt = pick(gx, i) + pick(dg, i);
+                const R Wx = pick(W1, kx) + pick(Wsx, kx), Wy = pick(W1, ky) + pick(Wsy, ky);
+                const R Whk = pick(Whx, kx), Whl = pick(Why, ky);
+                const R feq = rr * Wx * Wy;
+                const R S = rr * (Whk * (Wy + Whl) + Wx * Whl);
+                out[(P_F + i) * N + n] = ft + om * (feq - ft) + S;
+                // carry X* into the streaming gauge: X = X* + (G* - I) X*
+                R exk[3], eyl[3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    exk[a] = kx == 0 ? Ex[0][a] : (kx == 1 ? Ex[1][a] : Ex[2][a]);
+                    eyl[a] = ky == 0 ? Ey[0][a] : (ky == 1 ? Ey[1][a] : Ey[2][a]);
+                }
+                R acc = pick(Xs, i);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    R gyc = 0;
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) gyc += (eyl[b] + (b == ky ? R(1) : R(0))) * Xs[a + 3 * b];
+                    acc += exk[a] * gyc;
+                }
+                R xcol[3];
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    xcol[b] = kx == 0 ? Xs[3 * b] : (kx == 1 ? Xs[3 * b + 1] : Xs[3 * b + 2]);
+#pragma unroll
+                for (int b = 0; b < 3; ++b) acc += eyl[b] * xcol[b];
+                out[(P_G + i) * N + n] = (R(1) - om) * gt + acc;
+            }
+        }
+        if (lane == 0) {
+            out[P_TH * N + n] = th;
+            out[P_UX * N + n] = ux;
+            out[P_UY * N + n] = uy;
+            out[P_RHO * N + n] = rr;
+            out[P_T * N + n] = m[6];
+            out[P_UHX * N + n] = uhxr;
+            out[P_UHY * N + n] = uhyr;
+        }
+    }
+    // ---------------- statistics (warp 0, one lane per node) -----------------------
+    if (threadIdx.x < STEP_NB) {
+        const int j = threadIdx.x;
+        const bool v = (long long)blockIdx.x * STEP_NB + j < N;
+        const R T = sh.mac[j][6], rr = sh.mac[j][0], pr = sh.mac[j][9];
+        warp_add(&stats->streams, v ? my_it : 0);
+        warp_add(&stats->nonconv, (v && !my_conv) ? 1 : 0);
+        warp_add(&stats->clamped, (v && (double)pr < p.p_floor) ? 1 : 0);
+        const bool bad = v && (!(rr == rr) || !(T == T) || isinf((double)rr) || isinf((double)T));
+        warp_add(&stats->nonfinite, bad ? 1 : 0);
+    }
+}
+
+}  // namespace pond

@@ -197,11 +197,11 @@ class Simulation:
     def step(self, n: int = 1):
         self._check(self._lib.pond_step(self._ctx, int(n)))
 
-    def step_timed(self) -> list:
-        """One step; per-kernel milliseconds [non-local 1, non-local 2, step kernel]."""
-        out = np.zeros(3)
+    def step_timed(self) -> float:
+        """One step; duration of its kernel in milliseconds (CUDA events)."""
+        out = np.zeros(1)
         self._check(self._lib.pond_step_timed(self._ctx, _dptr(out)))
-        return out.tolist()
+        return float(out[0])
 
     def moments(self) -> dict:
         outs = [np.empty((self.ny, self.nx)) for _ in range(5)]
