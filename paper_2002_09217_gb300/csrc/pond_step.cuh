@@ -35,6 +35,7 @@ struct StepShared {
     R lam[STEP_NB][3];         // current arrival gauge (theta, ux, uy)
     R mac[STEP_NB][10];        // rho, u*x, u*y, uhx, uhy, E, T, P, theta*, p
     double base[STEP_NB][4];   // exact FP64 sums of the node's stored f, f cx, f cy, g
+    double gsum[STEP_NB];      // FP64 sum of the streamed g of the final stream (2 rho E)
     int active[STEP_NB];
     int any_active;
 };
@@ -48,6 +49,20 @@ __device__ __forceinline__ R ell_inc(int k, int a, R e)
     if (k == 1) return -e * (two_c + e);
     if (k == 0) return R(0.5) * e * (two_c + e - R(1));
     return R(0.5) * e * (two_c + e + R(1));
+}
+
+// 1-D lattice weights W_-1, W_0, W_+1 = 1/6, 2/3, 1/6 as values of type R whose sum is
+// exactly one: in FP32 the nearest floats to 1/6 and 2/3 sum to 1 + 3e-8, a bias that every
+// collision would add to the mass and energy; W_+-1 = 1/6 rounded down and W_0 = 1 - 2 W_+-1
+// (both exact floats) sum to one exactly.
+template <typename R> __device__ __forceinline__ R wlat(int a);
+template <> __device__ __forceinline__ float wlat<float>(int a)
+{
+    return a == 1 ? 0x1.555556p-1f : 0x1.555554p-3f;
+}
+template <> __device__ __forceinline__ double wlat<double>(int a)
+{
+    return a == 1 ? 1.0 - 2.0 * (1.0 / 6.0) : 1.0 / 6.0;
 }
 
 // One cubic Lagrange basis function a_j(xi) on nodes 0..3.
@@ -300,6 +315,7 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                     m[0] = (R)rho; m[1] = (R)uxs; m[2] = (R)uys; m[3] = (R)uhx; m[4] = (R)uhy;
                     m[5] = (R)E; m[6] = (R)T; m[7] = (R)P; m[8] = (R)ths; m[9] = (R)pr;
                     // exact FP64 copies the collision needs are re-derived there
+                    sh.gsum[j] = sh.base[j][3] + (double)sh.dsum[j][3];
                     sh.base[j][0] = rho;
                     sh.base[j][1] = uxs - uxd;
                     sh.base[j][2] = uys - uyd;
@@ -329,7 +345,7 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         const R qm1 = fdiv_((R)(sh.base[grp][3] - (double)th), (sst + s) * s);
         const R wsx = dux * inv_s, wsy = duy * inv_s;
         const R dvx = (R)((double)Fx * p.dt / rho_d) * inv_s, dvy = (R)((double)Fy * p.dt / rho_d) * inv_s;
-        const R W1[3] = {R(1.0 / 6.0), R(2.0 / 3.0), R(1.0 / 6.0)};
+        const R W1[3] = {wlat<R>(0), wlat<R>(1), wlat<R>(2)};
         // transfer increments from lambda* = (ths, u*) into the streaming gauge, and from the
         // force-shifted frame (ths, u* + F dt/rho) (Eq. S-i)
         R Ex[3][3], Ey[3][3], Wsx[3], Wsy[3], Whx[3], Why[3];
@@ -358,7 +374,10 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         const R My = cM * (Fy * H - (Ixy * uxr + Iyy * uyr));
         const R cN = dtr * rr / (R(2) * Pr);
         const R Nxx = rr + cN * Ixx, Nxy = cN * Ixy, Nyy = rr + cN * Iyy;
-        const R Pd = Pr / rr;
+        // P/rho in the g equilibrium as sqrt(theta*)^2 times the lattice temperature of
+        // the weights in use (sum_i W_i c_ix^2 = 2 W_+-1), so that the equilibrium's zeroth
+        // moment is 2 rho E to rounding also in FP32 (sum_i W_i (v_x^2 - P/rho - u_x^2) = 0)
+        const R Pd = sst * sst * (R(2) * W1[0]);
         const R work = R(2) * (uhxr * Fx + uhyr * Fy);
         R Xs[9];
 #pragma unroll
@@ -376,6 +395,7 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                                    - rr * (vx * vx + vy * vy) / (R(2) * Pr) + R(1));
             Xs[i] = om * geq + dtr * (gc + w * work);
         }
+        R fo[2] = {R(0), R(0)}, go[2] = {R(0), R(0)};
 #pragma unroll
         for (int rep = 0; rep < 2; ++rep) {
             const int i = lane + rep * LPN;
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                 const R Whk = pick(Whx, kx), Whl = pick(Why, ky);
                 const R feq = rr * Wx * Wy;
                 const R S = rr * (Whk * (Wy + Whl) + Wx * Whl);
-                out[(P_F + i) * N + n] = ft + om * (feq - ft) + S;
+                fo[rep] = ft + om * (feq - ft) + S;
                 // carry X* into the streaming gauge: X = X* + (G* - I) X*
                 R exk[3], eyl[3];
 #pragma unroll
@@ -408,8 +428,31 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                     xcol[b] = kx == 0 ? Xs[3 * b] : (kx == 1 ? Xs[3 * b + 1] : Xs[3 * b + 2]);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) acc += eyl[b] * xcol[b];
-                out[(P_G + i) * N + n] = (R(1) - om) * gt + acc;
+                go[rep] = (R(1) - om) * gt + acc;
             }
+        }
+        // The collision conserves mass exactly and changes the energy by dt (M_0 + 2 uhat.F);
+        // the rest population (i = 4) takes the FP64 remainder so that the stored
+        // populations keep these sums up to one rounding instead of drifting with it.
+        {
+            double sf = (lane != 4 ? (double)fo[0] : 0.0) + (lane == 0 ? (double)fo[1] : 0.0);
+            double sg = (lane != 4 ? (double)go[0] : 0.0) + (lane == 0 ? (double)go[1] : 0.0);
+#pragma unroll
+            for (int o = LPN / 2; o > 0; o >>= 1) {
+                sf += __shfl_xor_sync(gmask, sf, o, LPN);
+                sg += __shfl_xor_sync(gmask, sg, o, LPN);
+            }
+            if (lane == 4) {
+                const double gtot = sh.gsum[grp] + p.dt * ((double)M0 + (double)work);
+                fo[0] = (R)(rho_d - sf);
+                go[0] = (R)(gtot - sg);
+            }
+        }
+        out[(P_F + lane) * N + n] = fo[0];
+        out[(P_G + lane) * N + n] = go[0];
+        if (lane == 0) {
+            out[(P_F + 8) * N + n] = fo[1];
+            out[(P_G + 8) * N + n] = go[1];
         }
         if (lane == 0) {
             out[P_TH * N + n] = th;
