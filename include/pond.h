@@ -101,6 +101,8 @@ typedef struct {
     int64_t nonconverged;  /* node updates whose frame search hit max_iter      */
     int64_t clamped;       /* node updates with p < p_floor                     */
     int64_t nonfinite;     /* node updates that produced NaN/Inf                */
+    int64_t stalled;       /* mixed form: frame searches stopped at the FP32
+                              rounding floor (residual no longer halving)      */
 } pond_stats_t;
 
 /* Create a context and allocate its device state (two state buffers of 25 planes,

@@ -393,6 +393,7 @@ pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
     out->nonconverged = (int64_t)hs.nonconv;
     out->clamped = (int64_t)hs.clamped;
     out->nonfinite = (int64_t)hs.nonfinite;
+    out->stalled = (int64_t)hs.stalled;
     return hs.nonfinite ? fail(c, POND_ENAN, "non-finite values in the state") : POND_OK;
 }
 

@@ -23,7 +23,7 @@ struct DevParams {
 };
 
 struct DevStats {
-    unsigned long long streams, nonconv, clamped, nonfinite, bad_init;
+    unsigned long long streams, nonconv, clamped, nonfinite, bad_init, stalled;
 };
 
 // lattice temperature T_L = 1/3 and 1-D weights W_-1, W_0, W_+1 (SM "Equilibrium")

@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
 #pragma unroll
     for (int i = 0; i < 9; ++i) { df[i] = 0; dg[i] = 0; }
     int it = 0;                      // iterations of this block
-    int my_it = 0, my_conv = 0;      // warp-0 lane bookkeeping for node `threadIdx.x`
+    int my_it = 0, my_conv = 0, my_stall = 0;   // warp-0 lane bookkeeping for node threadIdx.x
+    double my_res = 1e300;                        // previous residual of that node
     const int kk = lane & 3, m1 = lane >> 2, m2 = m1 + 2;
     while (sh.any_active && it < p.max_iter) {
         ++it;
@@ -307,10 +308,16 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                 res = fmax(res, fabs(uys - uyd) / sd);
                 const bool conv = res <= p.tol;
                 const bool bad = !(res == res);
+                // FP32 form only: the streamed moments carry FP32 rounding that the EoS
+                // cancellation inside interfaces can lift above tol; once a corrector no
+                // longer halves the residual the iteration has reached that floor and stops.
+                const bool stall = sizeof(R) == 4 && it >= 2 && !conv && res > 0.5 * my_res;
+                my_res = res;
                 my_it = it;
-                if (conv || bad || it >= p.max_iter) {
+                if (conv || bad || stall || it >= p.max_iter) {
                     sh.active[j] = 0;
-                    my_conv = conv;
+                    my_conv = conv || stall;
+                    my_stall = stall;
                     R *m = sh.mac[j];
                     m[0] = (R)rho; m[1] = (R)uxs; m[2] = (R)uys; m[3] = (R)uhx; m[4] = (R)uhy;
                     m[5] = (R)E; m[6] = (R)T; m[7] = (R)P; m[8] = (R)ths; m[9] = (R)pr;
@@ -471,6 +478,7 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         const R T = sh.mac[j][6], rr = sh.mac[j][0], pr = sh.mac[j][9];
         warp_add(&stats->streams, v ? my_it : 0);
         warp_add(&stats->nonconv, (v && !my_conv) ? 1 : 0);
+        warp_add(&stats->stalled, (v && my_stall) ? 1 : 0);
         warp_add(&stats->clamped, (v && (double)pr < p.p_floor) ? 1 : 0);
         const bool bad = v && (!(rr == rr) || !(T == T) || isinf((double)rr) || isinf((double)T));
         warp_add(&stats->nonfinite, bad ? 1 : 0);

@@ -76,7 +76,7 @@ class Workload:
     R: float = R_GAS
     delta: float = 1.0 / 3.0
     k_cond: float = -1.0
-    p_floor: float = 1e-3 / 6.0
+    p_floor: float = 0.05 / 6.0     # 5 % of p_cr
 
     @property
     def nodes(self) -> int:
