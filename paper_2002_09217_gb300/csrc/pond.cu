@@ -199,6 +199,13 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     d.a = c->eos.a; d.b = c->eos.b; d.R = c->eos.R; d.delta = c->eos.delta; d.cv = c->eos.R / c->eos.delta;
     d.kappa = kappa; d.tau = tau; d.omega = 1.0 / tau; d.dt = opts->dt; d.k_cond = opts->k_cond;
     d.p_floor = opts->p_floor; d.tol = opts->tol; d.max_iter = opts->max_iter;
+    d.pd.a = d.a; d.pd.b = d.b; d.pd.R = d.R; d.pd.cv = d.cv; d.pd.inv_cv = 1.0 / d.cv;
+    d.pd.kappa = d.kappa; d.pd.p_floor = d.p_floor; d.pd.dt = d.dt; d.pd.omega = d.omega;
+    d.pd.mu_coef = (d.tau - 0.5) * d.dt; d.pd.cvR = d.cv + d.R; d.pd.k_cond = d.k_cond;
+    d.pf.a = (float)d.pd.a; d.pf.b = (float)d.pd.b; d.pf.R = (float)d.pd.R; d.pf.cv = (float)d.pd.cv;
+    d.pf.inv_cv = (float)d.pd.inv_cv; d.pf.kappa = (float)d.pd.kappa; d.pf.p_floor = (float)d.pd.p_floor;
+    d.pf.dt = (float)d.pd.dt; d.pf.omega = (float)d.pd.omega; d.pf.mu_coef = (float)d.pd.mu_coef;
+    d.pf.cvR = (float)d.pd.cvR; d.pf.k_cond = (float)d.pd.k_cond;
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
     size_t sb = (size_t)NPL * c->N * c->esize;

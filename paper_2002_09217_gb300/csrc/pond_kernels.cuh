@@ -14,13 +14,29 @@ constexpr int NPL = 25;
 enum : int { P_F = 0, P_G = 9, P_TH = 18, P_UX = 19, P_UY = 20, P_RHO = 21, P_T = 22,
              P_UHX = 23, P_UHY = 24 };
 
+// Model constants in the arithmetic type of a kernel (float copies keep FP64 work out of
+// the FP32 paths).
+template <typename T>
+struct TypedParams {
+    T a, b, R, cv, inv_cv, kappa, p_floor, dt, omega;
+    T mu_coef;   // (tau - 1/2) dt, so that mu = mu_coef * P
+    T cvR;       // C_v + R (default conductivity k = mu (C_v + R))
+    T k_cond;    // >= 0: fixed conductivity
+};
+
 struct DevParams {
     int nx, ny, bcx, bcy;
     long long N;
     double a, b, R, delta, cv;
     double kappa, tau, omega, dt, k_cond, p_floor, tol;
     int max_iter;
+    TypedParams<float> pf;
+    TypedParams<double> pd;
 };
+
+template <typename R> __device__ __forceinline__ const TypedParams<R> &typed(const DevParams &p);
+template <> __device__ __forceinline__ const TypedParams<float> &typed<float>(const DevParams &p) { return p.pf; }
+template <> __device__ __forceinline__ const TypedParams<double> &typed<double>(const DevParams &p) { return p.pd; }
 
 struct DevStats {
     unsigned long long streams, nonconv, clamped, nonfinite, bad_init, stalled;

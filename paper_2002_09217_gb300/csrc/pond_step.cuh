@@ -8,8 +8,9 @@
 //            M_0 = 2 div q (Eq. korteweg, Eq. gtilde).
 //   phase 1  frame search (block lockstep): the group streams all 9 directions x 16 stencil
 //            nodes (each lane 2 stencil positions for every direction), reduces the
-//            increments with warp shuffles, and warp 0 (one lane per node) takes the moments,
-//            inverts e -> T, evaluates the EoS and the residual in FP64.
+//            increments with warp shuffles, and warp 0 (one lane per node, 32 nodes per
+//            instruction) takes the moments, inverts e -> T, evaluates the EoS and the
+//            residual in FP64.
 //   phase 2  BGK collision with the force source, heat-flux correction and forced g
 //            equilibrium, one population per lane.
 //
@@ -33,9 +34,11 @@ template <typename R>
 struct StepShared {
     R dsum[STEP_NB][4];        // sum dF, sum dF cx, sum dF cy, sum dG of the current stream
     R lam[STEP_NB][3];         // current arrival gauge (theta, ux, uy)
+    R nl[STEP_NB][3];          // lagged F_x, F_y, rho E_lambda of the node
     R mac[STEP_NB][10];        // rho, u*x, u*y, uhx, uhy, E, T, P, theta*, p
+    R dlam[STEP_NB][3];        // theta* - theta, u*x - ux, u*y - uy (from FP64)
+    R hilo[STEP_NB][4];        // rho and sum g~ as (hi, lo) pairs of R
     double base[STEP_NB][4];   // exact FP64 sums of the node's stored f, f cx, f cy, g
-    double gsum[STEP_NB];      // FP64 sum of the streamed g of the final stream (2 rho E)
     int active[STEP_NB];
     int any_active;
 };
@@ -65,7 +68,14 @@ template <> __device__ __forceinline__ double wlat<double>(int a)
     return a == 1 ? 1.0 - 2.0 * (1.0 / 6.0) : 1.0 / 6.0;
 }
 
-// One cubic Lagrange basis function a_j(xi) on nodes 0..3.
+// Stencil weight W_i of the isotropic D2Q9 difference operators, as a constant of type R.
+template <typename R>
+__device__ __forceinline__ R wst(int ex, int ey)
+{
+    return (ex == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0)) * (ey == 0 ? R(2.0 / 3.0) : R(1.0 / 6.0));
+}
+
+// One cubic Lagrange basis function a_j(xi) on nodes 0..3 (SM "Reconstruction").
 template <typename R>
 __device__ __forceinline__ R lag1(int j, R xi)
 {
@@ -90,10 +100,22 @@ template <typename R> __device__ __forceinline__ R fdiv_(R a, R b);
 template <> __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
 template <> __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
 
-template <typename R>
-__device__ __forceinline__ R pressure_(const DevParams &p, R r, R t)
+// 1/x in FP64 from the FP32 reciprocal and two Newton steps (relative error ~1e-28
+// before the final rounding), for the frame-search EoS in warp 0.
+__device__ __forceinline__ double rcp_d(double x)
 {
-    return r * (R)p.R * t / (R(1) - (R)p.b * r) - (R)p.a * r * r;
+    double r = (double)__frcp_rn((float)x);
+    r = r * (2.0 - x * r);
+    return r * (2.0 - x * r);
+}
+
+// Error-free sum of two values of type R (Knuth TwoSum).
+template <typename R>
+__device__ __forceinline__ void two_sum_(R a, R b, R &s, R &e)
+{
+    s = a + b;
+    R bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
 }
 
 // Contribution of stencil node `nd` to direction (jx, jy) of the arrival node, in the
@@ -142,6 +164,7 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
 {
     constexpr int LPN = STEP_LPN;
     __shared__ StepShared<R> sh;
+    const TypedParams<R> &q = typed<R>(p);
     const long long N = p.N;
     const int grp = threadIdx.x / LPN, lane = threadIdx.x % LPN;
     const unsigned gmask = 0xffu << (LPN * (grp % (32 / LPN)));
@@ -153,46 +176,56 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
     // ---------------- phase 0: non-local terms, own populations --------------------
     R Fx = 0, Fy = 0, M0 = 0, rEl = 0;
     {
-        // lane -> non-rest neighbour (cx, cy); index skips the rest direction 4
+        // lane -> non-rest neighbour (cx, cy); index skips the rest direction 4, so the
+        // opposite neighbour (-cx, -cy) sits on lane 7 - l
         const int dir = lane < 4 ? lane : lane + 1;
         const int cx = dir % 3 - 1, cy = dir / 3 - 1;
         const int mx = bc_wrap(X + cx, p.nx, p.bcx), my = bc_wrap(Y + cy, p.ny, p.bcy);
         const R *rho = in + P_RHO * N, *T = in + P_T * N;
-        R r0 = rho[(long long)my * p.nx + mx], pr0 = 0;
+        const R r0 = rho[(long long)my * p.nx + mx], t0 = T[(long long)my * p.nx + mx];
+        const R pr0 = r0 * q.R * t0 / (R(1) - q.b * r0) - q.a * r0 * r0;
+        // gradients from differences to the centre value (sum_i W_i c_i = 0), which keeps
+        // their FP32 rounding proportional to the differences
         R grx = 0, gry = 0, lap = 0, ghx = 0, ghy = 0, gTx = 0, gTy = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const int ex = i % 3 - 1, ey = i / 3 - 1;
+            if (ex == 0 && ey == 0) continue;
             long long m = (long long)bc_wrap(my + ey, p.ny, p.bcy) * p.nx + bc_wrap(mx + ex, p.nx, p.bcx);
-            R w = (R)(w1d(ex + 1) * w1d(ey + 1));
-            R r = rho[m], t = T[m];
-            R pr = pressure_<R>(p, r, t);
-            R h = (R)p.cv * t - (R)p.a * r + pr / r;
-            if (i == 4) pr0 = pr;
-            grx += w * R(ex) * r;
-            gry += w * R(ey) * r;
-            lap += w * (r - r0);
-            ghx += w * R(ex) * h;
-            ghy += w * R(ey) * h;
-            gTx += w * R(ex) * t;
-            gTy += w * R(ey) * t;
+            const R w = wst<R>(ex, ey);
+            const R r = rho[m], t = T[m];
+            const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
+            const R dr = r - r0, dT = t - t0;
+            const R dh = q.cv * dT - q.a * dr + (pr / r - pr0 / r0);
+            grx += w * R(ex) * dr;
+            gry += w * R(ey) * dr;
+            lap += w * dr;
+            ghx += w * R(ex) * dh;
+            ghy += w * R(ey) * dh;
+            gTx += w * R(ex) * dT;
+            gTy += w * R(ey) * dT;
         }
         grx *= R(3); gry *= R(3); lap *= R(6);
         ghx *= R(3); ghy *= R(3); gTx *= R(3); gTy *= R(3);
-        const R kap = (R)p.kappa;
+        const R kap = q.kappa;
         const R iso = -kap * (r0 * lap + R(0.5) * (grx * grx + gry * gry));
         const R Kxx = iso + kap * grx * grx, Kxy = kap * grx * gry, Kyy = iso + kap * gry * gry;
-        const R P0 = pr0 > (R)p.p_floor ? pr0 : (R)p.p_floor;
-        const R mu = (R)(p.tau - 0.5) * P0 * (R)p.dt;
-        const R kc = p.k_cond >= 0.0 ? (R)p.k_cond : mu * (R)(p.cv + p.R);
+        const R P0 = pr0 > q.p_floor ? pr0 : q.p_floor;
+        const R mu = q.mu_coef * P0;
+        const R kc = q.k_cond >= R(0) ? q.k_cond : mu * q.cvR;
         const R qx = -mu * ghx + kc * gTx, qy = -mu * ghy + kc * gTy;
-        const R w = (R)(w1d(cx + 1) * w1d(cy + 1));
-        Fx = -R(3) * w * (R(cx) * Kxx + R(cy) * Kxy);
-        Fy = -R(3) * w * (R(cx) * Kxy + R(cy) * Kyy);
-        M0 = R(6) * w * (R(cx) * qx + R(cy) * qy);
-        // interface energy at the node itself: gradient from the 8 neighbours' densities
-        rEl = 0;
-        R gxn = R(3) * w * R(cx) * r0, gyn = R(3) * w * R(cy) * r0;
+        const R w = wst<R>(cx, cy);
+        // divergences from the difference to the opposite neighbour (lane 7 - l); each
+        // opposite pair is counted by both of its lanes, hence the halved factors
+        const int opp = 7 - lane;
+        const R Kxx_o = __shfl_sync(gmask, Kxx, opp, LPN), Kxy_o = __shfl_sync(gmask, Kxy, opp, LPN);
+        const R Kyy_o = __shfl_sync(gmask, Kyy, opp, LPN);
+        const R qx_o = __shfl_sync(gmask, qx, opp, LPN), qy_o = __shfl_sync(gmask, qy, opp, LPN);
+        const R r_o = __shfl_sync(gmask, r0, opp, LPN);
+        Fx = -R(1.5) * w * (R(cx) * (Kxx - Kxx_o) + R(cy) * (Kxy - Kxy_o));
+        Fy = -R(1.5) * w * (R(cx) * (Kxy - Kxy_o) + R(cy) * (Kyy - Kyy_o));
+        M0 = R(3) * w * (R(cx) * (qx - qx_o) + R(cy) * (qy - qy_o));
+        R gxn = R(1.5) * w * R(cx) * (r0 - r_o), gyn = R(1.5) * w * R(cy) * (r0 - r_o);
 #pragma unroll
         for (int o = LPN / 2; o > 0; o >>= 1) {
             Fx += __shfl_xor_sync(gmask, Fx, o, LPN);
@@ -213,16 +246,27 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         sh.lam[grp][0] = in[P_TH * N + nn];
         sh.lam[grp][1] = in[P_UX * N + nn];
         sh.lam[grp][2] = in[P_UY * N + nn];
+        sh.nl[grp][0] = Fx;
+        sh.nl[grp][1] = Fy;
+        sh.nl[grp][2] = rEl;
         sh.active[grp] = valid ? 1 : 0;
+    }
+    if (threadIdx.x < STEP_NB) {
+        // exact FP64 sums of node j's stored populations, one node per lane of warp 0
+        const long long nj = min((long long)blockIdx.x * STEP_NB + threadIdx.x, N - 1);
         double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            b0 += (double)fx[i];
-            b1 += (double)fx[i] * (double)(i % 3 - 1);
-            b2 += (double)fx[i] * (double)(i / 3 - 1);
-            b3 += (double)gx[i];
+            const double f = (double)in[(P_F + i) * N + nj];
+            b0 += f;
+            if (i % 3 == 0) b1 -= f;
+            if (i % 3 == 2) b1 += f;
+            if (i / 3 == 0) b2 -= f;
+            if (i / 3 == 2) b2 += f;
+            b3 += (double)in[(P_G + i) * N + nj];
         }
-        sh.base[grp][0] = b0; sh.base[grp][1] = b1; sh.base[grp][2] = b2; sh.base[grp][3] = b3;
+        sh.base[threadIdx.x][0] = b0; sh.base[threadIdx.x][1] = b1;
+        sh.base[threadIdx.x][2] = b2; sh.base[threadIdx.x][3] = b3;
     }
     if (threadIdx.x == 0) sh.any_active = 1;
     __syncthreads();
@@ -231,8 +275,8 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
     R df[9], dg[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) { df[i] = 0; dg[i] = 0; }
-    int it = 0;                      // iterations of this block
-    int my_it = 0, my_conv = 0, my_stall = 0;   // warp-0 lane bookkeeping for node threadIdx.x
+    int it = 0;                                   // iterations of this block
+    int my_it = 0, my_conv = 0, my_stall = 0;     // warp-0 lane bookkeeping for node threadIdx.x
     double my_res = 1e300;                        // previous residual of that node
     const int kk = lane & 3, m1 = lane >> 2, m2 = m1 + 2;
     while (sh.any_active && it < p.max_iter) {
@@ -241,12 +285,10 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
             const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
             const R s = sqrt_(th), inv_s = R(1) / s;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) { df[i] = 0; dg[i] = 0; }
-#pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int jx = i % 3, jy = i / 3;
-                const R dx = -(s * R(jx - 1) + ux) * (R)p.dt;
-                const R dy = -(s * R(jy - 1) + uy) * (R)p.dt;
+                const R dx = -(s * R(jx - 1) + ux) * q.dt;
+                const R dy = -(s * R(jy - 1) + uy) * q.dt;
                 const R flx = floor(dx), fly = floor(dy);
                 const int x0 = X + (int)flx - 1, y0 = Y + (int)fly - 1;
                 const R ax = lag1<R>(kk, dx - flx + R(1));
@@ -278,8 +320,6 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                     a3 += dg[i];
                 }
                 sh.dsum[grp][0] = a0; sh.dsum[grp][1] = a1; sh.dsum[grp][2] = a2; sh.dsum[grp][3] = a3;
-                // stash the group's lagged terms for warp 0 (once is enough, cheap to repeat)
-                sh.mac[grp][0] = Fx; sh.mac[grp][1] = Fy; sh.mac[grp][2] = rEl;
             }
         }
         __syncthreads();
@@ -288,24 +328,30 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
             const int j = threadIdx.x;
             if (sh.active[j]) {
                 const double dt = p.dt;
-                const double Fxd = (double)sh.mac[j][0], Fyd = (double)sh.mac[j][1];
-                const double rEd = (double)sh.mac[j][2];
-                const double thd = (double)sh.lam[j][0], uxd = (double)sh.lam[j][1], uyd = (double)sh.lam[j][2];
-                const double sd = sqrt(thd);
+                const double Fxd = (double)sh.nl[j][0], Fyd = (double)sh.nl[j][1];
+                const double rEd = (double)sh.nl[j][2];
+                const R thr = sh.lam[j][0];
+                const double thd = (double)thr, uxd = (double)sh.lam[j][1], uyd = (double)sh.lam[j][2];
+                const R sr = sqrt_(thr);
+                const double sd = (double)sr;
                 const double rho = sh.base[j][0] + (double)sh.dsum[j][0];
-                const double irho = 1.0 / rho;
-                const double uxs = uxd + sd * (sh.base[j][1] + (double)sh.dsum[j][1]) * irho;
-                const double uys = uyd + sd * (sh.base[j][2] + (double)sh.dsum[j][2]) * irho;
+                const double irho = rcp_d(rho);
+                const double dux = sd * (sh.base[j][1] + (double)sh.dsum[j][1]) * irho;
+                const double duy = sd * (sh.base[j][2] + (double)sh.dsum[j][2]) * irho;
+                const double uxs = uxd + dux, uys = uyd + duy;
                 const double uhx = uxs + 0.5 * Fxd * dt * irho, uhy = uys + 0.5 * Fyd * dt * irho;
-                const double E = 0.5 * (sh.base[j][3] + (double)sh.dsum[j][3]) * irho;
+                const double gs = sh.base[j][3] + (double)sh.dsum[j][3];
+                const double E = 0.5 * gs * irho;
                 const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEd * irho;
-                const double T = (e + p.a * rho) / p.cv;
-                const double pr = rho * p.R * T / (1.0 - p.b * rho) - p.a * rho * rho;
+                const double T = (e + p.a * rho) * p.pd.inv_cv;
+                const double pr = rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho;
                 const double P = pr > p.p_floor ? pr : p.p_floor;
                 const double ths = P * irho * 3.0;
-                double res = fabs(ths - thd) / thd;
-                res = fmax(res, fabs(uxs - uxd) / sd);
-                res = fmax(res, fabs(uys - uyd) / sd);
+                const double dth = ths - thd;
+                // relative change of the gauge (FP64 differences, FP32 scaling suffices)
+                const float rth = (float)fabs(dth) / (float)thr;
+                const float rux = (float)fabs(dux) / (float)sr, ruy = (float)fabs(duy) / (float)sr;
+                const double res = (double)fmaxf(rth, fmaxf(rux, ruy));
                 const bool conv = res <= p.tol;
                 const bool bad = !(res == res);
                 // FP32 form only: the streamed moments carry FP32 rounding that the EoS
@@ -321,12 +367,10 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                     R *m = sh.mac[j];
                     m[0] = (R)rho; m[1] = (R)uxs; m[2] = (R)uys; m[3] = (R)uhx; m[4] = (R)uhy;
                     m[5] = (R)E; m[6] = (R)T; m[7] = (R)P; m[8] = (R)ths; m[9] = (R)pr;
-                    // exact FP64 copies the collision needs are re-derived there
-                    sh.gsum[j] = sh.base[j][3] + (double)sh.dsum[j][3];
-                    sh.base[j][0] = rho;
-                    sh.base[j][1] = uxs - uxd;
-                    sh.base[j][2] = uys - uyd;
-                    sh.base[j][3] = ths;
+                    sh.dlam[j][0] = (R)dth; sh.dlam[j][1] = (R)dux; sh.dlam[j][2] = (R)duy;
+                    const R rh = (R)rho, gh = (R)gs;
+                    sh.hilo[j][0] = rh; sh.hilo[j][1] = (R)(rho - (double)rh);
+                    sh.hilo[j][2] = gh; sh.hilo[j][3] = (R)(gs - (double)gh);
                 } else {
                     sh.lam[j][0] = (R)ths;
                     sh.lam[j][1] = (R)uxs;
@@ -346,12 +390,11 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         const R *m = sh.mac[grp];
         const R rr = m[0], uxr = m[1], uyr = m[2], uhxr = m[3], uhyr = m[4], Er = m[5];
         const R Pr = m[7], thsr = m[8];
-        const double rho_d = sh.base[grp][0];
-        const R dux = (R)sh.base[grp][1], duy = (R)sh.base[grp][2];
         const R sst = sqrt_(thsr);
-        const R qm1 = fdiv_((R)(sh.base[grp][3] - (double)th), (sst + s) * s);
-        const R wsx = dux * inv_s, wsy = duy * inv_s;
-        const R dvx = (R)((double)Fx * p.dt / rho_d) * inv_s, dvy = (R)((double)Fy * p.dt / rho_d) * inv_s;
+        const R qm1 = fdiv_(sh.dlam[grp][0], (sst + s) * s);
+        const R wsx = sh.dlam[grp][1] * inv_s, wsy = sh.dlam[grp][2] * inv_s;
+        const R dtr = q.dt, om = q.omega;
+        const R dvx = Fx * dtr / rr * inv_s, dvy = Fy * dtr / rr * inv_s;
         const R W1[3] = {wlat<R>(0), wlat<R>(1), wlat<R>(2)};
         // transfer increments from lambda* = (ths, u*) into the streaming gauge, and from the
         // force-shifted frame (ths, u* + F dt/rho) (Eq. S-i)
@@ -369,7 +412,6 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                 Why[k] += (ell_inc<R>(k, a, qm1 * R(a - 1) + wsy + dvy) - Ey[k][a]) * W1[a];
             }
         }
-        const R om = (R)p.omega, dtr = (R)p.dt;
         // g: forced equilibrium (Eq. new geq), heat-flux correction (Eq. gtilde) and the
         // force-work source 2 W_i uhat.F, all in lambda*, in every lane (9 values)
         const R H = Er + Pr / rr;
@@ -439,20 +481,30 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
             }
         }
         // The collision conserves mass exactly and changes the energy by dt (M_0 + 2 uhat.F);
-        // the rest population (i = 4) takes the FP64 remainder so that the stored
-        // populations keep these sums up to one rounding instead of drifting with it.
+        // the rest population (i = 4) takes the remainder, summed error-free as (hi, lo)
+        // pairs, so that the stored populations keep these sums up to one rounding.
         {
-            double sf = (lane != 4 ? (double)fo[0] : 0.0) + (lane == 0 ? (double)fo[1] : 0.0);
-            double sg = (lane != 4 ? (double)go[0] : 0.0) + (lane == 0 ? (double)go[1] : 0.0);
+            R fh = (lane != 4 ? fo[0] : R(0)), fl = (lane == 0 ? fo[1] : R(0));
+            R gh = (lane != 4 ? go[0] : R(0)), gl = (lane == 0 ? go[1] : R(0));
+            two_sum_(fh, fl, fh, fl);
+            two_sum_(gh, gl, gh, gl);
 #pragma unroll
             for (int o = LPN / 2; o > 0; o >>= 1) {
-                sf += __shfl_xor_sync(gmask, sf, o, LPN);
-                sg += __shfl_xor_sync(gmask, sg, o, LPN);
+                const R fh2 = __shfl_xor_sync(gmask, fh, o, LPN), fl2 = __shfl_xor_sync(gmask, fl, o, LPN);
+                const R gh2 = __shfl_xor_sync(gmask, gh, o, LPN), gl2 = __shfl_xor_sync(gmask, gl, o, LPN);
+                R e;
+                two_sum_(fh, fh2, fh, e);
+                fl = fl + fl2 + e;
+                two_sum_(gh, gh2, gh, e);
+                gl = gl + gl2 + e;
             }
             if (lane == 4) {
-                const double gtot = sh.gsum[grp] + p.dt * ((double)M0 + (double)work);
-                fo[0] = (R)(rho_d - sf);
-                go[0] = (R)(gtot - sg);
+                // target sums: rho (hi, lo) and sum g~ + dt (M_0 + work)
+                R th_, tl_;
+                two_sum_(sh.hilo[grp][2], dtr * (M0 + work), th_, tl_);
+                tl_ += sh.hilo[grp][3];
+                fo[0] = (sh.hilo[grp][0] - fh) + (sh.hilo[grp][1] - fl);
+                go[0] = (th_ - gh) + (tl_ - gl);
             }
         }
         out[(P_F + lane) * N + n] = fo[0];
@@ -460,8 +512,6 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         if (lane == 0) {
             out[(P_F + 8) * N + n] = fo[1];
             out[(P_G + 8) * N + n] = go[1];
-        }
-        if (lane == 0) {
             out[P_TH * N + n] = th;
             out[P_UX * N + n] = ux;
             out[P_UY * N + n] = uy;
@@ -479,8 +529,8 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         warp_add(&stats->streams, v ? my_it : 0);
         warp_add(&stats->nonconv, (v && !my_conv) ? 1 : 0);
         warp_add(&stats->stalled, (v && my_stall) ? 1 : 0);
-        warp_add(&stats->clamped, (v && (double)pr < p.p_floor) ? 1 : 0);
-        const bool bad = v && (!(rr == rr) || !(T == T) || isinf((double)rr) || isinf((double)T));
+        warp_add(&stats->clamped, (v && pr < q.p_floor) ? 1 : 0);
+        const bool bad = v && (!(rr == rr) || !(T == T) || isinf(rr) || isinf(T));
         warp_add(&stats->nonfinite, bad ? 1 : 0);
     }
 }
