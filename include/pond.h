@@ -79,7 +79,9 @@ typedef struct { int32_t kind; double a, b, R, delta; } pond_eos;
  * k_cond: conductivity; < 0 selects k = mu (C_v + R), mu = (tau - 1/2) P dt.
  * p_floor: pressure floor of the gauge temperature theta = max(p, p_floor)/(rho T_L).
  * stream: a cudaStream_t (NULL = default stream).
- * dalloc/dfree/alloc_ctx: optional device allocator (both or neither). */
+ * dalloc/dfree/alloc_ctx: optional device allocator (both or neither).
+ * lanes_per_node: threads cooperating on one node in the step kernel, 8 or 16
+ * (0 = choose from the grid size); a performance knob, results are the same to rounding. */
 typedef struct {
     int32_t precision;
     int32_t max_iter;
@@ -91,6 +93,8 @@ typedef struct {
     void *(*dalloc)(size_t bytes, void *alloc_ctx);
     void (*dfree)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
+    int32_t lanes_per_node;
+    int32_t reserved;
 } pond_opts;
 
 /* Device counters accumulated since the last pond_stats() call that reset them. */

@@ -35,6 +35,7 @@ struct pond_ctx {
     DevStats *dstats = nullptr;
     cudaStream_t stream = nullptr;
     int64_t steps = 0;
+    int lanes = 8;                 // lanes per node of the step kernel (8 or 16)
     bool initialised = false;
     std::string err;
     size_t bytes = 0;
@@ -90,7 +91,8 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
     R *out = (R *)c->state[1 - c->cur];
     const unsigned nb = blocks_for(c->N, STEP_NB);
     if (ev) cudaEventRecord(ev[0], c->stream);
-    k_pond_step<R><<<nb, STEP_NB * STEP_LPN, 0, c->stream>>>(c->dp, in, out, c->dstats);
+    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, 0, c->stream>>>(c->dp, in, out, c->dstats);
+    else k_pond_step<R, 8><<<nb, STEP_NB * 8, 0, c->stream>>>(c->dp, in, out, c->dstats);
     if (ev) cudaEventRecord(ev[1], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
@@ -175,6 +177,8 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     if (!(opts->tol > 0.0) || opts->max_iter < 1 || opts->max_iter > 1000) return POND_EINVAL;
     if (!(opts->p_floor > 0.0)) return POND_EINVAL;
     if ((opts->dalloc == nullptr) != (opts->dfree == nullptr)) return POND_EINVAL;
+    if (opts->lanes_per_node != 0 && opts->lanes_per_node != 8 && opts->lanes_per_node != 16)
+        return POND_EINVAL;
 
     pond_ctx *c = new pond_ctx();
     c->grid = *grid;
@@ -186,6 +190,10 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     c->stream = (cudaStream_t)opts->stream;
     c->N = (size_t)grid->nx * (size_t)grid->ny;
     c->esize = opts->precision == POND_MIXED ? sizeof(float) : sizeof(double);
+    // 16 lanes per node while 8 would leave the GPU under-filled (fewer than ~300k
+    // threads in flight); the caller may fix it (autotuning).
+    c->lanes = opts->lanes_per_node ? opts->lanes_per_node
+                                    : (opts->precision == POND_MIXED && c->N * 8 < 300000 ? 16 : 8);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
         std::string m = std::string("no usable CUDA device: ") + cudaGetErrorString(e);

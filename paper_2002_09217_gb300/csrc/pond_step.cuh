@@ -1,14 +1,14 @@
 // pond_step.cuh -- the fused time-step kernel of the PonD van der Waals model (sm_103a).
 //
 // One launch per time step.  A block owns NB = 32 nodes; each node is served by a group
-// of LPN = 8 lanes of one warp.  Per node:
+// of LPN = 8 or 16 lanes of one warp.  Per node:
 //   phase 0  non-local terms from the previous step's rho and T (radius 2): lane l of the
 //            group takes the l-th non-rest neighbour, builds the Korteweg stress K and the
 //            heat flux q there, and the group sums W c . K and W c . q into F = -div K and
 //            M_0 = 2 div q (Eq. korteweg, Eq. gtilde).
 //   phase 1  frame search (block lockstep): the group streams all 9 directions x 16 stencil
-//            nodes (each lane 2 stencil positions for every direction), reduces the
-//            increments with warp shuffles, and warp 0 (one lane per node, 32 nodes per
+//            nodes (each lane 16/LPN stencil positions of every direction), reduces each
+//            direction's increment with warp shuffles, and warp 0 (one lane per node, 32 nodes per
 //            instruction) takes the moments, inverts e -> T, evaluates the EoS and the
 //            residual in FP64.
 //   phase 2  BGK collision with the force source, heat-flux correction and forced g
@@ -27,8 +27,9 @@
 
 namespace pond {
 
-constexpr int STEP_NB = 32;   // nodes per block
-constexpr int STEP_LPN = 8;   // lanes per node
+constexpr int STEP_NB = 32;   // nodes per block (lanes per node LPN = 8 or 16 is a template
+                              // parameter: more lanes per node for grids too small to fill
+                              // the GPU with 8)
 
 template <typename R>
 struct StepShared {
@@ -151,23 +152,26 @@ __device__ __forceinline__ void pair_inc(const DevParams &p, const R *__restrict
             rf += Gx[a] * df + Ex[a] * fx[i];
             rg += Gx[a] * dg + Ex[a] * gx[i];
         }
-        sf += Gy[b] * rf + Ey[b] * fx[3 * b + jx];
-        sg += Gy[b] * rg + Ey[b] * gx[3 * b + jx];
+        const R fxj = jx == 0 ? fx[3 * b] : (jx == 1 ? fx[3 * b + 1] : fx[3 * b + 2]);
+        const R gxj = jx == 0 ? gx[3 * b] : (jx == 1 ? gx[3 * b + 1] : gx[3 * b + 2]);
+        sf += Gy[b] * rf + Ey[b] * fxj;
+        sg += Gy[b] * rg + Ey[b] * gxj;
     }
     tf = sf;
     tg = sg;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, const R *__restrict__ in,
-                                                                  R *__restrict__ out, DevStats *stats)
+template <typename R, int LPN>
+__global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R *__restrict__ in,
+                                                             R *__restrict__ out, DevStats *stats)
 {
-    constexpr int LPN = STEP_LPN;
+    static_assert(LPN == 8 || LPN == 16, "8 or 16 lanes per node");
+    constexpr int PPL = 16 / LPN;   // stencil positions per lane and direction
     __shared__ StepShared<R> sh;
     const TypedParams<R> &q = typed<R>(p);
     const long long N = p.N;
     const int grp = threadIdx.x / LPN, lane = threadIdx.x % LPN;
-    const unsigned gmask = 0xffu << (LPN * (grp % (32 / LPN)));
+    const unsigned gmask = (LPN == 8 ? 0xffu : 0xffffu) << (LPN * (grp % (32 / LPN)));
     const long long n = (long long)blockIdx.x * STEP_NB + grp;
     const bool valid = n < N;
     const long long nn = valid ? n : N - 1;   // clamped index for harmless loads
@@ -178,7 +182,8 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
     {
         // lane -> non-rest neighbour (cx, cy); index skips the rest direction 4, so the
         // opposite neighbour (-cx, -cy) sits on lane 7 - l
-        const int dir = lane < 4 ? lane : lane + 1;
+        const int l8 = lane & 7;
+        const int dir = l8 < 4 ? l8 : l8 + 1;
         const int cx = dir % 3 - 1, cy = dir / 3 - 1;
         const int mx = bc_wrap(X + cx, p.nx, p.bcx), my = bc_wrap(Y + cy, p.ny, p.bcy);
         const R *rho = in + P_RHO * N, *T = in + P_T * N;
@@ -214,10 +219,10 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         const R mu = q.mu_coef * P0;
         const R kc = q.k_cond >= R(0) ? q.k_cond : mu * q.cvR;
         const R qx = -mu * ghx + kc * gTx, qy = -mu * ghy + kc * gTy;
-        const R w = wst<R>(cx, cy);
+        const R w = lane < 8 ? wst<R>(cx, cy) : R(0);
         // divergences from the difference to the opposite neighbour (lane 7 - l); each
         // opposite pair is counted by both of its lanes, hence the halved factors
-        const int opp = 7 - lane;
+        const int opp = 7 - l8;
         const R Kxx_o = __shfl_sync(gmask, Kxx, opp, LPN), Kxy_o = __shfl_sync(gmask, Kxy, opp, LPN);
         const R Kyy_o = __shfl_sync(gmask, Kyy, opp, LPN);
         const R qx_o = __shfl_sync(gmask, qx, opp, LPN), qy_o = __shfl_sync(gmask, qy, opp, LPN);
@@ -272,19 +277,20 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
     __syncthreads();
 
     // ---------------- phase 1: frame search (block lockstep) -----------------------
-    R df[9], dg[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) { df[i] = 0; dg[i] = 0; }
+    // my_df/my_dg: increments of population `lane` (and of population 8 on lane 0 when a
+    // group has 8 lanes) after the final stream of the node
+    R my_df = 0, my_dg = 0, my_df8 = 0, my_dg8 = 0;
     int it = 0;                                   // iterations of this block
     int my_it = 0, my_conv = 0, my_stall = 0;     // warp-0 lane bookkeeping for node threadIdx.x
     double my_res = 1e300;                        // previous residual of that node
-    const int kk = lane & 3, m1 = lane >> 2, m2 = m1 + 2;
+    const int kk = lane & 3, m1 = (lane >> 2) & 3, m2 = m1 + 2;
     while (sh.any_active && it < p.max_iter) {
         ++it;
         if (sh.active[grp]) {
             const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
             const R s = sqrt_(th), inv_s = R(1) / s;
-#pragma unroll
+            R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 1
             for (int i = 0; i < 9; ++i) {
                 const int jx = i % 3, jy = i / 3;
                 const R dx = -(s * R(jx - 1) + ux) * q.dt;
@@ -293,32 +299,33 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                 const int x0 = X + (int)flx - 1, y0 = Y + (int)fly - 1;
                 const R ax = lag1<R>(kk, dx - flx + R(1));
                 const R eta = dy - fly + R(1);
-                const R ay1 = lag1<R>(m1, eta), ay2 = lag1<R>(m2, eta);
                 const long long xx = bc_wrap(x0 + kk, p.nx, p.bcx);
-                const long long n1 = (long long)bc_wrap(y0 + m1, p.ny, p.bcy) * p.nx + xx;
-                const long long n2 = (long long)bc_wrap(y0 + m2, p.ny, p.bcy) * p.nx + xx;
-                R tf, tg, uf, ug;
-                pair_inc<R>(p, in, n1, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
-                pair_inc<R>(p, in, n2, jx, jy, th, s, inv_s, ux, uy, fx, gx, uf, ug);
-                df[i] = ax * (ay1 * tf + ay2 * uf);
-                dg[i] = ax * (ay1 * tg + ay2 * ug);
+                R vf = 0, vg = 0;
+#pragma unroll
+                for (int pp = 0; pp < PPL; ++pp) {
+                    const int mm = pp == 0 ? m1 : m2;
+                    const long long nd = (long long)bc_wrap(y0 + mm, p.ny, p.bcy) * p.nx + xx;
+                    R tf, tg;
+                    pair_inc<R>(p, in, nd, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
+                    const R ay = lag1<R>(mm, eta);
+                    vf += ay * tf;
+                    vg += ay * tg;
+                }
+                vf *= ax;
+                vg *= ax;
+#pragma unroll
+                for (int o = LPN / 2; o > 0; o >>= 1) {
+                    vf += __shfl_xor_sync(gmask, vf, o, LPN);
+                    vg += __shfl_xor_sync(gmask, vg, o, LPN);
+                }
+                if (lane == i) { my_df = vf; my_dg = vg; }
+                if (i == 8) { my_df8 = vf; my_dg8 = vg; }
+                a0 += vf;
+                a1 += vf * R(jx - 1);
+                a2 += vf * R(jy - 1);
+                a3 += vg;
             }
-#pragma unroll
-            for (int o = LPN / 2; o > 0; o >>= 1)
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    df[i] += __shfl_xor_sync(gmask, df[i], o, LPN);
-                    dg[i] += __shfl_xor_sync(gmask, dg[i], o, LPN);
-                }
             if (lane == 0) {
-                R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    a0 += df[i];
-                    a1 += df[i] * R(i % 3 - 1);
-                    a2 += df[i] * R(i / 3 - 1);
-                    a3 += dg[i];
-                }
                 sh.dsum[grp][0] = a0; sh.dsum[grp][1] = a1; sh.dsum[grp][2] = a2; sh.dsum[grp][3] = a3;
             }
         }
@@ -445,12 +452,14 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
             Xs[i] = om * geq + dtr * (gc + w * work);
         }
         R fo[2] = {R(0), R(0)}, go[2] = {R(0), R(0)};
+        constexpr int REPS = (9 + LPN - 1) / LPN;
 #pragma unroll
-        for (int rep = 0; rep < 2; ++rep) {
+        for (int rep = 0; rep < REPS; ++rep) {
             const int i = lane + rep * LPN;
             if (i < 9) {
                 const int kx = i % 3, ky = i / 3;
-                const R ft = pick(fx, i) + pick(df, i), gt = pick(gx, i) + pick(dg, i);
+                const R dfi = rep == 0 ? my_df : my_df8, dgi = rep == 0 ? my_dg : my_dg8;
+                const R ft = pick(fx, i) + dfi, gt = pick(gx, i) + dgi;
                 const R Wx = pick(W1, kx) + pick(Wsx, kx), Wy = pick(W1, ky) + pick(Wsy, ky);
                 const R Whk = pick(Whx, kx), Whl = pick(Why, ky);
                 const R feq = rr * Wx * Wy;
@@ -484,8 +493,8 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
         // the rest population (i = 4) takes the remainder, summed error-free as (hi, lo)
         // pairs, so that the stored populations keep these sums up to one rounding.
         {
-            R fh = (lane != 4 ? fo[0] : R(0)), fl = (lane == 0 ? fo[1] : R(0));
-            R gh = (lane != 4 ? go[0] : R(0)), gl = (lane == 0 ? go[1] : R(0));
+            R fh = (lane != 4 ? fo[0] : R(0)), fl = (REPS > 1 && lane == 0 ? fo[1] : R(0));
+            R gh = (lane != 4 ? go[0] : R(0)), gl = (REPS > 1 && lane == 0 ? go[1] : R(0));
             two_sum_(fh, fl, fh, fl);
             two_sum_(gh, gl, gh, gl);
 #pragma unroll
@@ -507,11 +516,15 @@ __global__ void __launch_bounds__(STEP_NB *STEP_LPN) k_pond_step(DevParams p, co
                 go[0] = (th_ - gh) + (tl_ - gl);
             }
         }
-        out[(P_F + lane) * N + n] = fo[0];
-        out[(P_G + lane) * N + n] = go[0];
+        if (lane < 9) {
+            out[(P_F + lane) * N + n] = fo[0];
+            out[(P_G + lane) * N + n] = go[0];
+        }
         if (lane == 0) {
-            out[(P_F + 8) * N + n] = fo[1];
-            out[(P_G + 8) * N + n] = go[1];
+            if (REPS > 1) {
+                out[(P_F + 8) * N + n] = fo[1];
+                out[(P_G + 8) * N + n] = go[1];
+            }
             out[P_TH * N + n] = th;
             out[P_UX * N + n] = ux;
             out[P_UY * N + n] = uy;

@@ -44,7 +44,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("dt", C.c_double), ("k_cond", C.c_double), ("p_floor", C.c_double),
                 ("stream", C.c_void_p), ("dalloc", _ALLOC), ("dfree", _FREE),
-                ("alloc_ctx", C.c_void_p)]
+                ("alloc_ctx", C.c_void_p), ("lanes_per_node", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -128,7 +128,8 @@ class Simulation:
                  delta: float = 1.0 / 3.0, kappa: float = 0.0, tau: float = 1.0,
                  precision: str = "mixed", dt: float = 0.5, tol: float | None = None,
                  max_iter: int = 20, k_cond: float = -1.0, p_floor: float = 1e-3 / 6.0,
-                 stream=None, torch_alloc: bool = True, ideal: bool = False):
+                 stream=None, torch_alloc: bool = True, ideal: bool = False,
+                 lanes_per_node: int = 0):
         torch = _torch()
         self._lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -164,10 +165,12 @@ class Simulation:
         lat = Lattice(POND_D2Q9)
         eos = Eos(POND_IDEAL if ideal else POND_VDW, a, b, R, delta)
         opts = Opts(POND_MIXED if precision == "mixed" else POND_FP64, max_iter, tol, dt, k_cond,
-                    p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None)
+                    p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None,
+                    lanes_per_node, 0)
         self.params = dict(nx=nx, ny=ny, bc_x=bc_x, bc_y=bc_y, a=a, b=b, R=R, delta=delta,
                            kappa=kappa, tau=tau, precision=precision, dt=dt, tol=tol,
-                           max_iter=max_iter, k_cond=k_cond, p_floor=p_floor)
+                           max_iter=max_iter, k_cond=k_cond, p_floor=p_floor,
+                           lanes_per_node=lanes_per_node)
         ctx = C.c_void_p()
         with torch.cuda.device(self._device):
             st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos), kappa, tau,

@@ -52,7 +52,7 @@ def test_invalid_parameters_are_rejected_on_the_host(lib):
     g = pond.Grid(0, 4, 0, 0)
     lat = pond.Lattice(0)
     eos = pond.Eos(0, 2 / 49, 2 / 21, 1.0, 1 / 3)
-    opts = pond.Opts(1, 20, 1e-6, 0.5, -1.0, 1e-4, None, pond._ALLOC(), pond._FREE(), None)
+    opts = pond.Opts(1, 20, 1e-6, 0.5, -1.0, 1e-4, None, pond._ALLOC(), pond._FREE(), None, 0, 0)
     out = ctypes.c_void_p()
     assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(eos), 0.0, 1.0,
                          ctypes.byref(opts), ctypes.byref(out)) == 1

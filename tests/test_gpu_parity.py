@@ -181,3 +181,15 @@ def test_state_round_trip_and_invalid_init(pond):
         with pytest.raises(pond.PondError) as ei:
             sim.init_fields(bad, w.ux, w.uy, w.T)
         assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("lanes", [8, 16])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_lanes_per_node_variants_match_oracle(pond, lanes, precision):
+    """Both work splits of the step kernel (8 or 16 lanes per node) meet the bar."""
+    w = inputs.droplet(n=40, ny=28, Tr=0.9, radius=7.0, steps=20)
+    P, st, _ = oracle_run(w)
+    ref = oracle.moments(P, st)
+    got, gstats = gpu_run(pond, w, precision, lanes_per_node=lanes)
+    err = rel_linf(got, ref)
+    assert max(err.values()) <= TOL[precision], err
