@@ -107,6 +107,9 @@ typedef struct {
     int64_t nonfinite;     /* node updates that produced NaN/Inf                */
     int64_t stalled;       /* mixed form: frame searches stopped at the FP32
                               rounding floor (residual no longer halving)      */
+    int64_t block_streams; /* streaming passes summed over kernel blocks (a block
+                              of 32 nodes streams until all its nodes stop)    */
+    int64_t max_streams;   /* largest streaming-pass count of any block        */
 } pond_stats_t;
 
 /* Create a context and allocate its device state (two state buffers of 25 planes,

@@ -1,6 +1,7 @@
 // pond.cu -- host side of libpond: the C ABI declared in include/pond.h.
 //
-// A context owns two 25-plane state buffers (ping-pong), a 5-plane FP64 staging buffer
+// A context owns two state buffers of one 32-value record per node (ping-pong), a
+// 5-plane FP64 staging buffer
 // for host <-> device field copies, the block partials of the conservation sums and a
 // small block of device counters.  Every call enqueues on the context stream; one time
 // step is one launch of the fused kernel k_pond_step (pond_step.cuh).
@@ -89,7 +90,7 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
-    const unsigned nb = blocks_for(c->N, STEP_NB);
+    const unsigned nb = blocks_for(c->N, STEP_NB);   // STEP_NB nodes per block
     if (ev) cudaEventRecord(ev[0], c->stream);
     if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, 0, c->stream>>>(c->dp, in, out, c->dstats);
     else k_pond_step<R, 8><<<nb, STEP_NB * 8, 0, c->stream>>>(c->dp, in, out, c->dstats);
@@ -216,7 +217,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     d.pf.cvR = (float)d.pd.cvR; d.pf.k_cond = (float)d.pd.k_cond;
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
-    size_t sb = (size_t)NPL * c->N * c->esize;
+    size_t sb = (size_t)SL * c->N * c->esize;
     c->state[0] = dev_alloc(c, sb);
     c->state[1] = dev_alloc(c, sb);
     c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
@@ -357,18 +358,18 @@ pond_status pond_get_state(pond_ctx *c, double *state)
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null output");
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
-    size_t total = (size_t)NPL * c->N;
-    if (!mixed(c)) {
-        CK(cudaMemcpyAsync(state, c->state[c->cur], total * sizeof(double), cudaMemcpyDeviceToHost,
-                           c->stream), "cudaMemcpyAsync D2H");
-        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-        return POND_OK;
-    }
-    std::vector<float> tmp(total);
-    CK(cudaMemcpyAsync(tmp.data(), c->state[c->cur], total * sizeof(float), cudaMemcpyDeviceToHost,
-                       c->stream), "cudaMemcpyAsync D2H");
+    const size_t N = c->N, rec = (size_t)SL * N;
+    std::vector<double> d(mixed(c) ? 0 : rec);
+    std::vector<float> f(mixed(c) ? rec : 0);
+    void *dst = mixed(c) ? (void *)f.data() : (void *)d.data();
+    CK(cudaMemcpyAsync(dst, c->state[c->cur], rec * c->esize, cudaMemcpyDeviceToHost, c->stream),
+       "cudaMemcpyAsync D2H");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    for (size_t k = 0; k < total; ++k) state[k] = (double)tmp[k];
+    for (int p = 0; p < NPL; ++p) {
+        const int o = rec_off(p);
+        for (size_t n = 0; n < N; ++n)
+            state[(size_t)p * N + n] = mixed(c) ? (double)f[n * SL + o] : d[n * SL + o];
+    }
     return POND_OK;
 }
 
@@ -377,16 +378,19 @@ pond_status pond_set_state(pond_ctx *c, const double *state)
     pond_status st = check_ctx(c);
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null input");
-    size_t total = (size_t)NPL * c->N;
-    if (!mixed(c)) {
-        CK(cudaMemcpyAsync(c->state[c->cur], state, total * sizeof(double), cudaMemcpyHostToDevice,
-                           c->stream), "cudaMemcpyAsync H2D");
-    } else {
-        std::vector<float> tmp(total);
-        for (size_t k = 0; k < total; ++k) tmp[k] = (float)state[k];
-        CK(cudaMemcpyAsync(c->state[c->cur], tmp.data(), total * sizeof(float), cudaMemcpyHostToDevice,
-                           c->stream), "cudaMemcpyAsync H2D");
+    const size_t N = c->N, rec = (size_t)SL * N;
+    std::vector<double> d(mixed(c) ? 0 : rec, 0.0);
+    std::vector<float> f(mixed(c) ? rec : 0, 0.0f);
+    for (int p = 0; p < NPL; ++p) {
+        const int o = rec_off(p);
+        for (size_t n = 0; n < N; ++n) {
+            if (mixed(c)) f[n * SL + o] = (float)state[(size_t)p * N + n];
+            else d[n * SL + o] = state[(size_t)p * N + n];
+        }
     }
+    const void *src = mixed(c) ? (const void *)f.data() : (const void *)d.data();
+    CK(cudaMemcpyAsync(c->state[c->cur], src, rec * c->esize, cudaMemcpyHostToDevice, c->stream),
+       "cudaMemcpyAsync H2D");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
     c->initialised = true;
     return POND_OK;
@@ -409,6 +413,8 @@ pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
     out->clamped = (int64_t)hs.clamped;
     out->nonfinite = (int64_t)hs.nonfinite;
     out->stalled = (int64_t)hs.stalled;
+    out->block_streams = (int64_t)hs.block_streams;
+    out->max_streams = (int64_t)hs.max_streams;
     return hs.nonfinite ? fail(c, POND_ENAN, "non-finite values in the state") : POND_OK;
 }
 

@@ -1,8 +1,13 @@
 // pond_kernels.cuh -- device code of the PonD van der Waals time step for sm_103a.
 //
-// Layout: a state buffer holds 25 planes of N = nx*ny values (x fastest):
-//   f_0..f_8, g_0..g_8, theta, u_x, u_y, rho, T, uhat_x, uhat_y
+// Layout: a state buffer holds one record of SL = 32 values per node (node = y*nx + x),
+// 128 bytes in FP32 so that a node is one cache line and its 21 streamed values are read
+// with six 16-byte loads:
+//   [0..8] f_0..f_8, [9..17] g_0..g_8, [18] theta, [19] u_x, [20] u_y, [21] unused,
+//   [22] rho, [23] T, [24] uhat_x, [25] uhat_y, [26..31] unused
 // with population index i = 3*(cy+1) + (cx+1).  R = float (mixed form) or double.
+// The ABI's state planes (f, g, theta, u_x, u_y, rho, T, uhat_x, uhat_y) map to record
+// offsets by rec_off().
 #pragma once
 
 #include <cuda_runtime.h>
@@ -10,9 +15,13 @@
 
 namespace pond {
 
-constexpr int NPL = 25;
-enum : int { P_F = 0, P_G = 9, P_TH = 18, P_UX = 19, P_UY = 20, P_RHO = 21, P_T = 22,
-             P_UHX = 23, P_UHY = 24 };
+constexpr int NPL = 25;   // planes of the ABI state
+constexpr int SL = 32;    // values per node record on the device
+enum : int { P_F = 0, P_G = 9, P_TH = 18, P_UX = 19, P_UY = 20, P_RHO = 22, P_T = 23,
+             P_UHX = 24, P_UHY = 25 };
+__host__ __device__ constexpr int rec_off(int plane) { return plane < 21 ? plane : plane + 1; }
+// value `off` of node n's record
+#define REC(buf, n, off) (buf)[(size_t)(n) * SL + (off)]
 
 // Model constants in the arithmetic type of a kernel (float copies keep FP64 work out of
 // the FP32 paths).
@@ -39,7 +48,7 @@ template <> __device__ __forceinline__ const TypedParams<float> &typed<float>(co
 template <> __device__ __forceinline__ const TypedParams<double> &typed<double>(const DevParams &p) { return p.pd; }
 
 struct DevStats {
-    unsigned long long streams, nonconv, clamped, nonfinite, bad_init, stalled;
+    unsigned long long streams, nonconv, clamped, nonfinite, bad_init, stalled, block_streams, max_streams;
 };
 
 // lattice temperature T_L = 1/3 and 1-D weights W_-1, W_0, W_+1 (SM "Equilibrium")
@@ -50,6 +59,9 @@ __device__ __forceinline__ double w1d(int a) { return a == 1 ? 2.0 / 3.0 : 1.0 /
 __device__ __forceinline__ int bc_wrap(int i, int n, int bc)
 {
     if (bc == 0) {
+        if (i >= 0 && i < n) return i;
+        if (i < 0 && i >= -n) return i + n;
+        if (i >= n && i < 2 * n) return i - n;
         i %= n;
         return i < 0 ? i + n : i;
     }
@@ -117,16 +129,16 @@ __global__ void k_init(DevParams p, const double *__restrict__ rho, const double
         int cx = i % 3 - 1, cy = i / 3 - 1;
         double w = w1d(cx + 1) * w1d(cy + 1);
         double vx = s * cx + ux[n], vy = s * cy + uy[n];
-        st[(P_F + i) * N + n] = (R)(r * w);
-        st[(P_G + i) * N + n] = (R)(r * w * (2.0 * e - 2.0 * P / r + vx * vx + vy * vy) + w * lam_e);
+        REC(st, n, P_F + i) = (R)(r * w);
+        REC(st, n, P_G + i) = (R)(r * w * (2.0 * e - 2.0 * P / r + vx * vx + vy * vy) + w * lam_e);
     }
-    st[P_TH * N + n] = (R)th;
-    st[P_UX * N + n] = (R)ux[n];
-    st[P_UY * N + n] = (R)uy[n];
-    st[P_RHO * N + n] = (R)r;
-    st[P_T * N + n] = (R)t;
-    st[P_UHX * N + n] = (R)ux[n];
-    st[P_UHY * N + n] = (R)uy[n];
+    REC(st, n, P_TH) = (R)th;
+    REC(st, n, P_UX) = (R)ux[n];
+    REC(st, n, P_UY) = (R)uy[n];
+    REC(st, n, P_RHO) = (R)r;
+    REC(st, n, P_T) = (R)t;
+    REC(st, n, P_UHX) = (R)ux[n];
+    REC(st, n, P_UHY) = (R)uy[n];
 }
 
 template <typename T>
@@ -148,10 +160,10 @@ __global__ void k_moments(DevParams p, const R *__restrict__ st, double *rho, do
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     const long long N = p.N;
-    double r = (double)st[P_RHO * N + n], t = (double)st[P_T * N + n];
+    double r = (double)REC(st, n, P_RHO), t = (double)REC(st, n, P_T);
     if (rho) rho[n] = r;
-    if (ux) ux[n] = (double)st[P_UHX * N + n];
-    if (uy) uy[n] = (double)st[P_UHY * N + n];
+    if (ux) ux[n] = (double)REC(st, n, P_UHX);
+    if (uy) uy[n] = (double)REC(st, n, P_UHY);
     if (T) T[n] = t;
     if (pr) pr[n] = r * p.R * t / (1.0 - p.b * r) - p.a * r * r;
 }
@@ -182,10 +194,10 @@ __global__ void k_conserve1(DevParams p, const R *__restrict__ st, double *part)
     double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
-        double r = (double)st[P_RHO * N + n];
+        double r = (double)REC(st, n, P_RHO);
         double eg = 0.0;
-        for (int i = 0; i < 9; ++i) eg += (double)st[(P_G + i) * N + n];
-        double v[4] = {r, r * (double)st[P_UHX * N + n], r * (double)st[P_UHY * N + n], 0.5 * eg};
+        for (int i = 0; i < 9; ++i) eg += (double)REC(st, n, P_G + i);
+        double v[4] = {r, r * (double)REC(st, n, P_UHX), r * (double)REC(st, n, P_UHY), 0.5 * eg};
         for (int k = 0; k < 4; ++k) pair_add(s[k], c[k], v[k], 0.0);
     }
     for (int o = 16; o > 0; o >>= 1)

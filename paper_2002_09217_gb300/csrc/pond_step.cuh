@@ -1,6 +1,6 @@
 // pond_step.cuh -- the fused time-step kernel of the PonD van der Waals model (sm_103a).
 //
-// One launch per time step.  A block owns NB = 32 nodes; each node is served by a group
+// One launch per time step.  A block owns NB = 16 nodes; each node is served by a group
 // of LPN = 8 or 16 lanes of one warp.  Per node:
 //   phase 0  non-local terms from the previous step's rho and T (radius 2): lane l of the
 //            group takes the l-th non-rest neighbour, builds the Korteweg stress K and the
@@ -27,9 +27,11 @@
 
 namespace pond {
 
-constexpr int STEP_NB = 32;   // nodes per block (lanes per node LPN = 8 or 16 is a template
+constexpr int STEP_NB = 16;   // nodes per block (lanes per node LPN = 8 or 16 is a template
                               // parameter: more lanes per node for grids too small to fill
-                              // the GPU with 8)
+                              // the GPU with 8); 16 nodes per block keep small grids spread
+                              // evenly over the 152 SMs
+constexpr unsigned STEP_NB_MASK = STEP_NB == 32 ? 0xffffffffu : ((1u << STEP_NB) - 1u);
 
 template <typename R>
 struct StepShared {
@@ -119,19 +121,53 @@ __device__ __forceinline__ void two_sum_(R a, R b, R &s, R &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+// The 21 streamed values of node nd's record (f[9], g[9], theta, u_x, u_y, plus rho and T
+// in [22..23]) with 16-byte loads through the read-only path.
+__device__ __forceinline__ void load_rec24(const float *__restrict__ b, float v[24])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(b);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 t = __ldg(q + k);
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_rec24(const double *__restrict__ b, double v[24])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 t = __ldg(q + k);
+        v[2 * k] = t.x; v[2 * k + 1] = t.y;
+    }
+}
+
+// rho and T of node m (adjacent in the record) with one 8- or 16-byte load.
+__device__ __forceinline__ void load_rhoT(const float *__restrict__ in, size_t m, float &r, float &t)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(in + m * SL + P_RHO));
+    r = v.x; t = v.y;
+}
+__device__ __forceinline__ void load_rhoT(const double *__restrict__ in, size_t m, double &r, double &t)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(in + m * SL + P_RHO));
+    r = v.x; t = v.y;
+}
+
 // Contribution of stencil node `nd` to direction (jx, jy) of the arrival node, in the
 // increment form; fx/gx are the arrival node's own stored populations.
 template <typename R>
-__device__ __forceinline__ void pair_inc(const DevParams &p, const R *__restrict__ in, long long nd,
-                                         int jx, int jy, R th, R s, R inv_s, R ux, R uy,
-                                         const R fx[9], const R gx[9], R &tf, R &tg)
+__device__ __forceinline__ void pair_inc(const R *__restrict__ in, size_t nd, int jx, int jy, R th,
+                                         R s, R inv_s, R ux, R uy, const R fx[9], const R gx[9],
+                                         R &tf, R &tg)
 {
-    const long long N = p.N;
-    R thn = in[P_TH * N + nd];
-    R sn = sqrt_(thn);
-    R qm1 = fdiv_(thn - th, (sn + s) * s);          // (s_n - s)/s without cancellation
-    R wx = (in[P_UX * N + nd] - ux) * inv_s;
-    R wy = (in[P_UY * N + nd] - uy) * inv_s;
+    R v[24];
+    load_rec24(in + nd * SL, v);
+    const R thn = v[P_TH];
+    const R sn = sqrt_(thn);
+    const R qm1 = fdiv_(thn - th, (sn + s) * s);    // (s_n - s)/s without cancellation
+    const R wx = (v[P_UX] - ux) * inv_s;
+    const R wy = (v[P_UY] - uy) * inv_s;
     R Ex[3], Ey[3], Gx[3], Gy[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -147,10 +183,8 @@ __device__ __forceinline__ void pair_inc(const DevParams &p, const R *__restrict
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int i = 3 * b + a;
-            R df = in[(P_F + i) * N + nd] - fx[i];
-            R dg = in[(P_G + i) * N + nd] - gx[i];
-            rf += Gx[a] * df + Ex[a] * fx[i];
-            rg += Gx[a] * dg + Ex[a] * gx[i];
+            rf += Gx[a] * (v[P_F + i] - fx[i]) + Ex[a] * fx[i];
+            rg += Gx[a] * (v[P_G + i] - gx[i]) + Ex[a] * gx[i];
         }
         const R fxj = jx == 0 ? fx[3 * b] : (jx == 1 ? fx[3 * b + 1] : fx[3 * b + 2]);
         const R gxj = jx == 0 ? gx[3 * b] : (jx == 1 ? gx[3 * b + 1] : gx[3 * b + 2]);
@@ -186,8 +220,8 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         const int dir = l8 < 4 ? l8 : l8 + 1;
         const int cx = dir % 3 - 1, cy = dir / 3 - 1;
         const int mx = bc_wrap(X + cx, p.nx, p.bcx), my = bc_wrap(Y + cy, p.ny, p.bcy);
-        const R *rho = in + P_RHO * N, *T = in + P_T * N;
-        const R r0 = rho[(long long)my * p.nx + mx], t0 = T[(long long)my * p.nx + mx];
+        R r0, t0;
+        load_rhoT(in, (size_t)my * p.nx + mx, r0, t0);
         const R pr0 = r0 * q.R * t0 / (R(1) - q.b * r0) - q.a * r0 * r0;
         // gradients from differences to the centre value (sum_i W_i c_i = 0), which keeps
         // their FP32 rounding proportional to the differences
@@ -196,9 +230,10 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         for (int i = 0; i < 9; ++i) {
             const int ex = i % 3 - 1, ey = i / 3 - 1;
             if (ex == 0 && ey == 0) continue;
-            long long m = (long long)bc_wrap(my + ey, p.ny, p.bcy) * p.nx + bc_wrap(mx + ex, p.nx, p.bcx);
+            const size_t m = (size_t)bc_wrap(my + ey, p.ny, p.bcy) * p.nx + bc_wrap(mx + ex, p.nx, p.bcx);
             const R w = wst<R>(ex, ey);
-            const R r = rho[m], t = T[m];
+            R r, t;
+            load_rhoT(in, m, r, t);
             const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
             const R dr = r - r0, dT = t - t0;
             const R dh = q.cv * dT - q.a * dr + (pr / r - pr0 / r0);
@@ -242,15 +277,19 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         rEl = R(0.5) * kap * (gxn * gxn + gyn * gyn);
     }
     R fx[9], gx[9];
+    {
+        R v[24];
+        load_rec24(in + (size_t)nn * SL, v);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        fx[i] = in[(P_F + i) * N + nn];
-        gx[i] = in[(P_G + i) * N + nn];
+        for (int i = 0; i < 9; ++i) {
+            fx[i] = v[P_F + i];
+            gx[i] = v[P_G + i];
+        }
     }
     if (lane == 0) {
-        sh.lam[grp][0] = in[P_TH * N + nn];
-        sh.lam[grp][1] = in[P_UX * N + nn];
-        sh.lam[grp][2] = in[P_UY * N + nn];
+        sh.lam[grp][0] = REC(in, nn, P_TH);
+        sh.lam[grp][1] = REC(in, nn, P_UX);
+        sh.lam[grp][2] = REC(in, nn, P_UY);
         sh.nl[grp][0] = Fx;
         sh.nl[grp][1] = Fy;
         sh.nl[grp][2] = rEl;
@@ -262,13 +301,13 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double f = (double)in[(P_F + i) * N + nj];
+            const double f = (double)REC(in, nj, P_F + i);
             b0 += f;
             if (i % 3 == 0) b1 -= f;
             if (i % 3 == 2) b1 += f;
             if (i / 3 == 0) b2 -= f;
             if (i / 3 == 2) b2 += f;
-            b3 += (double)in[(P_G + i) * N + nj];
+            b3 += (double)REC(in, nj, P_G + i);
         }
         sh.base[threadIdx.x][0] = b0; sh.base[threadIdx.x][1] = b1;
         sh.base[threadIdx.x][2] = b2; sh.base[threadIdx.x][3] = b3;
@@ -306,7 +345,7 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
                     const int mm = pp == 0 ? m1 : m2;
                     const long long nd = (long long)bc_wrap(y0 + mm, p.ny, p.bcy) * p.nx + xx;
                     R tf, tg;
-                    pair_inc<R>(p, in, nd, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
+                    pair_inc<R>(in, (size_t)nd, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
                     const R ay = lag1<R>(mm, eta);
                     vf += ay * tf;
                     vg += ay * tg;
@@ -384,7 +423,7 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
                     sh.lam[j][2] = (R)uys;
                 }
             }
-            const int any = __any_sync(0xffffffffu, sh.active[j]);
+            const int any = __any_sync(STEP_NB_MASK, sh.active[j]);
             if (j == 0) sh.any_active = any;
         }
         __syncthreads();
@@ -517,21 +556,21 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
             }
         }
         if (lane < 9) {
-            out[(P_F + lane) * N + n] = fo[0];
-            out[(P_G + lane) * N + n] = go[0];
+            REC(out, n, P_F + lane) = fo[0];
+            REC(out, n, P_G + lane) = go[0];
         }
         if (lane == 0) {
             if (REPS > 1) {
-                out[(P_F + 8) * N + n] = fo[1];
-                out[(P_G + 8) * N + n] = go[1];
+                REC(out, n, P_F + 8) = fo[1];
+                REC(out, n, P_G + 8) = go[1];
             }
-            out[P_TH * N + n] = th;
-            out[P_UX * N + n] = ux;
-            out[P_UY * N + n] = uy;
-            out[P_RHO * N + n] = rr;
-            out[P_T * N + n] = m[6];
-            out[P_UHX * N + n] = uhxr;
-            out[P_UHY * N + n] = uhyr;
+            REC(out, n, P_TH) = th;
+            REC(out, n, P_UX) = ux;
+            REC(out, n, P_UY) = uy;
+            REC(out, n, P_RHO) = rr;
+            REC(out, n, P_T) = m[6];
+            REC(out, n, P_UHX) = uhxr;
+            REC(out, n, P_UHY) = uhyr;
         }
     }
     // ---------------- statistics (warp 0, one lane per node) -----------------------
@@ -545,6 +584,10 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         warp_add(&stats->clamped, (v && pr < q.p_floor) ? 1 : 0);
         const bool bad = v && (!(rr == rr) || !(T == T) || isinf(rr) || isinf(T));
         warp_add(&stats->nonfinite, bad ? 1 : 0);
+        if (j == 0) {
+            atomicAdd(&stats->block_streams, (unsigned long long)it);
+            atomicMax(&stats->max_streams, (unsigned long long)it);
+        }
     }
 }
 
