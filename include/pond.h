@@ -159,6 +159,29 @@ pond_status pond_step_timed(pond_ctx *ctx, double *ms_out);
 /* Read (and, if reset != 0, zero) the device counters.  Synchronises. */
 pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);
 
+/* Conservation sums without any allocation, for callers that cannot allocate device
+ * memory themselves or through the library: code running where cudaMalloc is not
+ * allowed, such as inside a region whose memory budget is fixed up front, or a host
+ * that hands the library only pre-placed buffers.  The paper has no counterpart; this
+ * is a service of the library.
+ *
+ * d_planes: device pointer to a state in the 25-plane FP64 layout of pond_get_state
+ * (plane p of node n at p*n_nodes + n), caller-owned and only read.  out: host array of
+ * 4 doubles {sum rho, sum rho uhat_x, sum rho uhat_y, sum_nodes sum_i g_i / 2}, summed in
+ * FP64 with compensated summation as pond_conservation does.  stream: cudaStream_t of
+ * the work (NULL = default stream); the call synchronises it before returning.
+ *
+ * Scratch: the block partials live in a file-scope device array of the library
+ * (32,776 doubles, 256 KiB, held on every device that loads the library until the
+ * process exits), so n_nodes may be at most 8,388,608; larger n_nodes, n_nodes < 1 or
+ * NULL pointers return POND_EINVAL.  The array's device address is looked up on the
+ * first call on each device (that call should come before any stream capture).  All
+ * calls share the one array: calls that overlap on the GPU (different streams, threads
+ * or processes sharing a context) race on it; every slot a call reads it has written
+ * itself first.  Returns POND_ECUDA on a CUDA error. */
+pond_status pond_conservation_noalloc(const double *d_planes, int64_t n_nodes, double out[4],
+                                      void *stream);
+
 /* Bytes of device memory the context holds (state + scratch). */
 size_t pond_device_bytes(const pond_ctx *ctx);
 

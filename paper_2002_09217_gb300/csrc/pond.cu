@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -148,9 +149,62 @@ pond_status init_common(pond_ctx *c, const double *d_rho, const double *d_ux, co
     return POND_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free conservation sums.  Scratch for the block partials lives in this
+// file-scope device array instead of memory the caller or the library allocates: every
+// device that loads the library holds these NOALLOC_SCRATCH_DOUBLES doubles until the
+// process exits.  Host code may not pass the symbol itself to a kernel (it is a host-side
+// stand-in, not a device address); the device address is looked up once per device.
+constexpr int NOALLOC_SPAN = 2048;          // nodes summed by one block
+constexpr int NOALLOC_MAX_BLOCKS = 4096;    // => at most 8,388,608 nodes per call
+constexpr int NOALLOC_SCRATCH_DOUBLES = 8 * NOALLOC_MAX_BLOCKS + 8;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+double *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device, looked up on first use.
+cudaError_t noalloc_scratch(double **ptr)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
+
+pond_status pond_conservation_noalloc(const double *d_planes, int64_t n_nodes, double out[4],
+                                      void *stream)
+{
+    if (!d_planes || !out || n_nodes < 1) return POND_EINVAL;
+    if (n_nodes > (int64_t)NOALLOC_SPAN * NOALLOC_MAX_BLOCKS) return POND_EINVAL;
+    double *scratch = nullptr;
+    if (noalloc_scratch(&scratch) != cudaSuccess) return POND_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)((n_nodes + NOALLOC_SPAN - 1) / NOALLOC_SPAN);
+    k_conserve_planes1<<<nb, 256, 0, s>>>(d_planes, (long long)n_nodes, NOALLOC_SPAN, scratch);
+    k_conserve2<<<1, 32, 0, s>>>(scratch, nb, scratch + 8 * NOALLOC_MAX_BLOCKS);
+    if (cudaGetLastError() != cudaSuccess) return POND_ECUDA;
+    if (cudaMemcpyAsync(out, scratch + 8 * NOALLOC_MAX_BLOCKS, 4 * sizeof(double),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return POND_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return POND_ECUDA;
+    return POND_OK;
+}
+
 
 const char *pond_version(void) { return "pond-gb300 0.1 (sm_103a)"; }
 

@@ -222,6 +222,43 @@ __global__ void k_conserve1(DevParams p, const R *__restrict__ st, double *part)
     }
 }
 
+// Stage 1 over the ABI's 25-plane FP64 state layout (plane p of node n at p*N + n), with
+// each block summing a fixed span of `span` nodes so that the number of partials is
+// ceil(N / span): {rho, rho uhat_x, rho uhat_y, sum_i g_i / 2} as in k_conserve1.
+__global__ void k_conserve_planes1(const double *__restrict__ planes, long long N, int span, double *part)
+{
+    double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    const long long lo = (long long)blockIdx.x * span;
+    const long long hi = lo + span < N ? lo + span : N;
+    for (long long n = lo + threadIdx.x; n < hi; n += blockDim.x) {
+        const double r = planes[21 * N + n];
+        double eg = 0.0;
+        for (int i = 0; i < 9; ++i) eg += planes[(9 + i) * N + n];
+        const double v[4] = {r, r * planes[23 * N + n], r * planes[24 * N + n], 0.5 * eg};
+        for (int k = 0; k < 4; ++k) pair_add(s[k], c[k], v[k], 0.0);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 4; ++k) {
+            double s2 = __shfl_xor_sync(0xffffffffu, s[k], o);
+            double c2 = __shfl_xor_sync(0xffffffffu, c[k], o);
+            pair_add(s[k], c[k], s2, c2);
+        }
+    __shared__ double sh[32][8];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) { sh[warp][2 * k] = s[k]; sh[warp][2 * k + 1] = c[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < 4; ++k) {
+            double ss = sh[0][2 * k], cc = sh[0][2 * k + 1];
+            for (int w = 1; w < nw; ++w) pair_add(ss, cc, sh[w][2 * k], sh[w][2 * k + 1]);
+            part[blockIdx.x * 8 + 2 * k] = ss;
+            part[blockIdx.x * 8 + 2 * k + 1] = cc;
+        }
+    }
+}
+
 // Stage 2: one thread folds the block partials into out[4].
 __global__ void k_conserve2(const double *part, int nblocks, double *out)
 {

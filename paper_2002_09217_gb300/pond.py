@@ -101,6 +101,8 @@ def load() -> C.CDLL:
         lib.pond_device_bytes.argtypes = [P]
         lib.pond_device_bytes.restype = C.c_size_t
         lib.pond_version.restype = C.c_char_p
+        lib.pond_conservation_noalloc.argtypes = [C.c_void_p, C.c_int64, dp, C.c_void_p]
+        lib.pond_conservation_noalloc.restype = C.c_int
         _lib = lib
         return lib
 
@@ -260,6 +262,21 @@ class Simulation:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def conservation_noalloc(d_planes, n_nodes: int, stream=None) -> np.ndarray:
+    """Conservation sums of a caller-owned device state in the 25-plane FP64 layout,
+    computed without any device allocation (see pond_conservation_noalloc in pond.h).
+    d_planes: a CUDA float64 tensor (or a raw device address) of 25 * n_nodes values."""
+    lib = load()
+    ptr = d_planes.data_ptr() if hasattr(d_planes, "data_ptr") else int(d_planes)
+    sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    out = np.zeros(4)
+    st = lib.pond_conservation_noalloc(C.c_void_p(ptr), int(n_nodes), _dptr(out),
+                                       C.c_void_p(sp) if sp else None)
+    if st != 0:
+        raise PondError(st, "pond_conservation_noalloc failed")
+    return out
 
 
 def from_workload(w, precision: str = "mixed", **kw) -> Simulation:
