@@ -245,10 +245,9 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     c->stream = (cudaStream_t)opts->stream;
     c->N = (size_t)grid->nx * (size_t)grid->ny;
     c->esize = opts->precision == POND_MIXED ? sizeof(float) : sizeof(double);
-    // 16 lanes per node while 8 would leave the GPU under-filled (fewer than ~300k
-    // threads in flight); the caller may fix it (autotuning).
-    c->lanes = opts->lanes_per_node ? opts->lanes_per_node
-                                    : (opts->precision == POND_MIXED && c->N * 8 < 300000 ? 16 : 8);
+    // 8 lanes per node unless the caller picks 16 (measured faster on every grid tried so
+    // far; the choice is exposed for the autotuner).
+    c->lanes = opts->lanes_per_node ? opts->lanes_per_node : 8;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
         std::string m = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
