@@ -80,8 +80,10 @@ typedef struct { int32_t kind; double a, b, R, delta; } pond_eos;
  * p_floor: pressure floor of the gauge temperature theta = max(p, p_floor)/(rho T_L).
  * stream: a cudaStream_t (NULL = default stream).
  * dalloc/dfree/alloc_ctx: optional device allocator (both or neither).
- * lanes_per_node: threads cooperating on one node in the step kernel, 8 or 16
- * (0 = choose from the grid size); a performance knob, results are the same to rounding. */
+ * lanes_per_node: threads cooperating on one node in the step kernel, 8 or 16 (0 = 8).
+ * tile_x: width of the step kernel's tile of 16 nodes, 1, 2, 4, 8 or 16 (tile height
+ * 16 / tile_x; 0 = 16 for grids of fewer than 4 rows, else 4).  Both are performance
+ * knobs (autotuning); results are the same to rounding. */
 typedef struct {
     int32_t precision;
     int32_t max_iter;
@@ -94,7 +96,7 @@ typedef struct {
     void (*dfree)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
     int32_t lanes_per_node;
-    int32_t reserved;
+    int32_t tile_x;
 } pond_opts;
 
 /* Device counters accumulated since the last pond_stats() call that reset them. */

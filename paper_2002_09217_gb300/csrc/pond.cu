@@ -91,10 +91,12 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
-    const unsigned nb = blocks_for(c->N, STEP_NB);   // STEP_NB nodes per block
+    const int tx = c->dp.tile_x, ty = STEP_NB / tx;
+    const unsigned nb = (unsigned)(c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty));
+    const size_t smem = (size_t)step_tile_slots(tx) * Slot<R>::stride * sizeof(R);
     if (ev) cudaEventRecord(ev[0], c->stream);
-    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, 0, c->stream>>>(c->dp, in, out, c->dstats);
-    else k_pond_step<R, 8><<<nb, STEP_NB * 8, 0, c->stream>>>(c->dp, in, out, c->dstats);
+    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats);
+    else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats);
     if (ev) cudaEventRecord(ev[1], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
@@ -234,6 +236,9 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     if ((opts->dalloc == nullptr) != (opts->dfree == nullptr)) return POND_EINVAL;
     if (opts->lanes_per_node != 0 && opts->lanes_per_node != 8 && opts->lanes_per_node != 16)
         return POND_EINVAL;
+    if (opts->tile_x != 0 && opts->tile_x != 1 && opts->tile_x != 2 && opts->tile_x != 4 &&
+        opts->tile_x != 8 && opts->tile_x != 16)
+        return POND_EINVAL;
 
     pond_ctx *c = new pond_ctx();
     c->grid = *grid;
@@ -248,6 +253,8 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     // 8 lanes per node unless the caller picks 16 (measured faster on every grid tried so
     // far; the choice is exposed for the autotuner).
     c->lanes = opts->lanes_per_node ? opts->lanes_per_node : 8;
+    // tile of the step kernel: a 16 x 1 strip for grids of few rows, 4 x 4 otherwise
+    int tile_x = opts->tile_x ? opts->tile_x : (grid->ny < 4 ? 16 : 4);
     cudaError_t e = cudaGetDevice(&c->device);
     if (e != cudaSuccess) {
         std::string m = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
@@ -261,6 +268,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     d.a = c->eos.a; d.b = c->eos.b; d.R = c->eos.R; d.delta = c->eos.delta; d.cv = c->eos.R / c->eos.delta;
     d.kappa = kappa; d.tau = tau; d.omega = 1.0 / tau; d.dt = opts->dt; d.k_cond = opts->k_cond;
     d.p_floor = opts->p_floor; d.tol = opts->tol; d.max_iter = opts->max_iter;
+    d.tile_x = tile_x; d.tiles_x = (grid->nx + tile_x - 1) / tile_x;
     d.pd.a = d.a; d.pd.b = d.b; d.pd.R = d.R; d.pd.cv = d.cv; d.pd.inv_cv = 1.0 / d.cv;
     d.pd.kappa = d.kappa; d.pd.p_floor = d.p_floor; d.pd.dt = d.dt; d.pd.omega = d.omega;
     d.pd.mu_coef = (d.tau - 0.5) * d.dt; d.pd.cvR = d.cv + d.R; d.pd.k_cond = d.k_cond;

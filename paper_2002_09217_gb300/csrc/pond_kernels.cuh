@@ -39,6 +39,7 @@ struct DevParams {
     double a, b, R, delta, cv;
     double kappa, tau, omega, dt, k_cond, p_floor, tol;
     int max_iter;
+    int tile_x, tiles_x;   // step kernel tile: tile_x by (16 / tile_x) nodes; tiles per row
     TypedParams<float> pf;
     TypedParams<double> pd;
 };

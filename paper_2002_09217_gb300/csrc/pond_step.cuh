@@ -14,6 +14,13 @@
 //   phase 2  BGK collision with the force source, heat-flux correction and forced g
 //            equilibrium, one population per lane.
 //
+// Staging.  Each block owns a tile of tile_x x (16 / tile_x) nodes and first copies the
+// records of the tile plus a halo of HALO = 3 nodes (their first 24 values) into shared
+// memory with 16-byte cp.async copies, one record slot per unwrapped coordinate, so that
+// periodic and zero-gradient boundaries need no special case.  All stencil reads of the
+// step come from there; a departure point farther than the halo (|v| dt >= 1) falls back
+// to a global load.
+//
 // Increment form.  With f~_i = sum_n A_n [G_n f(n)]_i and sum_n A_n = 1,
 //   f~_i = f_i(x) + sum_n A_n ( [G_n (f(n) - f(x))]_i + [(G_n - I) f(x)]_i ),
 // where G_n is the transfer map from the gauge of stencil node n into the arrival gauge
@@ -32,6 +39,29 @@ constexpr int STEP_NB = 16;   // nodes per block (lanes per node LPN = 8 or 16 i
                               // the GPU with 8); 16 nodes per block keep small grids spread
                               // evenly over the 152 SMs
 constexpr unsigned STEP_NB_MASK = STEP_NB == 32 ? 0xffffffffu : ((1u << STEP_NB) - 1u);
+constexpr int HALO = 3;       // staged halo width (stencil reach for |v| dt < 1)
+
+// Shared-memory record slot: the first 24 values of a node record (f, g, theta, u, pad,
+// rho, T), padded to a 16-byte multiple that spreads consecutive slots over the banks.
+template <typename R> struct Slot;
+template <> struct Slot<float> { static constexpr int stride = 28, chunks = 6; };
+template <> struct Slot<double> { static constexpr int stride = 26, chunks = 12; };
+
+// Bytes of dynamic shared memory of the step kernel for a tile of tile_x columns.
+__host__ __device__ constexpr int step_tile_slots(int tile_x)
+{
+    return (tile_x + 2 * HALO) * (STEP_NB / tile_x + 2 * HALO);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 template <typename R>
 struct StepShared {
@@ -142,6 +172,26 @@ __device__ __forceinline__ void load_rec24(const double *__restrict__ b, double 
     }
 }
 
+// The same 24 values from a shared-memory slot.
+__device__ __forceinline__ void load_slot24(const float *sl, float v[24])
+{
+    const float4 *q = reinterpret_cast<const float4 *>(sl);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 t = q[k];
+        v[4 * k] = t.x; v[4 * k + 1] = t.y; v[4 * k + 2] = t.z; v[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_slot24(const double *sl, double v[24])
+{
+    const double2 *q = reinterpret_cast<const double2 *>(sl);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 t = q[k];
+        v[2 * k] = t.x; v[2 * k + 1] = t.y;
+    }
+}
+
 // rho and T of node m (adjacent in the record) with one 8- or 16-byte load.
 __device__ __forceinline__ void load_rhoT(const float *__restrict__ in, size_t m, float &r, float &t)
 {
@@ -157,12 +207,9 @@ __device__ __forceinline__ void load_rhoT(const double *__restrict__ in, size_t 
 // Contribution of stencil node `nd` to direction (jx, jy) of the arrival node, in the
 // increment form; fx/gx are the arrival node's own stored populations.
 template <typename R>
-__device__ __forceinline__ void pair_inc(const R *__restrict__ in, size_t nd, int jx, int jy, R th,
-                                         R s, R inv_s, R ux, R uy, const R fx[9], const R gx[9],
-                                         R &tf, R &tg)
+__device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R s, R inv_s, R ux,
+                                         R uy, const R fx[9], const R gx[9], R &tf, R &tg)
 {
-    R v[24];
-    load_rec24(in + nd * SL, v);
     const R thn = v[P_TH];
     const R sn = sqrt_(thn);
     const R qm1 = fdiv_(thn - th, (sn + s) * s);    // (s_n - s)/s without cancellation
@@ -202,14 +249,41 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
     static_assert(LPN == 8 || LPN == 16, "8 or 16 lanes per node");
     constexpr int PPL = 16 / LPN;   // stencil positions per lane and direction
     __shared__ StepShared<R> sh;
+    extern __shared__ __align__(16) unsigned char step_dyn_smem[];
+    R *tile = reinterpret_cast<R *>(step_dyn_smem);
+    constexpr int TS = Slot<R>::stride;
     const TypedParams<R> &q = typed<R>(p);
     const long long N = p.N;
     const int grp = threadIdx.x / LPN, lane = threadIdx.x % LPN;
     const unsigned gmask = (LPN == 8 ? 0xffu : 0xffffu) << (LPN * (grp % (32 / LPN)));
-    const long long n = (long long)blockIdx.x * STEP_NB + grp;
-    const bool valid = n < N;
-    const long long nn = valid ? n : N - 1;   // clamped index for harmless loads
-    const int X = (int)(nn % p.nx), Y = (int)(nn / p.nx);
+    // tile of TX x TY nodes; node grp at (tx, ty) of the tile
+    const int TX = p.tile_x, TY = STEP_NB / TX;
+    const int X0 = (blockIdx.x % p.tiles_x) * TX, Y0 = (blockIdx.x / p.tiles_x) * TY;
+    const int WT = TX + 2 * HALO, HT = TY + 2 * HALO;
+    const int tx = grp % TX, ty = grp / TX;
+    const bool valid = X0 + tx < p.nx && Y0 + ty < p.ny;
+    const int X = min(X0 + tx, p.nx - 1), Y = min(Y0 + ty, p.ny - 1);
+    const long long n = (long long)Y * p.nx + X;
+    // slot of the unwrapped coordinate (u, v) in the staged tile, or -1 outside it
+    auto slot_of = [&](int u, int v) -> int {
+        const int cu = u - (X0 - HALO), cv = v - (Y0 - HALO);
+        return (cu >= 0 && cu < WT && cv >= 0 && cv < HT) ? cv * WT + cu : -1;
+    };
+
+    // ---------------- staging: tile + halo records into shared memory --------------
+    {
+        constexpr int CH = Slot<R>::chunks;
+        const int total = WT * HT * CH;
+        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+            const int sl = idx / CH, ch = idx - sl * CH;
+            const int gxw = bc_wrap(X0 - HALO + sl % WT, p.nx, p.bcx);
+            const int gyw = bc_wrap(Y0 - HALO + sl / WT, p.ny, p.bcy);
+            const R *src = in + ((size_t)gyw * p.nx + gxw) * SL + ch * (16 / sizeof(R));
+            cp_async16(tile + sl * TS + ch * (16 / sizeof(R)), src);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
 
     // ---------------- phase 0: non-local terms, own populations --------------------
     R Fx = 0, Fy = 0, M0 = 0, rEl = 0;
@@ -219,9 +293,9 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         const int l8 = lane & 7;
         const int dir = l8 < 4 ? l8 : l8 + 1;
         const int cx = dir % 3 - 1, cy = dir / 3 - 1;
-        const int mx = bc_wrap(X + cx, p.nx, p.bcx), my = bc_wrap(Y + cy, p.ny, p.bcy);
-        R r0, t0;
-        load_rhoT(in, (size_t)my * p.nx + mx, r0, t0);
+        const int mx = X0 + tx + cx, my = Y0 + ty + cy;   // unwrapped, inside the halo
+        const R *c0 = tile + slot_of(mx, my) * TS;
+        const R r0 = c0[P_RHO], t0 = c0[P_T];
         const R pr0 = r0 * q.R * t0 / (R(1) - q.b * r0) - q.a * r0 * r0;
         // gradients from differences to the centre value (sum_i W_i c_i = 0), which keeps
         // their FP32 rounding proportional to the differences
@@ -230,10 +304,9 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         for (int i = 0; i < 9; ++i) {
             const int ex = i % 3 - 1, ey = i / 3 - 1;
             if (ex == 0 && ey == 0) continue;
-            const size_t m = (size_t)bc_wrap(my + ey, p.ny, p.bcy) * p.nx + bc_wrap(mx + ex, p.nx, p.bcx);
+            const R *cm = tile + slot_of(mx + ex, my + ey) * TS;
             const R w = wst<R>(ex, ey);
-            R r, t;
-            load_rhoT(in, m, r, t);
+            const R r = cm[P_RHO], t = cm[P_T];
             const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
             const R dr = r - r0, dT = t - t0;
             const R dh = q.cv * dT - q.a * dr + (pr / r - pr0 / r0);
@@ -276,20 +349,17 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         }
         rEl = R(0.5) * kap * (gxn * gxn + gyn * gyn);
     }
+    const R *own = tile + slot_of(X0 + tx, Y0 + ty) * TS;
     R fx[9], gx[9];
-    {
-        R v[24];
-        load_rec24(in + (size_t)nn * SL, v);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            fx[i] = v[P_F + i];
-            gx[i] = v[P_G + i];
-        }
+    for (int i = 0; i < 9; ++i) {
+        fx[i] = own[P_F + i];
+        gx[i] = own[P_G + i];
     }
     if (lane == 0) {
-        sh.lam[grp][0] = REC(in, nn, P_TH);
-        sh.lam[grp][1] = REC(in, nn, P_UX);
-        sh.lam[grp][2] = REC(in, nn, P_UY);
+        sh.lam[grp][0] = own[P_TH];
+        sh.lam[grp][1] = own[P_UX];
+        sh.lam[grp][2] = own[P_UY];
         sh.nl[grp][0] = Fx;
         sh.nl[grp][1] = Fy;
         sh.nl[grp][2] = rEl;
@@ -297,17 +367,17 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
     }
     if (threadIdx.x < STEP_NB) {
         // exact FP64 sums of node j's stored populations, one node per lane of warp 0
-        const long long nj = min((long long)blockIdx.x * STEP_NB + threadIdx.x, N - 1);
+        const R *rj = tile + slot_of(X0 + threadIdx.x % TX, Y0 + threadIdx.x / TX) * TS;
         double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double f = (double)REC(in, nj, P_F + i);
+            const double f = (double)rj[P_F + i];
             b0 += f;
             if (i % 3 == 0) b1 -= f;
             if (i % 3 == 2) b1 += f;
             if (i / 3 == 0) b2 -= f;
             if (i / 3 == 2) b2 += f;
-            b3 += (double)REC(in, nj, P_G + i);
+            b3 += (double)rj[P_G + i];
         }
         sh.base[threadIdx.x][0] = b0; sh.base[threadIdx.x][1] = b1;
         sh.base[threadIdx.x][2] = b2; sh.base[threadIdx.x][3] = b3;
@@ -338,14 +408,21 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
                 const int x0 = X + (int)flx - 1, y0 = Y + (int)fly - 1;
                 const R ax = lag1<R>(kk, dx - flx + R(1));
                 const R eta = dy - fly + R(1);
-                const long long xx = bc_wrap(x0 + kk, p.nx, p.bcx);
                 R vf = 0, vg = 0;
 #pragma unroll
                 for (int pp = 0; pp < PPL; ++pp) {
                     const int mm = pp == 0 ? m1 : m2;
-                    const long long nd = (long long)bc_wrap(y0 + mm, p.ny, p.bcy) * p.nx + xx;
+                    const int sl = slot_of(x0 + kk, y0 + mm);
+                    R v[24];
+                    if (sl >= 0) {
+                        load_slot24(tile + sl * TS, v);
+                    } else {
+                        const size_t nd = (size_t)bc_wrap(y0 + mm, p.ny, p.bcy) * p.nx +
+                                          bc_wrap(x0 + kk, p.nx, p.bcx);
+                        load_rec24(in + nd * SL, v);
+                    }
                     R tf, tg;
-                    pair_inc<R>(in, (size_t)nd, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
+                    pair_inc<R>(v, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
                     const R ay = lag1<R>(mm, eta);
                     vf += ay * tf;
                     vg += ay * tg;
@@ -576,7 +653,7 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
     // ---------------- statistics (warp 0, one lane per node) -----------------------
     if (threadIdx.x < STEP_NB) {
         const int j = threadIdx.x;
-        const bool v = (long long)blockIdx.x * STEP_NB + j < N;
+        const bool v = X0 + j % TX < p.nx && Y0 + j / TX < p.ny;
         const R T = sh.mac[j][6], rr = sh.mac[j][0], pr = sh.mac[j][9];
         warp_add(&stats->streams, v ? my_it : 0);
         warp_add(&stats->nonconv, (v && !my_conv) ? 1 : 0);

@@ -44,7 +44,7 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("dt", C.c_double), ("k_cond", C.c_double), ("p_floor", C.c_double),
                 ("stream", C.c_void_p), ("dalloc", _ALLOC), ("dfree", _FREE),
-                ("alloc_ctx", C.c_void_p), ("lanes_per_node", C.c_int32), ("reserved", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("lanes_per_node", C.c_int32), ("tile_x", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -131,7 +131,7 @@ class Simulation:
                  precision: str = "mixed", dt: float = 0.5, tol: float | None = None,
                  max_iter: int = 20, k_cond: float = -1.0, p_floor: float = 1e-3 / 6.0,
                  stream=None, torch_alloc: bool = True, ideal: bool = False,
-                 lanes_per_node: int = 0):
+                 lanes_per_node: int = 0, tile_x: int = 0):
         torch = _torch()
         self._lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -168,11 +168,11 @@ class Simulation:
         eos = Eos(POND_IDEAL if ideal else POND_VDW, a, b, R, delta)
         opts = Opts(POND_MIXED if precision == "mixed" else POND_FP64, max_iter, tol, dt, k_cond,
                     p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None,
-                    lanes_per_node, 0)
+                    lanes_per_node, tile_x)
         self.params = dict(nx=nx, ny=ny, bc_x=bc_x, bc_y=bc_y, a=a, b=b, R=R, delta=delta,
                            kappa=kappa, tau=tau, precision=precision, dt=dt, tol=tol,
                            max_iter=max_iter, k_cond=k_cond, p_floor=p_floor,
-                           lanes_per_node=lanes_per_node)
+                           lanes_per_node=lanes_per_node, tile_x=tile_x)
         ctx = C.c_void_p()
         with torch.cuda.device(self._device):
             st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos), kappa, tau,

@@ -193,3 +193,24 @@ def test_lanes_per_node_variants_match_oracle(pond, lanes, precision):
     got, gstats = gpu_run(pond, w, precision, lanes_per_node=lanes)
     err = rel_linf(got, ref)
     assert max(err.values()) <= TOL[precision], err
+
+
+@pytest.mark.parametrize("tile_x", [1, 2, 4, 8, 16])
+def test_tile_shapes_match_oracle(pond, tile_x):
+    """Every step-kernel tile shape (tile_x x 16/tile_x nodes, staged with a halo of 3)
+    gives the oracle's result, including ragged tiles at the grid edge and departure
+    points beyond the halo (a fast uniform flow, |v| dt > 1)."""
+    w = inputs.droplet(n=37, ny=23, Tr=0.9, radius=6.0, steps=12)
+    P, st, _ = oracle_run(w)
+    ref = oracle.moments(P, st)
+    got, _ = gpu_run(pond, w, "fp64", tile_x=tile_x)
+    err = rel_linf(got, ref)
+    assert max(err.values()) <= TOL["fp64"], err
+    # fast flow: u = 2.6, dt = 0.5 -> departures up to ~1.6 nodes away plus the stencil
+    fast = inputs.slab(nx=30, ny=9, Tr=0.95, steps=6)
+    fast.ux = np.full_like(fast.rho, 2.6)
+    P, st, _ = oracle_run(fast)
+    ref = oracle.moments(P, st)
+    got, _ = gpu_run(pond, fast, "fp64", tile_x=tile_x)
+    err = rel_linf(got, ref)
+    assert max(err.values()) <= TOL["fp64"], err
