@@ -293,7 +293,10 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         const int l8 = lane & 7;
         const int dir = l8 < 4 ? l8 : l8 + 1;
         const int cx = dir % 3 - 1, cy = dir / 3 - 1;
-        const int mx = X0 + tx + cx, my = Y0 + ty + cy;   // unwrapped, inside the halo
+        // the neighbour in unwrapped tile coordinates; a zero-gradient edge clamps it onto
+        // the grid first (its stencil is that of the boundary node itself)
+        const int mx = p.bcx == 0 ? X0 + tx + cx : bc_wrap(X0 + tx + cx, p.nx, 1);
+        const int my = p.bcy == 0 ? Y0 + ty + cy : bc_wrap(Y0 + ty + cy, p.ny, 1);
         const R *c0 = tile + slot_of(mx, my) * TS;
         const R r0 = c0[P_RHO], t0 = c0[P_T];
         const R pr0 = r0 * q.R * t0 / (R(1) - q.b * r0) - q.a * r0 * r0;
