@@ -3,7 +3,7 @@
 // Layout: a state buffer holds one record of SL = 32 values per node (node = y*nx + x),
 // 128 bytes in FP32 so that a node is one cache line and its 21 streamed values are read
 // with six 16-byte loads:
-//   [0..8] f_0..f_8, [9..17] g_0..g_8, [18] theta, [19] u_x, [20] u_y, [21] unused,
+//   [0..8] f_0..f_8, [9..17] g_0..g_8, [18] theta, [19] u_x, [20] u_y, [21] spare,
 //   [22] rho, [23] T, [24] uhat_x, [25] uhat_y, [26..31] unused
 // with population index i = 3*(cy+1) + (cx+1).  R = float (mixed form) or double.
 // The ABI's state planes (f, g, theta, u_x, u_y, rho, T, uhat_x, uhat_y) map to record
@@ -17,8 +17,8 @@ namespace pond {
 
 constexpr int NPL = 25;   // planes of the ABI state
 constexpr int SL = 32;    // values per node record on the device
-enum : int { P_F = 0, P_G = 9, P_TH = 18, P_UX = 19, P_UY = 20, P_RHO = 22, P_T = 23,
-             P_UHX = 24, P_UHY = 25 };
+enum : int { P_F = 0, P_G = 9, P_TH = 18, P_UX = 19, P_UY = 20, P_SQ = 21, P_RHO = 22, P_T = 23,
+             P_UHX = 24, P_UHY = 25 };   // P_SQ: spare value, sqrt(theta) in staged copies
 __host__ __device__ constexpr int rec_off(int plane) { return plane < 21 ? plane : plane + 1; }
 // value `off` of node n's record
 #define REC(buf, n, off) (buf)[(size_t)(n) * SL + (off)]

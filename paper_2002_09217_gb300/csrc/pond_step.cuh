@@ -211,7 +211,7 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
                                          R uy, const R fx[9], const R gx[9], R &tf, R &tg)
 {
     const R thn = v[P_TH];
-    const R sn = sqrt_(thn);
+    const R sn = v[P_SQ];
     const R qm1 = fdiv_(thn - th, (sn + s) * s);    // (s_n - s)/s without cancellation
     const R wx = (v[P_UX] - ux) * inv_s;
     const R wy = (v[P_UY] - uy) * inv_s;
@@ -282,6 +282,10 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
             cp_async16(tile + sl * TS + ch * (16 / sizeof(R)), src);
         }
         cp_async_wait_all();
+        __syncthreads();
+        // sqrt(theta) of every staged node into the slot's spare value, once per step
+        for (int sl = threadIdx.x; sl < WT * HT; sl += blockDim.x)
+            tile[sl * TS + P_SQ] = sqrt_(tile[sl * TS + P_TH]);
         __syncthreads();
     }
 
@@ -402,47 +406,55 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
             const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
             const R s = sqrt_(th), inv_s = R(1) / s;
             R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            // rows of directions (jy) in a rolled loop, the three directions of a row
+            // unrolled so that their transfer coefficients are compile-time selections
 #pragma unroll 1
-            for (int i = 0; i < 9; ++i) {
-                const int jx = i % 3, jy = i / 3;
-                const R dx = -(s * R(jx - 1) + ux) * q.dt;
+            for (int jy = 0; jy < 3; ++jy) {
                 const R dy = -(s * R(jy - 1) + uy) * q.dt;
-                const R flx = floor(dx), fly = floor(dy);
-                const int x0 = X + (int)flx - 1, y0 = Y + (int)fly - 1;
-                const R ax = lag1<R>(kk, dx - flx + R(1));
+                const R fly = floor(dy);
+                const int y0 = Y + (int)fly - 1;
                 const R eta = dy - fly + R(1);
-                R vf = 0, vg = 0;
 #pragma unroll
-                for (int pp = 0; pp < PPL; ++pp) {
-                    const int mm = pp == 0 ? m1 : m2;
-                    const int sl = slot_of(x0 + kk, y0 + mm);
-                    R v[24];
-                    if (sl >= 0) {
-                        load_slot24(tile + sl * TS, v);
-                    } else {
-                        const size_t nd = (size_t)bc_wrap(y0 + mm, p.ny, p.bcy) * p.nx +
-                                          bc_wrap(x0 + kk, p.nx, p.bcx);
-                        load_rec24(in + nd * SL, v);
+                for (int jx = 0; jx < 3; ++jx) {
+                    const int i = 3 * jy + jx;
+                    const R dx = -(s * R(jx - 1) + ux) * q.dt;
+                    const R flx = floor(dx);
+                    const int x0 = X + (int)flx - 1;
+                    const R ax = lag1<R>(kk, dx - flx + R(1));
+                    R vf = 0, vg = 0;
+#pragma unroll
+                    for (int pp = 0; pp < PPL; ++pp) {
+                        const int mm = pp == 0 ? m1 : m2;
+                        const int sl = slot_of(x0 + kk, y0 + mm);
+                        R v[24];
+                        if (sl >= 0) {
+                            load_slot24(tile + sl * TS, v);
+                        } else {
+                            const size_t nd = (size_t)bc_wrap(y0 + mm, p.ny, p.bcy) * p.nx +
+                                              bc_wrap(x0 + kk, p.nx, p.bcx);
+                            load_rec24(in + nd * SL, v);
+                            v[P_SQ] = sqrt_(v[P_TH]);
+                        }
+                        R tf, tg;
+                        pair_inc<R>(v, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
+                        const R ay = lag1<R>(mm, eta);
+                        vf += ay * tf;
+                        vg += ay * tg;
                     }
-                    R tf, tg;
-                    pair_inc<R>(v, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
-                    const R ay = lag1<R>(mm, eta);
-                    vf += ay * tf;
-                    vg += ay * tg;
-                }
-                vf *= ax;
-                vg *= ax;
+                    vf *= ax;
+                    vg *= ax;
 #pragma unroll
-                for (int o = LPN / 2; o > 0; o >>= 1) {
-                    vf += __shfl_xor_sync(gmask, vf, o, LPN);
-                    vg += __shfl_xor_sync(gmask, vg, o, LPN);
+                    for (int o = LPN / 2; o > 0; o >>= 1) {
+                        vf += __shfl_xor_sync(gmask, vf, o, LPN);
+                        vg += __shfl_xor_sync(gmask, vg, o, LPN);
+                    }
+                    if (lane == i) { my_df = vf; my_dg = vg; }
+                    if (i == 8) { my_df8 = vf; my_dg8 = vg; }
+                    a0 += vf;
+                    a1 += vf * R(jx - 1);
+                    a2 += vf * R(jy - 1);
+                    a3 += vg;
                 }
-                if (lane == i) { my_df = vf; my_dg = vg; }
-                if (i == 8) { my_df8 = vf; my_dg8 = vg; }
-                a0 += vf;
-                a1 += vf * R(jx - 1);
-                a2 += vf * R(jy - 1);
-                a3 += vg;
             }
             if (lane == 0) {
                 sh.dsum[grp][0] = a0; sh.dsum[grp][1] = a1; sh.dsum[grp][2] = a2; sh.dsum[grp][3] = a3;
@@ -554,11 +566,11 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
         // moment is 2 rho E to rounding also in FP32 (sum_i W_i (v_x^2 - P/rho - u_x^2) = 0)
         const R Pd = sst * sst * (R(2) * W1[0]);
         const R work = R(2) * (uhxr * Fx + uhyr * Fy);
-        R Xs[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const R cx = R(i % 3 - 1), cy = R(i / 3 - 1);
-            const R w = W1[i % 3] * W1[i / 3];
+        // X*_i for this lane's population(s) only, then gathered across the group
+        auto xstar = [&](int i) -> R {
+            const int ix = i % 3, iy = i / 3;
+            const R cx = R(ix - 1), cy = R(iy - 1);
+            const R w = pick(W1, ix) * pick(W1, iy);
             const R ccx = sst * cx, ccy = sst * cy;                  // v - u* in lambda*
             const R Axx = ccx * ccx + R(2) * ccx * uxr - Pd;          // v v - P/rho I - u u
             const R Axy = ccx * ccy + ccx * uyr + ccy * uxr;
@@ -568,8 +580,14 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
             const R uc = uxr * cx + uyr * cy;
             const R gc = M0 * w * (R(1) + rr * uc * uc / (R(2) * Pr * R(POND_TL))
                                    - rr * (vx * vx + vy * vy) / (R(2) * Pr) + R(1));
-            Xs[i] = om * geq + dtr * (gc + w * work);
-        }
+            return om * geq + dtr * (gc + w * work);
+        };
+        const R my_x = xstar(lane < 9 ? lane : 8);
+        const R my_x8 = xstar(8);
+        R Xs[9];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) Xs[k] = __shfl_sync(gmask, my_x, k, LPN);
+        Xs[8] = LPN > 8 ? __shfl_sync(gmask, my_x, 8, LPN) : my_x8;
         R fo[2] = {R(0), R(0)}, go[2] = {R(0), R(0)};
         constexpr int REPS = (9 + LPN - 1) / LPN;
 #pragma unroll
