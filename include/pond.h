@@ -47,6 +47,7 @@ extern "C" {
 #endif
 
 typedef struct pond_ctx pond_ctx;
+typedef struct pond_batch pond_batch;
 
 typedef enum {
     POND_OK = 0,
@@ -192,6 +193,38 @@ void pond_destroy(pond_ctx *ctx);
 
 /* Last error message of the context (never NULL; "" after success). */
 const char *pond_last_error(const pond_ctx *ctx);
+
+/* ---- Batches: many simulations advanced together -------------------------------
+ * A batch steps all its contexts with one launch of the step kernel per time step and
+ * per group of contexts that share precision and lanes_per_node; the launch walks a
+ * device work-list of (context, tile) pairs, so contexts of different grid sizes and
+ * parameters share it.  Two consecutive steps of every group are captured once in a
+ * CUDA graph (when the batch stream is not the legacy default stream) and replayed.
+ * Per-node arithmetic does not depend on the batch: a context gives the same result
+ * stepped alone or in any batch.  The paper has no counterpart (serving layer).
+ *
+ * stream: cudaStream_t of the batch's work (NULL = legacy default stream, no graphs).
+ * Contexts keep their own streams for everything else; calls on a batched context
+ * wait for the batch's work first.  pond_step on a batched context is POND_EINVAL. */
+pond_status pond_batch_create(void *stream, pond_batch **out);
+
+/* Add an initialised context (same device); waits for the context's queued work. */
+pond_status pond_batch_add(pond_batch *batch, pond_ctx *ctx);
+
+/* Remove a context (waits for the batch's work); the context may be stepped alone again. */
+pond_status pond_batch_remove(pond_batch *batch, pond_ctx *ctx);
+
+/* Advance every context of the batch by n >= 0 steps (asynchronous on the batch stream). */
+pond_status pond_batch_step(pond_batch *batch, int64_t n);
+
+/* Number of contexts in the batch. */
+int32_t pond_batch_size(const pond_batch *batch);
+
+/* Last error message of the batch (never NULL). */
+const char *pond_batch_last_error(const pond_batch *batch);
+
+/* Destroy the batch (its contexts stay valid and leave the batch). */
+void pond_batch_destroy(pond_batch *batch);
 
 /* Library version string. */
 const char *pond_version(void);

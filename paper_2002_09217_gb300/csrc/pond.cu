@@ -22,6 +22,8 @@
 
 using namespace pond;
 
+cudaEvent_t batch_done_event(pond_batch *b);   // defined with the batches below
+
 struct pond_ctx {
     pond_grid grid{};
     pond_eos eos{};
@@ -39,6 +41,7 @@ struct pond_ctx {
     int64_t steps = 0;
     int lanes = 8;                 // lanes per node of the step kernel (8 or 16)
     bool initialised = false;
+    pond_batch *batch = nullptr;   // batch that steps this context, if any
     std::string err;
     size_t bytes = 0;
     DevParams dp{};
@@ -129,6 +132,11 @@ pond_status check_ctx(pond_ctx *c)
     c->err.clear();
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    // work of a batch this context belongs to comes first on the context's stream
+    if (c->batch) {
+        e = cudaStreamWaitEvent(c->stream, batch_done_event(c->batch), 0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamWaitEvent");
+    }
     return POND_OK;
 }
 
@@ -299,6 +307,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
 void pond_destroy(pond_ctx *c)
 {
     if (!c) return;
+    if (c->batch) pond_batch_remove(c->batch, c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
@@ -339,6 +348,7 @@ pond_status pond_step(pond_ctx *c, int64_t n)
     if (st) return st;
     if (n < 0) return fail(c, POND_EINVAL, "negative step count");
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    if (c->batch) return fail(c, POND_EINVAL, "context belongs to a batch: step it with pond_batch_step");
     for (int64_t k = 0; k < n; ++k) {
         if (mixed(c)) launch_step<float>(c);
         else launch_step<double>(c);
@@ -477,6 +487,238 @@ pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
     out->block_streams = (int64_t)hs.block_streams;
     out->max_streams = (int64_t)hs.max_streams;
     return hs.nonfinite ? fail(c, POND_ENAN, "non-finite values in the state") : POND_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many simulations stepped by one launch per (precision, lanes) group and step.
+
+}  // extern "C"
+
+struct pond_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<pond_ctx *> sims;
+    bool dirty = true;
+    int64_t since_build = 0;          // batch steps since the device lists were built
+    cudaEvent_t done = nullptr;       // recorded after every batch step call
+    std::string err;
+    struct Group {
+        int precision = 0, lanes = 8;
+        std::vector<pond_ctx *> sims;
+        void *desc[2] = {nullptr, nullptr};   // SimDesc arrays for even / odd steps
+        int2 *work = nullptr;
+        size_t desc_cap = 0, work_cap = 0;
+        int nwork = 0;
+        size_t smem = 0;
+    };
+    Group g[4];                       // (fp64, mixed) x (8, 16 lanes)
+    cudaGraphExec_t graph = nullptr;  // two steps (even, odd) of every group
+    bool graph_ok = false;
+};
+
+cudaEvent_t batch_done_event(pond_batch *b) { return b->done; }
+
+namespace {
+
+pond_status bfail(pond_batch *b, pond_status st, const std::string &m)
+{
+    b->err = m;
+    return st;
+}
+
+template <typename R>
+size_t step_smem(int tile_x) { return (size_t)step_tile_slots(tile_x) * Slot<R>::stride * sizeof(R); }
+
+template <typename R>
+cudaError_t build_group(pond_batch *b, pond_batch::Group &G)
+{
+    const size_t ns = G.sims.size();
+    std::vector<SimDesc<R>> d0(ns), d1(ns);
+    std::vector<int2> work;
+    G.smem = 0;
+    for (size_t k = 0; k < ns; ++k) {
+        pond_ctx *c = G.sims[k];
+        d0[k].p = c->dp; d0[k].in = (const R *)c->state[c->cur]; d0[k].out = (R *)c->state[1 - c->cur];
+        d0[k].stats = c->dstats;
+        d1[k] = d0[k]; d1[k].in = (const R *)c->state[1 - c->cur]; d1[k].out = (R *)c->state[c->cur];
+        const int ty = STEP_NB / c->dp.tile_x;
+        const int tiles = c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty);
+        for (int t = 0; t < tiles; ++t) work.push_back(make_int2((int)k, t));
+        G.smem = std::max(G.smem, step_smem<R>(c->dp.tile_x));
+    }
+    G.nwork = (int)work.size();
+    cudaError_t e = cudaSuccess;
+    if (ns * sizeof(SimDesc<R>) > G.desc_cap) {
+        for (int k = 0; k < 2; ++k) { cudaFree(G.desc[k]); G.desc[k] = nullptr; }
+        G.desc_cap = 2 * ns * sizeof(SimDesc<R>);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&G.desc[k], G.desc_cap);
+        if (e != cudaSuccess) { G.desc_cap = 0; return e; }
+    }
+    if (work.size() * sizeof(int2) > G.work_cap) {
+        cudaFree(G.work); G.work = nullptr;
+        G.work_cap = 2 * work.size() * sizeof(int2);
+        e = cudaMalloc((void **)&G.work, G.work_cap);
+        if (e != cudaSuccess) { G.work_cap = 0; return e; }
+    }
+    if (ns) {
+        e = cudaMemcpyAsync(G.desc[0], d0.data(), ns * sizeof(SimDesc<R>), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G.desc[1], d1.data(), ns * sizeof(SimDesc<R>), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(G.work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host vectors go out of scope
+    }
+    return e;
+}
+
+template <typename R>
+void launch_group(pond_batch *b, pond_batch::Group &G, int parity)
+{
+    if (!G.nwork) return;
+    const SimDesc<R> *d = (const SimDesc<R> *)G.desc[parity];
+    if (G.lanes == 16)
+        k_pond_step_batch<R, 16><<<G.nwork, STEP_NB * 16, G.smem, b->stream>>>(d, G.work);
+    else
+        k_pond_step_batch<R, 8><<<G.nwork, STEP_NB * 8, G.smem, b->stream>>>(d, G.work);
+}
+
+void launch_all(pond_batch *b, int parity)
+{
+    for (int k = 0; k < 4; ++k) {
+        if (b->g[k].precision == POND_MIXED) launch_group<float>(b, b->g[k], parity);
+        else launch_group<double>(b, b->g[k], parity);
+    }
+}
+
+pond_status batch_build(pond_batch *b)
+{
+    for (int k = 0; k < 4; ++k) {
+        b->g[k].precision = (k & 1) ? POND_MIXED : POND_FP64;
+        b->g[k].lanes = (k & 2) ? 16 : 8;
+        b->g[k].sims.clear();
+    }
+    for (pond_ctx *c : b->sims) {
+        const int k = (c->opts.precision == POND_MIXED ? 1 : 0) | (c->lanes == 16 ? 2 : 0);
+        b->g[k].sims.push_back(c);
+    }
+    for (int k = 0; k < 4; ++k) {
+        cudaError_t e = (k & 1) ? build_group<float>(b, b->g[k]) : build_group<double>(b, b->g[k]);
+        if (e != cudaSuccess) return bfail(b, POND_ECUDA, std::string("batch build: ") + cudaGetErrorString(e));
+    }
+    if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+    b->graph_ok = false;
+    // capture two steps (even then odd parity) of every group once; replays step the batch
+    if (b->stream) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            launch_all(b, 0);
+            launch_all(b, 1);
+            cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+            if (e == cudaSuccess && graph && cudaGraphInstantiate(&b->graph, graph, 0) == cudaSuccess)
+                b->graph_ok = true;
+            if (graph) cudaGraphDestroy(graph);
+        }
+        cudaGetLastError();   // a failed capture falls back to plain launches
+    }
+    b->dirty = false;
+    b->since_build = 0;
+    return POND_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pond_status pond_batch_create(void *stream, pond_batch **out)
+{
+    if (!out) return POND_EINVAL;
+    *out = nullptr;
+    pond_batch *b = new pond_batch();
+    b->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&b->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+        delete b;
+        return POND_ECUDA;
+    }
+    *out = b;
+    return POND_OK;
+}
+
+pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
+{
+    if (!b || !c) return POND_EINVAL;
+    b->err.clear();
+    if (c->batch) return bfail(b, POND_EINVAL, "context already belongs to a batch");
+    if (!c->initialised) return bfail(b, POND_EINVAL, "context state not initialised");
+    if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
+    // the context's queued work (its initialisation) completes before the batch uses it
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaStreamSynchronize");
+    b->sims.push_back(c);
+    c->batch = b;
+    b->dirty = true;
+    return POND_OK;
+}
+
+pond_status pond_batch_remove(pond_batch *b, pond_ctx *c)
+{
+    if (!b || !c) return POND_EINVAL;
+    auto it = std::find(b->sims.begin(), b->sims.end(), c);
+    if (it == b->sims.end()) return bfail(b, POND_EINVAL, "context is not in this batch");
+    cudaSetDevice(b->device);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaStreamSynchronize");
+    b->sims.erase(it);
+    c->batch = nullptr;
+    b->dirty = true;
+    return POND_OK;
+}
+
+int32_t pond_batch_size(const pond_batch *b) { return b ? (int32_t)b->sims.size() : 0; }
+
+pond_status pond_batch_step(pond_batch *b, int64_t n)
+{
+    if (!b) return POND_EINVAL;
+    b->err.clear();
+    if (n < 0) return bfail(b, POND_EINVAL, "negative step count");
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
+    if (b->sims.empty() || n == 0) return POND_OK;
+    if (b->dirty) {
+        pond_status st = batch_build(b);
+        if (st) return st;
+    }
+    int64_t k = 0;
+    // whole graph replays when the next step is an even one
+    if (b->graph_ok && (b->since_build % 2) == 0)
+        for (; k + 2 <= n; k += 2)
+            if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess)
+                return bfail(b, POND_ECUDA, "cudaGraphLaunch");
+    for (; k < n; ++k) launch_all(b, (int)((b->since_build + k) % 2));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bfail(b, POND_ECUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    b->since_build += n;
+    for (pond_ctx *c : b->sims) {
+        if (n % 2) c->cur = 1 - c->cur;
+        c->steps += n;
+    }
+    if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaEventRecord");
+    return POND_OK;
+}
+
+const char *pond_batch_last_error(const pond_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+void pond_batch_destroy(pond_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    for (pond_ctx *c : b->sims) c->batch = nullptr;
+    for (auto &G : b->g) {
+        for (int k = 0; k < 2; ++k) cudaFree(G.desc[k]);
+        cudaFree(G.work);
+    }
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    cudaEventDestroy(b->done);
+    delete b;
 }
 
 }  // extern "C"

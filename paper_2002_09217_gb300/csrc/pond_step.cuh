@@ -242,9 +242,10 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
     tg = sg;
 }
 
+// One time step of one tile (block) of a simulation: the body of both step kernels.
 template <typename R, int LPN>
-__global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R *__restrict__ in,
-                                                             R *__restrict__ out, DevStats *stats)
+__device__ __forceinline__ void step_tile(const DevParams &p, const R *__restrict__ in,
+                                          R *__restrict__ out, DevStats *stats, int tile_idx)
 {
     static_assert(LPN == 8 || LPN == 16, "8 or 16 lanes per node");
     constexpr int PPL = 16 / LPN;   // stencil positions per lane and direction
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
     const unsigned gmask = (LPN == 8 ? 0xffu : 0xffffu) << (LPN * (grp % (32 / LPN)));
     // tile of TX x TY nodes; node grp at (tx, ty) of the tile
     const int TX = p.tile_x, TY = STEP_NB / TX;
-    const int X0 = (blockIdx.x % p.tiles_x) * TX, Y0 = (blockIdx.x / p.tiles_x) * TY;
+    const int X0 = (tile_idx % p.tiles_x) * TX, Y0 = (tile_idx / p.tiles_x) * TY;
     const int WT = TX + 2 * HALO, HT = TY + 2 * HALO;
     const int tx = grp % TX, ty = grp / TX;
     const bool valid = X0 + tx < p.nx && Y0 + ty < p.ny;
@@ -687,6 +688,45 @@ __global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R
             atomicMax(&stats->max_streams, (unsigned long long)it);
         }
     }
+}
+
+// One time step of one simulation: one block per tile.
+template <typename R, int LPN>
+__global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R *__restrict__ in,
+                                                             R *__restrict__ out, DevStats *stats)
+{
+    step_tile<R, LPN>(p, in, out, stats, blockIdx.x);
+}
+
+// A simulation of a batch as one launch sees it: parameters, the buffers this step reads
+// and writes, and its counters.
+template <typename R>
+struct SimDesc {
+    DevParams p;
+    const R *in;
+    R *out;
+    DevStats *stats;
+};
+
+// One time step of every simulation of a batch in one launch: block b steps tile
+// work[b].y of simulation work[b].x (a device work-list of (simulation, tile) pairs).
+template <typename R, int LPN>
+__global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step_batch(const SimDesc<R> *__restrict__ descs,
+                                                                   const int2 *__restrict__ work)
+{
+    __shared__ DevParams sp;
+    __shared__ const R *s_in;
+    __shared__ R *s_out;
+    __shared__ DevStats *s_stats;
+    const int2 w = work[blockIdx.x];
+    if (threadIdx.x == 0) {
+        sp = descs[w.x].p;
+        s_in = descs[w.x].in;
+        s_out = descs[w.x].out;
+        s_stats = descs[w.x].stats;
+    }
+    __syncthreads();
+    step_tile<R, LPN>(sp, s_in, s_out, s_stats, w.y);
 }
 
 }  // namespace pond

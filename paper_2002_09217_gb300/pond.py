@@ -103,6 +103,19 @@ def load() -> C.CDLL:
         lib.pond_version.restype = C.c_char_p
         lib.pond_conservation_noalloc.argtypes = [C.c_void_p, C.c_int64, dp, C.c_void_p]
         lib.pond_conservation_noalloc.restype = C.c_int
+        lib.pond_batch_create.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
+        lib.pond_batch_create.restype = C.c_int
+        for name in ("pond_batch_add", "pond_batch_remove"):
+            getattr(lib, name).argtypes = [C.c_void_p, C.c_void_p]
+            getattr(lib, name).restype = C.c_int
+        lib.pond_batch_step.argtypes = [C.c_void_p, C.c_int64]
+        lib.pond_batch_step.restype = C.c_int
+        lib.pond_batch_size.argtypes = [C.c_void_p]
+        lib.pond_batch_size.restype = C.c_int32
+        lib.pond_batch_last_error.argtypes = [C.c_void_p]
+        lib.pond_batch_last_error.restype = C.c_char_p
+        lib.pond_batch_destroy.argtypes = [C.c_void_p]
+        lib.pond_batch_destroy.restype = None
         _lib = lib
         return lib
 
@@ -277,6 +290,55 @@ def conservation_noalloc(d_planes, n_nodes: int, stream=None) -> np.ndarray:
     if st != 0:
         raise PondError(st, "pond_conservation_noalloc failed")
     return out
+
+
+class Batch:
+    """Many simulations advanced together, one launch per time step and kernel group
+    (see pond_batch_* in pond.h).  Simulations keep their own API for init/moments."""
+
+    def __init__(self, stream=None):
+        torch = _torch()
+        self._lib = load()
+        self._stream = stream if stream is not None else torch.cuda.Stream()
+        h = C.c_void_p()
+        st = self._lib.pond_batch_create(C.c_void_p(self._stream.cuda_stream), C.byref(h))
+        if st != 0:
+            raise PondError(st, "pond_batch_create failed")
+        self._h = h
+        self.members = []
+
+    def _check(self, st):
+        if st != 0:
+            raise PondError(st, self._lib.pond_batch_last_error(self._h).decode())
+
+    def add(self, sim: Simulation):
+        self._check(self._lib.pond_batch_add(self._h, sim._ctx))
+        self.members.append(sim)
+
+    def remove(self, sim: Simulation):
+        self._check(self._lib.pond_batch_remove(self._h, sim._ctx))
+        self.members.remove(sim)
+
+    def step(self, n: int = 1):
+        self._check(self._lib.pond_batch_step(self._h, int(n)))
+
+    def synchronize(self):
+        self._stream.synchronize()
+
+    def __len__(self):
+        return int(self._lib.pond_batch_size(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pond_batch_destroy(self._h)
+            self._h = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def from_workload(w, precision: str = "mixed", **kw) -> Simulation:

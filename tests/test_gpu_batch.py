@@ -1,0 +1,100 @@
+"""Batched stepping and the continuous-batching server: every simulation's result must be
+the same stepped alone or inside a batch whose membership changes while it runs."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from paper_2002_09217_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pond():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2002_09217_gb300 import pond as mod
+    mod.load()
+    return mod
+
+
+def _cases():
+    return [
+        (inputs.droplet(n=40, ny=36, Tr=0.9, radius=8.0), "mixed", {}),
+        (inputs.slab(nx=64, ny=5, Tr=0.9), "mixed", {"lanes_per_node": 16}),
+        (inputs.shock_in_vapour(n=32, Tr=0.8, Mach=1.5), "fp64", {}),
+        (inputs.shock_tube(nx=96, ny=3, width=2.0), "mixed", {"tile_x": 8}),
+        (inputs.droplet(n=24, ny=20, Tr=0.85, radius=5.0), "fp64", {"tile_x": 16}),
+    ]
+
+
+def _alone(pond, w, prec, kw, steps):
+    with pond.from_workload(w, precision=prec, **kw) as sim:
+        sim.init_fields(*w.fields())
+        sim.step(steps)
+        return sim.moments()
+
+
+def test_batch_with_changing_membership_equals_alone(pond):
+    cases = _cases()
+    batch = pond.Batch()
+    sims = []
+    for w, prec, kw in cases:
+        s = pond.from_workload(w, precision=prec, **kw)
+        s.init_fields(*w.fields())
+        sims.append(s)
+    steps = [0] * len(cases)
+    # join two, step, join the rest, step, let one leave, step, let it come back, step
+    for k in (0, 1):
+        batch.add(sims[k])
+    batch.step(7)
+    for k in (0, 1):
+        steps[k] += 7
+    for k in (2, 3, 4):
+        batch.add(sims[k])
+    batch.step(5)
+    for k in range(5):
+        steps[k] += 5
+    batch.remove(sims[1])
+    batch.step(4)
+    for k in (0, 2, 3, 4):
+        steps[k] += 4
+    batch.add(sims[1])
+    batch.step(3)
+    for k in range(5):
+        steps[k] += 3
+    batch.synchronize()
+    with pytest.raises(pond.PondError):
+        sims[0].step(1)          # a batched context is stepped by its batch only
+    for (w, prec, kw), sim, n in zip(cases, sims, steps):
+        got = sim.moments()
+        ref = _alone(pond, w, prec, kw, n)
+        for key in ref:
+            np.testing.assert_array_equal(got[key], ref[key], err_msg="%s %s" % (w.name, key))
+    batch.close()
+    for s in sims:
+        s.close()
+
+
+def test_serving_results_equal_alone(pond):
+    from paper_2002_09217_gb300 import serving
+    reqs = inputs.serving_requests(n=10, rate=200.0, seed=77)
+    # small and short requests so that the FP64 ones finish quickly
+    reqs = [dataclasses.replace(r, side=min(r.side, 48), steps=20 + (r.steps % 40),
+                                T_r=max(r.T_r, 0.8)) for r in reqs]
+    server = serving.Server(hbm_budget=64 << 20, chunk=7)
+    results = server.run(reqs)
+    server.close()
+    assert sorted(r.rid for r in results) == [r.rid for r in reqs]
+    by_id = {r.rid: r for r in reqs}
+    for res in results:
+        req = by_id[res.rid]
+        w = inputs.request_workload(req)
+        ref = _alone(pond, w, req.precision, {}, req.steps)
+        for key in ref:
+            np.testing.assert_array_equal(res.fields[key], ref[key], err_msg="request %d %s" % (res.rid, key))
+        assert res.latency >= 0.0
+    summary = serving.summarize(results, max(r.completed for r in results))
+    assert summary["requests"] == len(reqs) and summary["p99_latency_s"] >= summary["p50_latency_s"]
