@@ -2,19 +2,20 @@
 
 Workload (default): the supercritical real-gas shock tube, 2048 x 4 nodes,
 T = 1.1 T_cr, density ratio 4 with a tanh step of width 4, zero-gradient ends in x.
-One bench "step" = one time step of the whole hot path (non-local terms, frame
-search with streaming, collision) over the grid.  Metric: MLUPS (million node
-updates per second) in the mixed FP32/FP64 form; the plain FP64 form is reported
-beside it.
+One bench "step" = one time step of the whole hot path (non-local terms, frame search
+with streaming, collision: one launch of the fused step kernel) over the grid.
+Metric: MLUPS (million node updates per second) in the mixed FP32/FP64 form; the plain
+FP64 form, a bounded continuous-batching serving sample and the FP64 CPU oracle are
+reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--impl reference] [--no-cpu]
+                  [--impl reference] [--no-cpu] [--no-serving] [--no-autotune]
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the
-simulation's stream, with the L2 flushed (a 512 MiB buffer written) between timed
-steps because the state (a few MB) is far smaller than L2.  Under torchrun (N > 1)
-each rank runs an independent replica (the workload does not shard) and the
-slowest rank's time counts.
+simulation's stream, with the L2 flushed (a 512 MiB buffer written) between timed steps
+because the state (about 1 MB) is far smaller than L2.  The launch shape (lanes per node,
+tile shape) comes from the autotuner.  Under torchrun (N > 1) each rank runs an
+independent replica (the workload does not shard) and the slowest rank's time counts.
 """
 from __future__ import annotations
 
@@ -118,20 +119,22 @@ def bytes_per_update(precision: str) -> int:
     return 48 * (4 if precision == "mixed" else 8)
 
 
+# Algorithmic FLOPs of the step kernel's formula, per node update:
+#  per stencil pair (9 directions x 16 stencil nodes per stream): gauge offsets (9),
+#  6 transfer-map increments (4 each), f and g increment components (2 x 57), Lagrange
+#  weight and accumulation (10) => 157; per direction: departure point and basis (20);
+#  per stream: moments and residual (60); per node update: collision (~1000).
+FLOPS_PAIR = 157
+FLOPS_DIR = 20
+FLOPS_STREAM_EXTRA = 60
+FLOPS_COLLIDE = 1000
+
+
 def flops_per_stream() -> int:
-    """Algorithmic FLOPs of one streaming pass of one node (the kernel's formula):
-    per direction: departure point + two cubic Lagrange bases (24), and per stencil
-    node: sqrt(theta_n) + 6 transfer coefficients (4 each) + f and g components
-    (2 x (9 + 3) FMA) + 2 interpolation FMA => 16 x (1 + 24 + 48 + 4) = 1232."""
-    return 9 * (24 + 16 * (1 + 24 + 48 + 4))
-
-
-FLOPS_PER_ITER_EXTRA = 60        # moments and residual per frame-search pass
-FLOPS_COLLIDE = 700              # equilibria, sources and the 3x3 (x) 3x3 map of g
+    return 9 * (FLOPS_DIR + 16 * FLOPS_PAIR) + FLOPS_STREAM_EXTRA
 
 
 def oracle_mlups(w, steps: int) -> dict:
-    import numpy as np  # noqa: F401
     import oracle
     P = oracle.Params(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R,
                       delta=w.delta, kappa=w.kappa, tau=w.tau, dt=w.dt, k_cond=w.k_cond,
@@ -147,6 +150,114 @@ def oracle_mlups(w, steps: int) -> dict:
                       % (steps, w.nx, w.ny), "state": st, "params": P}
 
 
+def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws):
+    """Timed steps of one precision form: per-step CUDA events, L2 flushed between."""
+    sim = pond.from_workload(w, precision=precision, stream=stream, **shape)
+    dev_fields = [torch.tensor(a, device=stream.device, dtype=torch.float64) for a in w.fields()]
+    with torch.cuda.stream(stream):
+        sim.init_fields(*dev_fields)
+        sim.step(warmup)
+    stream.synchronize()
+    sim.stats(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            evs[k][0].record(stream)
+            sim.step(1)
+            evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    st = sim.stats()
+    # the kernel alone, timed by the library with events around its launch
+    kms = 0.0
+    reps = min(steps, 50)
+    for k in range(reps):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+        kms += sim.step_timed() / reps
+    sim.close()
+    return ms, st, kms
+
+
+def roofline(w, precision, its, kernel_ms, pk):
+    fl = its * flops_per_stream() + FLOPS_COLLIDE
+    achieved = w.nodes * fl / (kernel_ms * 1e-3) / 1e12
+    peak = alu_peak_tflops(precision, pk["sm_max_mhz"])
+    return {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_src": "%s: 152 SM x 128 lanes x 2 flop x %.0f MHz%s" % (
+                "FP32" if precision == "mixed" else "FP64", pk["sm_max_mhz"],
+                "" if precision == "mixed" else " / 64"),
+            "flops_per_update": fl, "kernel_ms": kernel_ms}
+
+
+def end_to_end(w, pond, torch, stream, precision, shape, n_seg: int, reps: int) -> dict:
+    import numpy as np
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.fields()]
+    sim = pond.from_workload(w, precision=precision, stream=stream, **shape)
+    times = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.init_fields(*[h.numpy() for h in host])
+        sim.step(n_seg)
+        sim.moments()
+        times.append(time.perf_counter() - t0)
+    sim.close()
+    t = statistics.median(times[1:])
+    return {"value": w.nodes * n_seg / t / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": 4 * w.nodes * 8 / n_seg, "d2h_bytes_per_step": 5 * w.nodes * 8 / n_seg,
+            "segment_steps": n_seg,
+            "note": "per call: init from pinned host (4 fields), %d steps, 5 fields back to host" % n_seg}
+
+
+def serving_sample(torch, n_req: int = 32) -> dict:
+    """Bounded sample of the serving workload: the seeded request mix with sides capped
+    at 256, step counts scaled by 1/10 and two-phase temperatures at or above 0.8 T_cr,
+    arrivals at 200 requests/s, device budget 8 GiB, served by the batching server."""
+    import dataclasses
+    from paper_2002_09217_gb300 import inputs, serving
+    reqs = inputs.serving_requests(n=n_req, rate=200.0)
+    reqs = [dataclasses.replace(r, side=min(r.side, 256), steps=max(100, r.steps // 10),
+                                T_r=max(r.T_r, 0.8)) for r in reqs]
+    server = serving.Server(hbm_budget=8 << 30, chunk=50, keep_fields=False)
+    t0 = time.perf_counter()
+    results = server.run(reqs)
+    wall = time.perf_counter() - t0
+    server.close()
+    summ = serving.summarize(results, wall)
+    summ["nonfinite_requests"] = sum(1 for r in results if r.status.get("nonfinite", 0))
+    summ["sample"] = ("%d requests of the seeded mix, side <= 256, steps/10, T_r >= 0.8, "
+                      "mixed and FP64 50/50, Poisson 200/s, 8 GiB budget" % n_req)
+    return summ
+
+
+def parity_vs_oracle(w, pond, stream, precision, shape, res, steps) -> dict:
+    import numpy as np
+    import oracle
+    ref = oracle.moments(res["params"], res["state"])
+    sim = pond.from_workload(w, precision=precision, stream=stream, **shape)
+    sim.init_fields(*w.fields())
+    sim.step(steps)
+    got = sim.moments()
+    sim.close()
+    out = {}
+    cs = float(np.sqrt(np.max(np.abs(ref["p"] / ref["rho"]))))
+    for k in ("rho", "ux", "uy", "T", "p"):
+        scale = np.abs(ref[k]).max()
+        if k in ("ux", "uy"):
+            scale = max(scale, cs)
+        out[k] = float(np.abs(got[k] - ref[k]).max() / scale)
+    out["steps"] = steps
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -156,6 +267,8 @@ def main():
     ap.add_argument("--workload", default="shocktube2048x4")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -185,40 +298,24 @@ def main():
             dist.destroy_process_group()
         return
 
-    from paper_2002_09217_gb300 import pond
+    from paper_2002_09217_gb300 import autotune, pond
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    pk = peaks()
 
-    def timed_run(precision: str, steps: int, warmup: int):
-        sim = pond.from_workload(w, precision=precision, stream=stream)
-        dev_fields = [torch.tensor(a, device=dev, dtype=torch.float64) for a in w.fields()]
-        with torch.cuda.stream(stream):
-            sim.init_fields(*dev_fields)
-            sim.step(warmup)
-        stream.synchronize()
-        sim.stats(reset=True)
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(steps)]
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-        with torch.cuda.stream(stream):
-            for k in range(steps):
-                flush.fill_(float(k))
-                evs[k][0].record(stream)
-                sim.step(1)
-                evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        st = sim.stats()
-        return sim, ms, st
+    def shape_for(prec):
+        if args.no_autotune:
+            return {}
+        best = autotune.tune(w, prec, stream=stream)
+        return {"lanes_per_node": best["lanes_per_node"], "tile_x": best["tile_x"]}
 
+    shape = shape_for(args.precision)
     clocks = ClockSampler(local)
     with clocks:
-        sim, ms, st = timed_run(args.precision, args.steps, args.warmup)
+        ms, st, kms = run_form(w, pond, torch, stream, flush, args.precision, args.steps,
+                               args.warmup, shape, ws)
     total_ms = sum(ms)
     if ws > 1:
         import torch.distributed as dist
@@ -228,107 +325,50 @@ def main():
     value = ws * w.nodes * args.steps / (total_ms * 1e-3) / 1e6
     its = st["streams"] / max(1, w.nodes * args.steps)
 
-    # per-kernel time of the dominant kernel (k_step) from events around one launch:
-    # the step is 3 launches; time the frame-search kernel alone via a second sim call
-    kstep_ms = kernel_time(sim, flush, stream, torch, reps=min(args.steps, 50))
-
-    # end to end through the public API with host buffers: init from pinned host arrays,
-    # n_seg time steps, moments back to host, per call
-    e2e = end_to_end(w, pond, torch, stream, args.precision, n_seg=100, reps=5)
-
-    pk = peaks()
-    sm_mhz = clocks.summary().get("sm_mhz") or pk["sm_max_mhz"]
-    fl_update = its * (flops_per_stream() + FLOPS_PER_ITER_EXTRA) + FLOPS_COLLIDE
-    achieved_tf = w.nodes * fl_update / (kstep_ms * 1e-3) / 1e12
-    peak_tf = alu_peak_tflops(args.precision, pk["sm_max_mhz"])
-
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt, "precision": args.precision,
+                   "launch_shape": shape or "default",
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "frame_search_streams_per_node": its,
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved_tf, "peak": peak_tf,
-                     "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
-                     "peak_src": "FP32 %s: 152 SM x 128 lanes x 2 x %.0f MHz" % (
-                         "" if args.precision == "mixed" else "/64 (FP64)", pk["sm_max_mhz"]),
-                     "flops_per_update": fl_update, "kernel_ms": kstep_ms},
+        "roofline": roofline(w, args.precision, its, kms, pk),
         "hbm": {"bytes_per_update": bytes_per_update(args.precision),
-                "achieved_gbs": value * 1e6 * bytes_per_update(args.precision) / 1e9,
+                "achieved_gbs": value / ws * 1e6 * bytes_per_update(args.precision) / 1e9,
                 "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
         "clocks": clocks.summary(),
-        "e2e": e2e,
     }
+    line["e2e"] = end_to_end(w, pond, torch, stream, args.precision, shape, n_seg=100, reps=5)
+
+    if args.precision == "mixed":
+        # the plain FP64 form of the same workload (fewer steps: the FP64 pipes are 1/64)
+        shape64 = shape_for("fp64")
+        ms64, st64, kms64 = run_form(w, pond, torch, stream, flush, "fp64", 30, 3, shape64, 1)
+        its64 = st64["streams"] / max(1, w.nodes * 30)
+        line["fp64"] = {"value": w.nodes * 30 / (sum(ms64) * 1e-3) / 1e6, "unit": "MLUPS",
+                        "ms_per_step": sum(ms64) / 30, "launch_shape": shape64 or "default",
+                        "frame_search_streams_per_node": its64,
+                        "roofline": roofline(w, "fp64", its64, kms64, pk)}
+
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_sample(torch)
+
     if rank == 0 and not args.no_cpu:
         cpu_steps = args.cpu_steps or max(1, min(40, int(3e5 // w.nodes)))
         res = oracle_mlups(w, cpu_steps)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        # parity of this run's GPU path against the oracle sample (same steps, fresh start)
-        line["linf_vs_oracle"] = parity_vs_oracle(w, pond, torch, stream, args.precision, res, cpu_steps + 1)
-    sim.close()
+        # this run's GPU path against the oracle sample (same steps from the same start)
+        line["linf_vs_oracle"] = parity_vs_oracle(w, pond, stream, args.precision, shape, res,
+                                                  cpu_steps + 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def kernel_time(sim, flush, stream, torch, reps: int) -> float:
-    """Average duration of the fused step kernel, timed by the library itself with CUDA
-    events on the context stream, L2 flushed before each launch."""
-    acc = 0.0
-    for k in range(reps):
-        with torch.cuda.stream(stream):
-            flush.fill_(float(k))
-        acc += sim.step_timed() / reps
-    return acc
-
-
-def end_to_end(w, pond, torch, stream, precision, n_seg: int, reps: int) -> dict:
-    import numpy as np
-    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in w.fields()]
-    outs = {k: torch.empty((w.ny, w.nx), dtype=torch.float64).pin_memory() for k in ("rho", "ux", "uy", "T", "p")}
-    sim = pond.from_workload(w, precision=precision, stream=stream)
-    times = []
-    for r in range(reps + 1):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sim.init_fields(*[h.numpy() for h in host])
-        sim.step(n_seg)
-        m = sim.moments()
-        for k in outs:
-            outs[k].numpy()[...] = m[k]
-        times.append(time.perf_counter() - t0)
-    sim.close()
-    t = statistics.median(times[1:])
-    return {"value": w.nodes * n_seg / t / 1e6, "unit": "MLUPS",
-            "h2d_bytes_per_step": 4 * w.nodes * 8 / n_seg, "d2h_bytes_per_step": 5 * w.nodes * 8 / n_seg,
-            "segment_steps": n_seg,
-            "note": "per call: init from pinned host (4 fields), %d steps, 5 fields back to host" % n_seg}
-
-
-def parity_vs_oracle(w, pond, torch, stream, precision, res, steps) -> dict:
-    import numpy as np
-    import oracle
-    ref = oracle.moments(res["params"], res["state"])
-    sim = pond.from_workload(w, precision=precision, stream=stream)
-    sim.init_fields(*w.fields())
-    sim.step(steps)
-    got = sim.moments()
-    sim.close()
-    out = {}
-    cs = float(np.sqrt(np.max(np.abs(ref["p"] / ref["rho"]))))
-    for k in ("rho", "ux", "uy", "T", "p"):
-        scale = np.abs(ref[k]).max()
-        if k in ("ux", "uy"):
-            scale = max(scale, cs)
-        out[k] = float(np.abs(got[k] - ref[k]).max() / scale)
-    out["steps"] = steps
-    return out
 
 
 if __name__ == "__main__":
