@@ -217,20 +217,28 @@ def end_to_end(w, pond, torch, stream, precision, shape, n_seg: int, reps: int) 
             "note": "per call: init from pinned host (4 fields), %d steps, 5 fields back to host" % n_seg}
 
 
-def serving_sample(torch, n_req: int = 32) -> dict:
+def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
     """Bounded sample of the serving workload: the seeded request mix with sides capped
     at 256, step counts scaled by 1/10 and two-phase temperatures at or above 0.8 T_cr,
-    arrivals at 200 requests/s, device budget 8 GiB, served by the batching server."""
+    arrivals at 200 requests/s, device budget 8 GiB per GPU, served by the batching
+    server; with several ranks each serves its placement share (no data exchange)."""
     import dataclasses
-    from paper_2002_09217_gb300 import inputs, serving
+    from paper_2002_09217_gb300 import inputs, placement, serving
     reqs = inputs.serving_requests(n=n_req, rate=200.0)
     reqs = [dataclasses.replace(r, side=min(r.side, 256), steps=max(100, r.steps // 10),
                                 T_r=max(r.T_r, 0.8)) for r in reqs]
+    mine = placement.my_share(reqs, rank, ws) if ws > 1 else reqs
     server = serving.Server(hbm_budget=8 << 30, chunk=50, keep_fields=False)
     t0 = time.perf_counter()
-    results = server.run(reqs)
+    results = server.run(mine)
     wall = time.perf_counter() - t0
     server.close()
+    if ws > 1:
+        import torch.distributed as dist
+        gathered = [None] * ws
+        dist.all_gather_object(gathered, (results, wall))
+        results = [r for part, _ in gathered for r in part]
+        wall = max(w for _, w in gathered)
     summ = serving.summarize(results, wall)
     summ["nonfinite_requests"] = sum(1 for r in results if r.status.get("nonfinite", 0))
     summ["sample"] = ("%d requests of the seeded mix, side <= 256, steps/10, T_r >= 0.8, "
@@ -354,8 +362,10 @@ def main():
                         "frame_search_streams_per_node": its64,
                         "roofline": roofline(w, "fp64", its64, kms64, pk)}
 
-    if rank == 0 and not args.no_serving:
-        line["serving"] = serving_sample(torch)
+    if not args.no_serving:
+        serv = serving_sample(torch, rank, ws)
+        if rank == 0:
+            line["serving"] = serv
 
     if rank == 0 and not args.no_cpu:
         cpu_steps = args.cpu_steps or max(1, min(40, int(3e5 // w.nodes)))
