@@ -96,7 +96,7 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
     R *out = (R *)c->state[1 - c->cur];
     const int tx = c->dp.tile_x, ty = STEP_NB / tx;
     const unsigned nb = (unsigned)(c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty));
-    const size_t smem = (size_t)step_tile_slots(tx) * Slot<R>::stride * sizeof(R);
+    const size_t smem = (size_t)step_tile_slots(tx, Slot<R>::stride) * Slot<R>::stride * sizeof(R);
     if (ev) cudaEventRecord(ev[0], c->stream);
     if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats);
     else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats);
@@ -527,7 +527,10 @@ pond_status bfail(pond_batch *b, pond_status st, const std::string &m)
 }
 
 template <typename R>
-size_t step_smem(int tile_x) { return (size_t)step_tile_slots(tile_x) * Slot<R>::stride * sizeof(R); }
+size_t step_smem(int tile_x)
+{
+    return (size_t)step_tile_slots(tile_x, Slot<R>::stride) * Slot<R>::stride * sizeof(R);
+}
 
 template <typename R>
 cudaError_t build_group(pond_batch *b, pond_batch::Group &G)

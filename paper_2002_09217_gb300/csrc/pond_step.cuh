@@ -40,6 +40,9 @@ constexpr int STEP_NB = 16;   // nodes per block (lanes per node LPN = 8 or 16 i
                               // evenly over the 152 SMs
 constexpr unsigned STEP_NB_MASK = STEP_NB == 32 ? 0xffffffffu : ((1u << STEP_NB) - 1u);
 constexpr int HALO = 3;       // staged halo width (stencil reach for |v| dt < 1)
+// resident blocks per SM the register budget is sized for (about 96 registers per thread
+// with 8 lanes per node, a few spilled values; 16 lanes keep their registers)
+#define STEP_MIN_BLOCKS(LPN) ((LPN) == 8 ? 5 : 2)
 
 // Shared-memory record slot: the first 24 values of a node record (f, g, theta, u, pad,
 // rho, T), padded to a 16-byte multiple that spreads consecutive slots over the banks.
@@ -47,10 +50,18 @@ template <typename R> struct Slot;
 template <> struct Slot<float> { static constexpr int stride = 28, chunks = 6; };
 template <> struct Slot<double> { static constexpr int stride = 26, chunks = 12; };
 
-// Bytes of dynamic shared memory of the step kernel for a tile of tile_x columns.
-__host__ __device__ constexpr int step_tile_slots(int tile_x)
+// Slots per staged row: the tile width plus halos, rounded up (FP32 slots of 28 words) to
+// 4 mod 8 so that vertically adjacent slots start 16 banks apart and the two stencil rows
+// a lane group reads fall on disjoint banks.
+__host__ __device__ constexpr int step_row_pitch(int tile_x, int slot_words)
 {
-    return (tile_x + 2 * HALO) * (STEP_NB / tile_x + 2 * HALO);
+    return slot_words == 28 ? ((tile_x + 2 * HALO + 3) / 8) * 8 + 4 : tile_x + 2 * HALO;
+}
+
+// Slots of the step kernel's staged tile (tile_x columns).
+__host__ __device__ constexpr int step_tile_slots(int tile_x, int slot_words)
+{
+    return step_row_pitch(tile_x, slot_words) * (STEP_NB / tile_x + 2 * HALO);
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -261,6 +272,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     const int TX = p.tile_x, TY = STEP_NB / TX;
     const int X0 = (tile_idx % p.tiles_x) * TX, Y0 = (tile_idx / p.tiles_x) * TY;
     const int WT = TX + 2 * HALO, HT = TY + 2 * HALO;
+    const int PT = step_row_pitch(TX, TS);   // slots per staged row (>= WT)
     const int tx = grp % TX, ty = grp / TX;
     const bool valid = X0 + tx < p.nx && Y0 + ty < p.ny;
     const int X = min(X0 + tx, p.nx - 1), Y = min(Y0 + ty, p.ny - 1);
@@ -268,7 +280,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     // slot of the unwrapped coordinate (u, v) in the staged tile, or -1 outside it
     auto slot_of = [&](int u, int v) -> int {
         const int cu = u - (X0 - HALO), cv = v - (Y0 - HALO);
-        return (cu >= 0 && cu < WT && cv >= 0 && cv < HT) ? cv * WT + cu : -1;
+        return (cu >= 0 && cu < WT && cv >= 0 && cv < HT) ? cv * PT + cu : -1;
     };
 
     // ---------------- staging: tile + halo records into shared memory --------------
@@ -276,17 +288,20 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         constexpr int CH = Slot<R>::chunks;
         const int total = WT * HT * CH;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int sl = idx / CH, ch = idx - sl * CH;
-            const int gxw = bc_wrap(X0 - HALO + sl % WT, p.nx, p.bcx);
-            const int gyw = bc_wrap(Y0 - HALO + sl / WT, p.ny, p.bcy);
+            const int k = idx / CH, ch = idx - k * CH;
+            const int cu = k % WT, cv = k / WT;
+            const int gxw = bc_wrap(X0 - HALO + cu, p.nx, p.bcx);
+            const int gyw = bc_wrap(Y0 - HALO + cv, p.ny, p.bcy);
             const R *src = in + ((size_t)gyw * p.nx + gxw) * SL + ch * (16 / sizeof(R));
-            cp_async16(tile + sl * TS + ch * (16 / sizeof(R)), src);
+            cp_async16(tile + (cv * PT + cu) * TS + ch * (16 / sizeof(R)), src);
         }
         cp_async_wait_all();
         __syncthreads();
         // sqrt(theta) of every staged node into the slot's spare value, once per step
-        for (int sl = threadIdx.x; sl < WT * HT; sl += blockDim.x)
+        for (int k = threadIdx.x; k < WT * HT; k += blockDim.x) {
+            const int sl = (k / WT) * PT + k % WT;
             tile[sl * TS + P_SQ] = sqrt_(tile[sl * TS + P_TH]);
+        }
         __syncthreads();
     }
 
@@ -375,20 +390,25 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     }
     if (threadIdx.x < STEP_NB) {
         // exact FP64 sums of node j's stored populations, one node per lane of warp 0
+        // (error-free in R: TwoSum cascades, each sum kept as an unevaluated (hi, lo) pair
+        // and rounded once to FP64, which keeps the FP64 pipe free in the FP32 form)
         const R *rj = tile + slot_of(X0 + threadIdx.x % TX, Y0 + threadIdx.x / TX) * TS;
-        double b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        R hi[4] = {R(0), R(0), R(0), R(0)}, lo[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const double f = (double)rj[P_F + i];
-            b0 += f;
-            if (i % 3 == 0) b1 -= f;
-            if (i % 3 == 2) b1 += f;
-            if (i / 3 == 0) b2 -= f;
-            if (i / 3 == 2) b2 += f;
-            b3 += (double)rj[P_G + i];
+            const R f = rj[P_F + i], gv = rj[P_G + i];
+            const R terms[4] = {f, R(i % 3 - 1) * f, R(i / 3 - 1) * f, gv};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k == 1 && i % 3 == 1) continue;
+                if (k == 2 && i / 3 == 1) continue;
+                R e;
+                two_sum_(hi[k], terms[k], hi[k], e);
+                lo[k] += e;
+            }
         }
-        sh.base[threadIdx.x][0] = b0; sh.base[threadIdx.x][1] = b1;
-        sh.base[threadIdx.x][2] = b2; sh.base[threadIdx.x][3] = b3;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sh.base[threadIdx.x][k] = (double)hi[k] + (double)lo[k];
     }
     if (threadIdx.x == 0) sh.any_active = 1;
     __syncthreads();
@@ -692,7 +712,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 
 // One time step of one simulation: one block per tile.
 template <typename R, int LPN>
-__global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step(DevParams p, const R *__restrict__ in,
+__global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(LPN)) k_pond_step(DevParams p, const R *__restrict__ in,
                                                              R *__restrict__ out, DevStats *stats)
 {
     step_tile<R, LPN>(p, in, out, stats, blockIdx.x);
@@ -711,7 +731,7 @@ struct SimDesc {
 // One time step of every simulation of a batch in one launch: block b steps tile
 // work[b].y of simulation work[b].x (a device work-list of (simulation, tile) pairs).
 template <typename R, int LPN>
-__global__ void __launch_bounds__(STEP_NB *LPN) k_pond_step_batch(const SimDesc<R> *__restrict__ descs,
+__global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(LPN)) k_pond_step_batch(const SimDesc<R> *__restrict__ descs,
                                                                    const int2 *__restrict__ work)
 {
     __shared__ DevParams sp;
