@@ -246,6 +246,30 @@ def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
     return summ
 
 
+def other_configs(pond, torch, stream) -> dict:
+    """MLUPS of the other full-size workloads (mixed form, default launch shape, a few
+    back-to-back steps after warm-up; the larger ones exceed L2 by themselves)."""
+    from paper_2002_09217_gb300 import inputs
+    out = {}
+    for name, steps in (("slab128x4", 200), ("droplet512x512", 20), ("dropletshock2048x1024", 10)):
+        w = inputs.config(name)
+        for prec in ("mixed", "fp64") if name == "slab128x4" else ("mixed",):
+            sim = pond.from_workload(w, precision=prec, stream=stream)
+            sim.init_fields(*w.fields())
+            sim.step(3)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sim.step(steps)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / steps
+            st = sim.stats()
+            sim.close()
+            out["%s/%s" % (name, prec)] = {"mlups": w.nodes / ms / 1e3, "ms_per_step": ms,
+                                           "streams_per_node": st["streams"] / max(1, st["node_updates"])}
+    return out
+
+
 def parity_vs_oracle(w, pond, stream, precision, shape, res, steps) -> dict:
     import numpy as np
     import oracle
@@ -361,6 +385,9 @@ def main():
                         "ms_per_step": sum(ms64) / 30, "launch_shape": shape64 or "default",
                         "frame_search_streams_per_node": its64,
                         "roofline": roofline(w, "fp64", its64, kms64, pk)}
+
+    if rank == 0:
+        line["other_configs"] = other_configs(pond, torch, stream)
 
     if not args.no_serving:
         serv = serving_sample(torch, rank, ws)

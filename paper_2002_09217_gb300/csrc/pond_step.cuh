@@ -40,9 +40,9 @@ constexpr int STEP_NB = 16;   // nodes per block (lanes per node LPN = 8 or 16 i
                               // evenly over the 152 SMs
 constexpr unsigned STEP_NB_MASK = STEP_NB == 32 ? 0xffffffffu : ((1u << STEP_NB) - 1u);
 constexpr int HALO = 3;       // staged halo width (stencil reach for |v| dt < 1)
-// resident blocks per SM the register budget is sized for (about 96 registers per thread
-// with 8 lanes per node, a few spilled values; 16 lanes keep their registers)
-#define STEP_MIN_BLOCKS(LPN) ((LPN) == 8 ? 5 : 2)
+// resident blocks per SM the register budget is sized for: FP32 with 8 lanes per node at
+// about 96 registers per thread (a few spilled values); the other variants keep theirs
+#define STEP_MIN_BLOCKS(R, LPN) ((sizeof(R) == 4 && (LPN) == 8) ? 5 : 2)
 
 // Shared-memory record slot: the first 24 values of a node record (f, g, theta, u, pad,
 // rho, T), padded to a 16-byte multiple that spreads consecutive slots over the banks.
@@ -712,7 +712,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 
 // One time step of one simulation: one block per tile.
 template <typename R, int LPN>
-__global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(LPN)) k_pond_step(DevParams p, const R *__restrict__ in,
+__global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(R, LPN)) k_pond_step(DevParams p, const R *__restrict__ in,
                                                              R *__restrict__ out, DevStats *stats)
 {
     step_tile<R, LPN>(p, in, out, stats, blockIdx.x);
@@ -731,7 +731,7 @@ struct SimDesc {
 // One time step of every simulation of a batch in one launch: block b steps tile
 // work[b].y of simulation work[b].x (a device work-list of (simulation, tile) pairs).
 template <typename R, int LPN>
-__global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(LPN)) k_pond_step_batch(const SimDesc<R> *__restrict__ descs,
+__global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(R, LPN)) k_pond_step_batch(const SimDesc<R> *__restrict__ descs,
                                                                    const int2 *__restrict__ work)
 {
     __shared__ DevParams sp;
