@@ -120,15 +120,21 @@ def bytes_per_update(precision: str) -> int:
     return 48 * (4 if precision == "mixed" else 8)
 
 
-# Algorithmic FLOPs of the step kernel's formula, per node update:
-#  per stencil pair (9 directions x 16 stencil nodes per stream): gauge offsets (9),
-#  6 transfer-map increments (4 each), f and g increment components (2 x 57), Lagrange
-#  weight and accumulation (10) => 157; per direction: departure point and basis (20);
-#  per stream: moments and residual (60); per node update: collision (~1000).
-FLOPS_PAIR = 157
+# Algorithmic FLOPs of the step kernel's formula, per node update (an FMA counts 2):
+#  per stencil pair (9 directions x 16 stencil nodes per stream): gauge offsets (8), the
+#  six transfer increments (4 for the offsets, ~20 for the increments), the x-increments
+#  of the three source rows for f and g (30), the f and g increment components (22),
+#  Lagrange weight and accumulation (7) => 91; per direction: departure point, basis and
+#  moment sums (20); per stream: moments and residual (60); per node update: the
+#  Korteweg tensor, heat flux and their divergences counted once per node (200; the kernel
+#  recomputes them at each neighbour) and the collision (1300: transfer rows of both axes
+#  ~230, forced g equilibrium ~410, BGK updates ~150, carrying X* into the streaming
+#  gauge ~390, exact rest-population remainders ~100).
+FLOPS_PAIR = 91
 FLOPS_DIR = 20
 FLOPS_STREAM_EXTRA = 60
-FLOPS_COLLIDE = 1000
+FLOPS_NONLOCAL = 200
+FLOPS_COLLIDE = 1300
 
 
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from
@@ -208,7 +214,7 @@ def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws)
 
 
 def roofline(w, precision, its, kernel_ms, pk):
-    fl = its * flops_per_stream() + FLOPS_COLLIDE
+    fl = its * flops_per_stream() + FLOPS_NONLOCAL + FLOPS_COLLIDE
     achieved = w.nodes * fl / (kernel_ms * 1e-3) / 1e12
     peak = alu_peak_tflops(precision, pk["sm_max_mhz"])
     return {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved, "peak": peak,

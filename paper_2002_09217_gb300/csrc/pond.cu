@@ -89,6 +89,35 @@ inline unsigned blocks_for(size_t n, unsigned bs) { return (unsigned)((n + bs - 
 
 bool mixed(const pond_ctx *c) { return c->opts.precision == POND_MIXED; }
 
+// Largest dynamic shared memory of a step block over the tile shapes, for lanes per node.
+template <typename R>
+size_t step_smem_max(int lanes)
+{
+    size_t m = 0;
+    for (int tx = 1; tx <= STEP_NB; tx *= 2)
+        m = std::max(m, step_smem_bytes(tx, Slot<R>::stride, (int)sizeof(R), lanes));
+    return m;
+}
+
+// Lets the step kernels of type R use more than the default 48 KB of dynamic shared
+// memory on the current device (idempotent; not a stream operation).
+template <typename R>
+cudaError_t allow_step_smem()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_pond_step<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_max<R>(8));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pond_step<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)step_smem_max<R>(16));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pond_step_batch<R, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)step_smem_max<R>(8));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_pond_step_batch<R, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)step_smem_max<R>(16));
+    return e;
+}
+
 template <typename R>
 pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
@@ -96,7 +125,7 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
     R *out = (R *)c->state[1 - c->cur];
     const int tx = c->dp.tile_x, ty = STEP_NB / tx;
     const unsigned nb = (unsigned)(c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty));
-    const size_t smem = (size_t)step_tile_slots(tx, Slot<R>::stride) * Slot<R>::stride * sizeof(R);
+    const size_t smem = step_smem_bytes(tx, Slot<R>::stride, (int)sizeof(R), c->lanes);
     if (ev) cudaEventRecord(ev[0], c->stream);
     if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats);
     else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats);
@@ -264,10 +293,10 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     // tile of the step kernel: a 16 x 1 strip for grids of few rows, 4 x 4 otherwise
     int tile_x = opts->tile_x ? opts->tile_x : (grid->ny < 4 ? 16 : 4);
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = opts->precision == POND_MIXED ? allow_step_smem<float>() : allow_step_smem<double>();
     if (e != cudaSuccess) {
-        std::string m = std::string("no usable CUDA device: ") + cudaGetErrorString(e);
         delete c;
-        (void)m;
         return POND_ECUDA;
     }
     DevParams &d = c->dp;
@@ -526,11 +555,6 @@ pond_status bfail(pond_batch *b, pond_status st, const std::string &m)
     return st;
 }
 
-template <typename R>
-size_t step_smem(int tile_x)
-{
-    return (size_t)step_tile_slots(tile_x, Slot<R>::stride) * Slot<R>::stride * sizeof(R);
-}
 
 template <typename R>
 cudaError_t build_group(pond_batch *b, pond_batch::Group &G)
@@ -547,7 +571,7 @@ cudaError_t build_group(pond_batch *b, pond_batch::Group &G)
         const int ty = STEP_NB / c->dp.tile_x;
         const int tiles = c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty);
         for (int t = 0; t < tiles; ++t) work.push_back(make_int2((int)k, t));
-        G.smem = std::max(G.smem, step_smem<R>(c->dp.tile_x));
+        G.smem = std::max(G.smem, step_smem_bytes(c->dp.tile_x, Slot<R>::stride, (int)sizeof(R), G.lanes));
     }
     G.nwork = (int)work.size();
     cudaError_t e = cudaSuccess;

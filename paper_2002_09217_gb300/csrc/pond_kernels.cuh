@@ -107,7 +107,6 @@ __global__ void k_init(DevParams p, const double *__restrict__ rho, const double
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    const long long N = p.N;
     int X = (int)(n % p.nx), Y = (int)(n / p.nx);
     double gx = 0.0, gy = 0.0;
     for (int i = 0; i < 9; ++i) {
@@ -160,7 +159,6 @@ __global__ void k_moments(DevParams p, const R *__restrict__ st, double *rho, do
 {
     long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    const long long N = p.N;
     double r = (double)REC(st, n, P_RHO), t = (double)REC(st, n, P_T);
     if (rho) rho[n] = r;
     if (ux) ux[n] = (double)REC(st, n, P_UHX);

@@ -40,12 +40,15 @@ constexpr int STEP_NB = 16;   // nodes per block (lanes per node LPN = 8 or 16 i
                               // evenly over the 152 SMs
 constexpr unsigned STEP_NB_MASK = STEP_NB == 32 ? 0xffffffffu : ((1u << STEP_NB) - 1u);
 constexpr int HALO = 3;       // staged halo width (stencil reach for |v| dt < 1)
-// resident blocks per SM the register budget is sized for: FP32 with 8 lanes per node at
-// about 96 registers per thread (a few spilled values); the other variants keep theirs
-#define STEP_MIN_BLOCKS(R, LPN) ((sizeof(R) == 4 && (LPN) == 8) ? 5 : 2)
+// resident blocks per SM the register budget is sized for: in FP32 five blocks of 128
+// threads (8 lanes per node, about 96 registers) or two of 256 (16 lanes); in FP64 one,
+// so that its wider values stay in registers
+#define STEP_MIN_BLOCKS(R, LPN) (sizeof(R) == 8 ? 1 : ((LPN) == 8 ? 5 : 2))
 
 // Shared-memory record slot: the first 24 values of a node record (f, g, theta, u, pad,
 // rho, T), padded to a 16-byte multiple that spreads consecutive slots over the banks.
+// slot words past the 24 staged values: p and p/rho of the staged node (shared memory only)
+constexpr int S_PR = 24, S_PRR = 25;
 template <typename R> struct Slot;
 template <> struct Slot<float> { static constexpr int stride = 28, chunks = 6; };
 template <> struct Slot<double> { static constexpr int stride = 26, chunks = 12; };
@@ -62,6 +65,19 @@ __host__ __device__ constexpr int step_row_pitch(int tile_x, int slot_words)
 __host__ __device__ constexpr int step_tile_slots(int tile_x, int slot_words)
 {
     return step_row_pitch(tile_x, slot_words) * (STEP_NB / tile_x + 2 * HALO);
+}
+
+// Per-lane partial increments of the 18 streamed populations of every node, behind the
+// staged tile: node j's row d (0..8 f, 9..17 g) holds its lanes' partials at
+// [j * step_part_stride(LPN) + d * LPN + lane]; the extra LPN per node offsets
+// neighbouring groups of a warp onto other banks.
+__host__ __device__ constexpr int step_part_stride(int lpn) { return 19 * lpn; }
+
+// Dynamic shared memory of one step block: staged tile + halo, then the partials.
+__host__ __device__ constexpr size_t step_smem_bytes(int tile_x, int slot_words, int elem_bytes, int lpn)
+{
+    return ((size_t)step_tile_slots(tile_x, slot_words) * slot_words +
+            (size_t)STEP_NB * step_part_stride(lpn)) * elem_bytes;
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
@@ -96,6 +112,15 @@ __device__ __forceinline__ R ell_inc(int k, int a, R e)
     if (k == 1) return -e * (two_c + e);
     if (k == 0) return R(0.5) * e * (two_c + e - R(1));
     return R(0.5) * e * (two_c + e + R(1));
+}
+
+// ell_inc for a target index k known only at run time: the same arithmetic, with the
+// k = 0 / k = 2 forms joined through their sign
+template <typename R>
+__device__ __forceinline__ R ell_inc_rt(int k, int a, R e)
+{
+    const R base = R(2 * (a - 1)) + e;
+    return k == 1 ? -e * base : R(0.5) * e * (base + R(k - 1));
 }
 
 // 1-D lattice weights W_-1, W_0, W_+1 = 1/6, 2/3, 1/6 as values of type R whose sum is
@@ -140,18 +165,23 @@ __device__ __forceinline__ R pick(const R (&a)[K], int i)
     return r;
 }
 
-template <typename R> __device__ __forceinline__ R fdiv_(R a, R b);
-template <> __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
-template <> __device__ __forceinline__ double fdiv_(double a, double b) { return a / b; }
-
 // 1/x in FP64 from the FP32 reciprocal and two Newton steps (relative error ~1e-28
-// before the final rounding), for the frame-search EoS in warp 0.
+// before the final rounding); x must lie in the FP32 normal range.
 __device__ __forceinline__ double rcp_d(double x)
 {
     double r = (double)__frcp_rn((float)x);
     r = r * (2.0 - x * r);
     return r * (2.0 - x * r);
 }
+
+// a / b for operands of moderate range (transfer-map offsets, collision coefficients):
+// the fast FP32 quotient, or a times the Newton reciprocal in FP64.
+template <typename R> __device__ __forceinline__ R fdiv_(R a, R b);
+template <> __device__ __forceinline__ float fdiv_(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv_(double a, double b) { return a * rcp_d(b); }
+template <typename R> __device__ __forceinline__ R frcp_(R b);
+template <> __device__ __forceinline__ float frcp_(float b) { return __frcp_rn(b); }
+template <> __device__ __forceinline__ double frcp_(double b) { return rcp_d(b); }
 
 // Error-free sum of two values of type R (Knuth TwoSum).
 template <typename R>
@@ -216,38 +246,49 @@ __device__ __forceinline__ void load_rhoT(const double *__restrict__ in, size_t 
 }
 
 // Contribution of stencil node `nd` to direction (jx, jy) of the arrival node, in the
-// increment form; fx/gx are the arrival node's own stored populations.
+// increment form.
+//
+// With the per-axis maps written as G = I + E (E = transfer increments, zero for equal
+// gauges), [G (f_n - f_x) + (G - I) f_x]_(jx,jy) regroups exactly into
+//   (f_n - f_x)_(jx,jy) + t_jy + sum_b Ey[b] (f_n(jx, b) + t_b),   t_b = sum_a Ex[a] f_n(a, b):
+// the difference of the two nodes' populations plus increments that multiply the source
+// values by the small E only, so the rounding stays relative to the differences and equal
+// gauges still give f_n - f_x exactly.
+template <typename R>
+__device__ __forceinline__ R sel3(int k, R a0, R a1, R a2)
+{
+    return k == 0 ? a0 : (k == 1 ? a1 : a2);
+}
+
+// fxj, gxj: the arrival node's own populations of direction (jx, jy).  jx must be a
+// compile-time constant after unrolling; jy may vary at run time (selects, no indexing).
 template <typename R>
 __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R s, R inv_s, R ux,
-                                         R uy, const R fx[9], const R gx[9], R &tf, R &tg)
+                                         R uy, R fxj, R gxj, R &tf, R &tg)
 {
     const R thn = v[P_TH];
     const R sn = v[P_SQ];
     const R qm1 = fdiv_(thn - th, (sn + s) * s);    // (s_n - s)/s without cancellation
     const R wx = (v[P_UX] - ux) * inv_s;
     const R wy = (v[P_UY] - uy) * inv_s;
-    R Ex[3], Ey[3], Gx[3], Gy[3];
+    R Ex[3], Ey[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         Ex[a] = ell_inc<R>(jx, a, qm1 * R(a - 1) + wx);
         Ey[a] = ell_inc<R>(jy, a, qm1 * R(a - 1) + wy);
-        Gx[a] = Ex[a] + (a == jx ? R(1) : R(0));
-        Gy[a] = Ey[a] + (a == jy ? R(1) : R(0));
     }
-    R sf = 0, sg = 0;
+    R txf[3], txg[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        R rf = 0, rg = 0;
+        txf[b] = Ex[0] * v[P_F + 3 * b] + Ex[1] * v[P_F + 3 * b + 1] + Ex[2] * v[P_F + 3 * b + 2];
+        txg[b] = Ex[0] * v[P_G + 3 * b] + Ex[1] * v[P_G + 3 * b + 1] + Ex[2] * v[P_G + 3 * b + 2];
+    }
+    R sf = (sel3(jy, v[P_F + jx], v[P_F + 3 + jx], v[P_F + 6 + jx]) - fxj) + sel3(jy, txf[0], txf[1], txf[2]);
+    R sg = (sel3(jy, v[P_G + jx], v[P_G + 3 + jx], v[P_G + 6 + jx]) - gxj) + sel3(jy, txg[0], txg[1], txg[2]);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int i = 3 * b + a;
-            rf += Gx[a] * (v[P_F + i] - fx[i]) + Ex[a] * fx[i];
-            rg += Gx[a] * (v[P_G + i] - gx[i]) + Ex[a] * gx[i];
-        }
-        const R fxj = jx == 0 ? fx[3 * b] : (jx == 1 ? fx[3 * b + 1] : fx[3 * b + 2]);
-        const R gxj = jx == 0 ? gx[3 * b] : (jx == 1 ? gx[3 * b + 1] : gx[3 * b + 2]);
-        sf += Gy[b] * rf + Ey[b] * fxj;
-        sg += Gy[b] * rg + Ey[b] * gxj;
+    for (int b = 0; b < 3; ++b) {
+        sf += Ey[b] * (v[P_F + 3 * b + jx] + txf[b]);
+        sg += Ey[b] * (v[P_G + 3 * b + jx] + txg[b]);
     }
     tf = sf;
     tg = sg;
@@ -265,7 +306,6 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     R *tile = reinterpret_cast<R *>(step_dyn_smem);
     constexpr int TS = Slot<R>::stride;
     const TypedParams<R> &q = typed<R>(p);
-    const long long N = p.N;
     const int grp = threadIdx.x / LPN, lane = threadIdx.x % LPN;
     const unsigned gmask = (LPN == 8 ? 0xffu : 0xffffu) << (LPN * (grp % (32 / LPN)));
     // tile of TX x TY nodes; node grp at (tx, ty) of the tile
@@ -297,10 +337,16 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         }
         cp_async_wait_all();
         __syncthreads();
-        // sqrt(theta) of every staged node into the slot's spare value, once per step
+        // per staged node, once per step: sqrt(theta) into the slot's spare value, and the
+        // vdW pressure and p/rho of the stored rho, T (for the non-local terms) into the
+        // slot words past the staged values
         for (int k = threadIdx.x; k < WT * HT; k += blockDim.x) {
-            const int sl = (k / WT) * PT + k % WT;
-            tile[sl * TS + P_SQ] = sqrt_(tile[sl * TS + P_TH]);
+            R *sl = tile + ((k / WT) * PT + k % WT) * TS;
+            sl[P_SQ] = sqrt_(sl[P_TH]);
+            const R r = sl[P_RHO], t = sl[P_T];
+            const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
+            sl[S_PR] = pr;
+            sl[S_PRR] = pr / r;
         }
         __syncthreads();
     }
@@ -319,7 +365,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         const int my = p.bcy == 0 ? Y0 + ty + cy : bc_wrap(Y0 + ty + cy, p.ny, 1);
         const R *c0 = tile + slot_of(mx, my) * TS;
         const R r0 = c0[P_RHO], t0 = c0[P_T];
-        const R pr0 = r0 * q.R * t0 / (R(1) - q.b * r0) - q.a * r0 * r0;
+        const R pr0 = c0[S_PR], prr0 = c0[S_PRR];
         // gradients from differences to the centre value (sum_i W_i c_i = 0), which keeps
         // their FP32 rounding proportional to the differences
         R grx = 0, gry = 0, lap = 0, ghx = 0, ghy = 0, gTx = 0, gTy = 0;
@@ -330,9 +376,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             const R *cm = tile + slot_of(mx + ex, my + ey) * TS;
             const R w = wst<R>(ex, ey);
             const R r = cm[P_RHO], t = cm[P_T];
-            const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
             const R dr = r - r0, dT = t - t0;
-            const R dh = q.cv * dT - q.a * dr + (pr / r - pr0 / r0);
+            const R dh = q.cv * dT - q.a * dr + (cm[S_PRR] - prr0);
             grx += w * R(ex) * dr;
             gry += w * R(ey) * dr;
             lap += w * dr;
@@ -414,9 +459,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     __syncthreads();
 
     // ---------------- phase 1: frame search (block lockstep) -----------------------
-    // my_df/my_dg: increments of population `lane` (and of population 8 on lane 0 when a
-    // group has 8 lanes) after the final stream of the node
-    R my_df = 0, my_dg = 0, my_df8 = 0, my_dg8 = 0;
+    // part: this lane's partial increments of the node's 18 populations in the latest stream
+    R *part = tile + step_tile_slots(TX, TS) * TS + grp * step_part_stride(LPN) + lane;
     int it = 0;                                   // iterations of this block
     int my_it = 0, my_conv = 0, my_stall = 0;     // warp-0 lane bookkeeping for node threadIdx.x
     double my_res = 1e300;                        // previous residual of that node
@@ -431,6 +475,12 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             // unrolled so that their transfer coefficients are compile-time selections
 #pragma unroll 1
             for (int jy = 0; jy < 3; ++jy) {
+                R fxr[3], gxr[3];   // own populations of this row of directions
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    fxr[a] = sel3(jy, fx[a], fx[3 + a], fx[6 + a]);
+                    gxr[a] = sel3(jy, gx[a], gx[3 + a], gx[6 + a]);
+                }
                 const R dy = -(s * R(jy - 1) + uy) * q.dt;
                 const R fly = floor(dy);
                 const int y0 = Y + (int)fly - 1;
@@ -457,25 +507,30 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                             v[P_SQ] = sqrt_(v[P_TH]);
                         }
                         R tf, tg;
-                        pair_inc<R>(v, jx, jy, th, s, inv_s, ux, uy, fx, gx, tf, tg);
+                        pair_inc<R>(v, jx, jy, th, s, inv_s, ux, uy, fxr[jx], gxr[jx], tf, tg);
                         const R ay = lag1<R>(mm, eta);
                         vf += ay * tf;
                         vg += ay * tg;
                     }
                     vf *= ax;
                     vg *= ax;
-#pragma unroll
-                    for (int o = LPN / 2; o > 0; o >>= 1) {
-                        vf += __shfl_xor_sync(gmask, vf, o, LPN);
-                        vg += __shfl_xor_sync(gmask, vg, o, LPN);
-                    }
-                    if (lane == i) { my_df = vf; my_dg = vg; }
-                    if (i == 8) { my_df8 = vf; my_dg8 = vg; }
+                    // this lane's partials: kept for the collision (the node's last stream
+                    // leaves them in place) and summed into the moments right away
+                    part[i * LPN] = vf;
+                    part[(9 + i) * LPN] = vg;
                     a0 += vf;
-                    a1 += vf * R(jx - 1);
+                    if (jx == 0) a1 -= vf;
+                    if (jx == 2) a1 += vf;
                     a2 += vf * R(jy - 1);
                     a3 += vg;
                 }
+            }
+#pragma unroll
+            for (int o = LPN / 2; o > 0; o >>= 1) {
+                a0 += __shfl_xor_sync(gmask, a0, o, LPN);
+                a1 += __shfl_xor_sync(gmask, a1, o, LPN);
+                a2 += __shfl_xor_sync(gmask, a2, o, LPN);
+                a3 += __shfl_xor_sync(gmask, a3, o, LPN);
             }
             if (lane == 0) {
                 sh.dsum[grp][0] = a0; sh.dsum[grp][1] = a1; sh.dsum[grp][2] = a2; sh.dsum[grp][3] = a3;
@@ -544,6 +599,24 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 
     // ---------------- phase 2: collision (one population per lane) -----------------
     if (valid) {
+        // increments of population `lane` (and of population 8 on lane 0 when a group has
+        // 8 lanes) from the node's final stream: the sum of its lanes' partials, read in a
+        // lane-rotated order so that the rows fall on different banks
+        R my_df = 0, my_dg = 0, my_df8 = 0, my_dg8 = 0;
+        {
+            const R *row = part - lane;
+            const int d = lane < 9 ? lane : 8;
+#pragma unroll
+            for (int l = 0; l < LPN; ++l) {
+                const int ll = (l + lane) & (LPN - 1);
+                my_df += row[d * LPN + ll];
+                my_dg += row[(9 + d) * LPN + ll];
+                if (LPN == 8) {
+                    my_df8 += row[8 * LPN + ll];
+                    my_dg8 += row[17 * LPN + ll];
+                }
+            }
+        }
         const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
         const R s = sqrt_(th), inv_s = R(1) / s;
         const R *m = sh.mac[grp];
@@ -553,34 +626,33 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         const R qm1 = fdiv_(sh.dlam[grp][0], (sst + s) * s);
         const R wsx = sh.dlam[grp][1] * inv_s, wsy = sh.dlam[grp][2] * inv_s;
         const R dtr = q.dt, om = q.omega;
-        const R dvx = Fx * dtr / rr * inv_s, dvy = Fy * dtr / rr * inv_s;
+        const R irr = frcp_(rr), iP2 = frcp_(R(2) * Pr);
+        const R dvx = Fx * dtr * irr * inv_s, dvy = Fy * dtr * irr * inv_s;
         const R W1[3] = {wlat<R>(0), wlat<R>(1), wlat<R>(2)};
         // transfer increments from lambda* = (ths, u*) into the streaming gauge, and from the
-        // force-shifted frame (ths, u* + F dt/rho) (Eq. S-i)
-        R Ex[3][3], Ey[3][3], Wsx[3], Wsy[3], Whx[3], Why[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            Wsx[k] = Wsy[k] = Whx[k] = Why[k] = 0;
+        // force-shifted frame (ths, u* + F dt/rho) (Eq. S-i), for the row k of one axis:
+        // E[a] = l_k increments at the source velocities, Ws = sum_a E[a] W_a, Wh = the
+        // force-shifted frame's extra weight
+        auto row = [&](int k, R w, R dv, R (&E)[3], R &Ws, R &Wh) {
+            Ws = 0;
+            Wh = 0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                Ex[k][a] = ell_inc<R>(k, a, qm1 * R(a - 1) + wsx);
-                Ey[k][a] = ell_inc<R>(k, a, qm1 * R(a - 1) + wsy);
-                Wsx[k] += Ex[k][a] * W1[a];
-                Wsy[k] += Ey[k][a] * W1[a];
-                Whx[k] += (ell_inc<R>(k, a, qm1 * R(a - 1) + wsx + dvx) - Ex[k][a]) * W1[a];
-                Why[k] += (ell_inc<R>(k, a, qm1 * R(a - 1) + wsy + dvy) - Ey[k][a]) * W1[a];
+                E[a] = ell_inc_rt<R>(k, a, qm1 * R(a - 1) + w);
+                Ws += E[a] * W1[a];
+                Wh += (ell_inc_rt<R>(k, a, qm1 * R(a - 1) + w + dv) - E[a]) * W1[a];
             }
-        }
+        };
         // g: forced equilibrium (Eq. new geq), heat-flux correction (Eq. gtilde) and the
         // force-work source 2 W_i uhat.F, all in lambda*, in every lane (9 values)
-        const R H = Er + Pr / rr;
-        const R Ixx = R(2) * uhxr * Fx + dtr * Fx * Fx * Er / (R(2) * Pr);
-        const R Ixy = uhxr * Fy + Fx * uhyr + dtr * Fx * Fy * Er / (R(2) * Pr);
-        const R Iyy = R(2) * uhyr * Fy + dtr * Fy * Fy * Er / (R(2) * Pr);
-        const R cM = dtr * rr / Pr;
+        const R H = Er + Pr * irr;
+        const R Ixx = R(2) * uhxr * Fx + dtr * Fx * Fx * Er * iP2;
+        const R Ixy = uhxr * Fy + Fx * uhyr + dtr * Fx * Fy * Er * iP2;
+        const R Iyy = R(2) * uhyr * Fy + dtr * Fy * Fy * Er * iP2;
+        const R cM = R(2) * dtr * rr * iP2;
         const R Mx = cM * (Fx * H - (Ixx * uxr + Ixy * uyr));
         const R My = cM * (Fy * H - (Ixy * uxr + Iyy * uyr));
-        const R cN = dtr * rr / (R(2) * Pr);
+        const R cN = dtr * rr * iP2;
         const R Nxx = rr + cN * Ixx, Nxy = cN * Ixy, Nyy = rr + cN * Iyy;
         // P/rho in the g equilibrium as sqrt(theta*)^2 times the lattice temperature of
         // the weights in use (sum_i W_i c_ix^2 = 2 W_+-1), so that the equilibrium's zeroth
@@ -599,8 +671,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             const R geq = w * (R(2) * rr * Er + Mx * ccx + My * ccy + Nxx * Axx + R(2) * Nxy * Axy + Nyy * Ayy);
             const R vx = ccx + uxr, vy = ccy + uyr;
             const R uc = uxr * cx + uyr * cy;
-            const R gc = M0 * w * (R(1) + rr * uc * uc / (R(2) * Pr * R(POND_TL))
-                                   - rr * (vx * vx + vy * vy) / (R(2) * Pr) + R(1));
+            const R gc = M0 * w * (R(1) + rr * uc * uc * iP2 * R(3)
+                                   - rr * (vx * vx + vy * vy) * iP2 + R(1));
             return om * geq + dtr * (gc + w * work);
         };
         const R my_x = xstar(lane < 9 ? lane : 8);
@@ -618,18 +690,14 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                 const int kx = i % 3, ky = i / 3;
                 const R dfi = rep == 0 ? my_df : my_df8, dgi = rep == 0 ? my_dg : my_dg8;
                 const R ft = pick(fx, i) + dfi, gt = pick(gx, i) + dgi;
-                const R Wx = pick(W1, kx) + pick(Wsx, kx), Wy = pick(W1, ky) + pick(Wsy, ky);
-                const R Whk = pick(Whx, kx), Whl = pick(Why, ky);
+                R exk[3], eyl[3], Wsk, Wsl, Whk, Whl;
+                row(kx, wsx, dvx, exk, Wsk, Whk);
+                row(ky, wsy, dvy, eyl, Wsl, Whl);
+                const R Wx = pick(W1, kx) + Wsk, Wy = pick(W1, ky) + Wsl;
                 const R feq = rr * Wx * Wy;
                 const R S = rr * (Whk * (Wy + Whl) + Wx * Whl);
                 fo[rep] = ft + om * (feq - ft) + S;
                 // carry X* into the streaming gauge: X = X* + (G* - I) X*
-                R exk[3], eyl[3];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    exk[a] = kx == 0 ? Ex[0][a] : (kx == 1 ? Ex[1][a] : Ex[2][a]);
-                    eyl[a] = ky == 0 ? Ey[0][a] : (ky == 1 ? Ey[1][a] : Ey[2][a]);
-                }
                 R acc = pick(Xs, i);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
