@@ -313,6 +313,13 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     d.pf.inv_cv = (float)d.pd.inv_cv; d.pf.kappa = (float)d.pd.kappa; d.pf.p_floor = (float)d.pd.p_floor;
     d.pf.dt = (float)d.pd.dt; d.pf.omega = (float)d.pd.omega; d.pf.mu_coef = (float)d.pd.mu_coef;
     d.pf.cvR = (float)d.pd.cvR; d.pf.k_cond = (float)d.pd.k_cond;
+    auto split = [](double x, float out[2]) {
+        out[0] = (float)x;
+        out[1] = (float)(x - (double)out[0]);
+    };
+    split(d.a, d.ff_a); split(d.b, d.ff_b); split(d.R, d.ff_R); split(d.pd.inv_cv, d.ff_icv);
+    split(d.p_floor, d.ff_pfl);
+    d.tol_f = (float)d.tol;
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
     size_t sb = (size_t)SL * c->N * c->esize;

@@ -42,6 +42,10 @@ struct DevParams {
     int tile_x, tiles_x;   // step kernel tile: tile_x by (16 / tile_x) nodes; tiles per row
     TypedParams<float> pf;
     TypedParams<double> pd;
+    // the FP32 form's frame-search EoS constants as (hi, lo) float pairs (hi + lo = the
+    // FP64 value to ~2^-48), and its tolerance
+    float ff_a[2], ff_b[2], ff_R[2], ff_icv[2], ff_pfl[2];
+    float tol_f;
 };
 
 template <typename R> __device__ __forceinline__ const TypedParams<R> &typed(const DevParams &p);

@@ -98,7 +98,8 @@ struct StepShared {
     R mac[STEP_NB][10];        // rho, u*x, u*y, uhx, uhy, E, T, P, theta*, p
     R dlam[STEP_NB][3];        // theta* - theta, u*x - ux, u*y - uy (from FP64)
     R hilo[STEP_NB][4];        // rho and sum g~ as (hi, lo) pairs of R
-    double base[STEP_NB][4];   // exact FP64 sums of the node's stored f, f cx, f cy, g
+    R bhi[STEP_NB][4];         // sums of the node's stored f, f cx, f cy, g, error-free as
+    R blo[STEP_NB][4];         //   unevaluated (hi, lo) pairs of R
     int active[STEP_NB];
     int any_active;
 };
@@ -190,6 +191,63 @@ __device__ __forceinline__ void two_sum_(R a, R b, R &s, R &e)
     s = a + b;
     R bb = s - a;
     e = (a - (s - bb)) + (b - bb);
+}
+
+// Float-float ("double-word") arithmetic for the FP32 form's frame-search EoS: a value is
+// an unevaluated pair hi + lo of floats.  Sums use Knuth's TwoSum, products the exact FMA
+// product error (Dekker's TwoProduct with a fused multiply-add), each result renormalised
+// with Dekker's Fast2Sum; relative error ~2^-44 per operation, far below the FP32 form's
+// needs, on the FP32 pipes (GB300 runs FP64 at 1/64 of the FP32 rate).
+struct ffv {
+    float hi, lo;
+};
+__device__ __forceinline__ ffv ff_norm(float a, float b)   // |a| >= |b| or a == 0
+{
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+__device__ __forceinline__ ffv ff_pair(float a, float b)   // any a, b
+{
+    ffv r;
+    two_sum_(a, b, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ ffv ff_add(ffv a, ffv b)
+{
+    float s, e;
+    two_sum_(a.hi, b.hi, s, e);
+    return ff_norm(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ ffv ff_add(ffv a, float b)
+{
+    float s, e;
+    two_sum_(a.hi, b, s, e);
+    return ff_norm(s, e + a.lo);
+}
+__device__ __forceinline__ ffv ff_neg(ffv a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ffv ff_mul(ffv a, ffv b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);   // never contracted into the sum below
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ ffv ff_mul(ffv a, float b)
+{
+    const float p = __fmul_rn(a.hi, b);
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return ff_norm(p, e);
+}
+// 1/a: the FP32 reciprocal and one Newton step r + r (1 - a r) with the residual in
+// float-float (Newton doubles the ~24 correct bits)
+__device__ __forceinline__ ffv ff_rcp(ffv a)
+{
+    const float r = __frcp_rn(a.hi);
+    const ffv ar = ff_mul(a, r);
+    const float res = (1.0f - ar.hi) - ar.lo;
+    return ff_norm(r, r * res);
 }
 
 // The 21 streamed values of node nd's record (f[9], g[9], theta, u_x, u_y, plus rho and T
@@ -292,6 +350,83 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
     }
     tf = sf;
     tg = sg;
+}
+
+// Results of one corrector evaluation (moments, e -> T, EoS) of a node, in R.
+template <typename R>
+struct EosOut {
+    R rho_hi, rho_lo;   // rho as a (hi, lo) pair
+    R gs_hi, gs_lo;     // sum of the streamed g as a (hi, lo) pair (= 2 rho E)
+    R uxs, uys;         // streamed velocity u* (the next gauge velocity)
+    R uhx, uhy;         // actual fluid velocity uhat = u* + F dt / (2 rho)
+    R E, T, P, pr;      // total energy per mass, temperature, floored and vdW pressure
+    R ths;              // theta* = P / (rho T_L)
+    R dth, dux, duy;    // theta* - theta, u* - u (the gauge change)
+};
+
+// FP64 form: the streamed moments are the stored sums (hi + lo, rounded to FP64) plus the
+// stream's increments (moments Eq.; SM "Thermodynamics": e = E - uhat^2/2 - E_lambda,
+// T = (e + a rho)/C_v, p = rho R T/(1 - b rho) - a rho^2, theta = max(p, p_floor)/(rho T_L)).
+__device__ __forceinline__ void eos_update(const DevParams &p, const double *bhi, const double *blo,
+                                           const double *dsum, const double *nl, const double *lam,
+                                           double sr, EosOut<double> &o)
+{
+    const double dt = p.dt;
+    const double Fxd = nl[0], Fyd = nl[1], rEd = nl[2];
+    const double thd = lam[0], uxd = lam[1], uyd = lam[2];
+    const double rho = (bhi[0] + blo[0]) + dsum[0];
+    const double irho = rcp_d(rho);
+    const double dux = sr * ((bhi[1] + blo[1]) + dsum[1]) * irho;
+    const double duy = sr * ((bhi[2] + blo[2]) + dsum[2]) * irho;
+    const double uxs = uxd + dux, uys = uyd + duy;
+    const double uhx = uxs + 0.5 * Fxd * dt * irho, uhy = uys + 0.5 * Fyd * dt * irho;
+    const double gs = (bhi[3] + blo[3]) + dsum[3];
+    const double E = 0.5 * gs * irho;
+    const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEd * irho;
+    const double T = (e + p.a * rho) * p.pd.inv_cv;
+    const double pr = rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho;
+    const double P = pr > p.p_floor ? pr : p.p_floor;
+    const double ths = P * irho * 3.0;
+    o.rho_hi = rho; o.rho_lo = 0.0; o.gs_hi = gs; o.gs_lo = 0.0;
+    o.uxs = uxs; o.uys = uys; o.uhx = uhx; o.uhy = uhy;
+    o.E = E; o.T = T; o.P = P; o.pr = pr; o.ths = ths;
+    o.dth = ths - thd; o.dux = dux; o.duy = duy;
+}
+
+// FP32 form: the same formulas in float-float from the exact (hi, lo) stored sums and the
+// FP32 increments; the results are rounded to FP32 once (the pairs of rho and sum g are
+// kept for the collision's exact remainders).
+__device__ __forceinline__ void eos_update(const DevParams &p, const float *bhi, const float *blo,
+                                           const float *dsum, const float *nl, const float *lam,
+                                           float sr, EosOut<float> &o)
+{
+    const float dt = p.pf.dt;
+    const ffv a = {p.ff_a[0], p.ff_a[1]}, b = {p.ff_b[0], p.ff_b[1]};
+    const ffv Rg = {p.ff_R[0], p.ff_R[1]}, icv = {p.ff_icv[0], p.ff_icv[1]};
+    const ffv rho = ff_add(ff_pair(bhi[0], blo[0]), dsum[0]);
+    const ffv irho = ff_rcp(rho);
+    const ffv mx = ff_add(ff_pair(bhi[1], blo[1]), dsum[1]);
+    const ffv my = ff_add(ff_pair(bhi[2], blo[2]), dsum[2]);
+    const ffv dux = ff_mul(ff_mul(mx, irho), sr), duy = ff_mul(ff_mul(my, irho), sr);
+    const ffv uxs = ff_add(dux, lam[1]), uys = ff_add(duy, lam[2]);
+    const ffv uhx = ff_add(uxs, 0.5f * nl[0] * dt * irho.hi);
+    const ffv uhy = ff_add(uys, 0.5f * nl[1] * dt * irho.hi);
+    const ffv gs = ff_add(ff_pair(bhi[3], blo[3]), dsum[3]);
+    const ffv E = ff_mul(ff_mul(gs, irho), 0.5f);
+    const ffv kin = ff_mul(ff_add(ff_mul(uhx, uhx), ff_mul(uhy, uhy)), 0.5f);
+    const ffv e = ff_add(ff_add(E, ff_neg(kin)), ff_neg(ff_mul(irho, nl[2])));
+    const ffv T = ff_mul(ff_add(e, ff_mul(rho, a)), icv);
+    const ffv den = ff_add(ff_neg(ff_mul(rho, b)), 1.0f);
+    const ffv pr = ff_add(ff_mul(ff_mul(ff_mul(rho, Rg), T), ff_rcp(den)),
+                          ff_neg(ff_mul(ff_mul(rho, rho), a)));
+    const bool floored = !(pr.hi > p.ff_pfl[0] || (pr.hi == p.ff_pfl[0] && pr.lo > p.ff_pfl[1]));
+    const ffv P = floored ? ffv{p.ff_pfl[0], p.ff_pfl[1]} : pr;
+    const ffv ths = ff_mul(ff_mul(P, irho), 3.0f);
+    o.rho_hi = rho.hi; o.rho_lo = rho.lo; o.gs_hi = gs.hi; o.gs_lo = gs.lo;
+    o.uxs = uxs.hi; o.uys = uys.hi; o.uhx = uhx.hi; o.uhy = uhy.hi;
+    o.E = E.hi; o.T = T.hi; o.P = P.hi; o.pr = pr.hi; o.ths = ths.hi;
+    o.dth = (ths.hi - lam[0]) + ths.lo;
+    o.dux = dux.hi; o.duy = duy.hi;
 }
 
 // One time step of one tile (block) of a simulation: the body of both step kernels.
@@ -453,7 +588,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             }
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sh.base[threadIdx.x][k] = (double)hi[k] + (double)lo[k];
+        for (int k = 0; k < 4; ++k) {
+            sh.bhi[threadIdx.x][k] = hi[k];
+            sh.blo[threadIdx.x][k] = lo[k];
+        }
     }
     if (threadIdx.x == 0) sh.any_active = 1;
     __syncthreads();
@@ -463,7 +601,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     R *part = tile + step_tile_slots(TX, TS) * TS + grp * step_part_stride(LPN) + lane;
     int it = 0;                                   // iterations of this block
     int my_it = 0, my_conv = 0, my_stall = 0;     // warp-0 lane bookkeeping for node threadIdx.x
-    double my_res = 1e300;                        // previous residual of that node
+    float my_res = 3.0e38f;                       // previous residual of that node
     const int kk = lane & 3, m1 = (lane >> 2) & 3, m2 = m1 + 2;
     while (sh.any_active && it < p.max_iter) {
         ++it;
@@ -537,41 +675,25 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             }
         }
         __syncthreads();
-        // warp 0: moments, e -> T, EoS, residual in FP64 for node j = threadIdx.x
+        // warp 0: moments, e -> T, EoS, residual for node j = threadIdx.x, in FP64 (FP64
+        // form) or float-float (FP32 form)
         if (threadIdx.x < STEP_NB) {
             const int j = threadIdx.x;
             if (sh.active[j]) {
-                const double dt = p.dt;
-                const double Fxd = (double)sh.nl[j][0], Fyd = (double)sh.nl[j][1];
-                const double rEd = (double)sh.nl[j][2];
                 const R thr = sh.lam[j][0];
-                const double thd = (double)thr, uxd = (double)sh.lam[j][1], uyd = (double)sh.lam[j][2];
                 const R sr = sqrt_(thr);
-                const double sd = (double)sr;
-                const double rho = sh.base[j][0] + (double)sh.dsum[j][0];
-                const double irho = rcp_d(rho);
-                const double dux = sd * (sh.base[j][1] + (double)sh.dsum[j][1]) * irho;
-                const double duy = sd * (sh.base[j][2] + (double)sh.dsum[j][2]) * irho;
-                const double uxs = uxd + dux, uys = uyd + duy;
-                const double uhx = uxs + 0.5 * Fxd * dt * irho, uhy = uys + 0.5 * Fyd * dt * irho;
-                const double gs = sh.base[j][3] + (double)sh.dsum[j][3];
-                const double E = 0.5 * gs * irho;
-                const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEd * irho;
-                const double T = (e + p.a * rho) * p.pd.inv_cv;
-                const double pr = rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho;
-                const double P = pr > p.p_floor ? pr : p.p_floor;
-                const double ths = P * irho * 3.0;
-                const double dth = ths - thd;
-                // relative change of the gauge (FP64 differences, FP32 scaling suffices)
-                const float rth = (float)fabs(dth) / (float)thr;
-                const float rux = (float)fabs(dux) / (float)sr, ruy = (float)fabs(duy) / (float)sr;
-                const double res = (double)fmaxf(rth, fmaxf(rux, ruy));
-                const bool conv = res <= p.tol;
+                EosOut<R> o;
+                eos_update(p, sh.bhi[j], sh.blo[j], sh.dsum[j], sh.nl[j], sh.lam[j], sr, o);
+                // relative change of the gauge
+                const float rth = fabsf((float)o.dth) / (float)thr;
+                const float rux = fabsf((float)o.dux) / (float)sr, ruy = fabsf((float)o.duy) / (float)sr;
+                const float res = fmaxf(rth, fmaxf(rux, ruy));
+                const bool conv = sizeof(R) == 4 ? res <= p.tol_f : (double)res <= p.tol;
                 const bool bad = !(res == res);
                 // FP32 form only: the streamed moments carry FP32 rounding that the EoS
                 // cancellation inside interfaces can lift above tol; once a corrector no
                 // longer halves the residual the iteration has reached that floor and stops.
-                const bool stall = sizeof(R) == 4 && it >= 2 && !conv && res > 0.5 * my_res;
+                const bool stall = sizeof(R) == 4 && it >= 2 && !conv && res > 0.5f * my_res;
                 my_res = res;
                 my_it = it;
                 if (conv || bad || stall || it >= p.max_iter) {
@@ -579,16 +701,15 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     my_conv = conv || stall;
                     my_stall = stall;
                     R *m = sh.mac[j];
-                    m[0] = (R)rho; m[1] = (R)uxs; m[2] = (R)uys; m[3] = (R)uhx; m[4] = (R)uhy;
-                    m[5] = (R)E; m[6] = (R)T; m[7] = (R)P; m[8] = (R)ths; m[9] = (R)pr;
-                    sh.dlam[j][0] = (R)dth; sh.dlam[j][1] = (R)dux; sh.dlam[j][2] = (R)duy;
-                    const R rh = (R)rho, gh = (R)gs;
-                    sh.hilo[j][0] = rh; sh.hilo[j][1] = (R)(rho - (double)rh);
-                    sh.hilo[j][2] = gh; sh.hilo[j][3] = (R)(gs - (double)gh);
+                    m[0] = o.rho_hi; m[1] = o.uxs; m[2] = o.uys; m[3] = o.uhx; m[4] = o.uhy;
+                    m[5] = o.E; m[6] = o.T; m[7] = o.P; m[8] = o.ths; m[9] = o.pr;
+                    sh.dlam[j][0] = o.dth; sh.dlam[j][1] = o.dux; sh.dlam[j][2] = o.duy;
+                    sh.hilo[j][0] = o.rho_hi; sh.hilo[j][1] = o.rho_lo;
+                    sh.hilo[j][2] = o.gs_hi; sh.hilo[j][3] = o.gs_lo;
                 } else {
-                    sh.lam[j][0] = (R)ths;
-                    sh.lam[j][1] = (R)uxs;
-                    sh.lam[j][2] = (R)uys;
+                    sh.lam[j][0] = o.ths;
+                    sh.lam[j][1] = o.uxs;
+                    sh.lam[j][2] = o.uys;
                 }
             }
             const int any = __any_sync(STEP_NB_MASK, sh.active[j]);
