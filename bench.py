@@ -295,6 +295,15 @@ def other_configs(pond, torch, stream) -> dict:
             sim.close()
             out["%s/%s" % (name, prec)] = {"mlups": w.nodes / ms / 1e3, "ms_per_step": ms,
                                            "streams_per_node": st["streams"] / max(1, st["node_updates"])}
+    # the speed-of-sound experiment (saturated liquid at 0.9 T_cr): pulse speed from the
+    # simulated pressure field, sampled every ~5 time units (closed form: 0.53588)
+    from paper_2002_09217_gb300 import experiments
+    w = inputs.sound_pulse(0.9, "liquid", nx=2048, width=12.0)
+    t0 = time.perf_counter()
+    res = experiments.sound_speed(w, "mixed", stream=stream)
+    el = time.perf_counter() - t0
+    out["%s/mixed" % w.name] = {"c_measured": res["c"], "steps": res["steps"], "wall_s": el,
+                                "mlups_incl_sampling": w.nodes * res["steps"] / el / 1e6}
     return out
 
 

@@ -150,7 +150,11 @@ pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 
 /* Full state as 25 host planes of nx*ny doubles: f_0..f_8, g_0..g_8, theta, u_x,
  * u_y (the gauge the populations are stored in), rho, T, uhat_x, uhat_y.
- * pond_get_state synchronises; pond_set_state replaces the current state. */
+ * pond_get_state synchronises; pond_set_state replaces the current state.  In the mixed
+ * form the library keeps, beside each node's FP32 populations, what storage rounding
+ * took from mass, energy and momentum: f_4 and g_4 are exchanged with it (as doubles;
+ * set_state splits them again), the momentum part (below one FP32 ulp of the
+ * populations) is not exchanged and set_state clears it. */
 pond_status pond_get_state(pond_ctx *ctx, double *state);
 pond_status pond_set_state(pond_ctx *ctx, const double *state);
 

@@ -1,6 +1,7 @@
 """Writes ``paper_2002_09217_gb300/workloads.json``: the thermodynamic constants
 that the synthetic workloads are built from (coexistence densities by Maxwell's
-rule, Rankine-Hugoniot post-shock states, the per-temperature time step).
+rule, Rankine-Hugoniot post-shock states, the per-temperature time step, the time step of
+uniform saturated states and of the critical state for the sound-pulse experiments).
 
 Run: ``python -m oracle.write_workloads``.  It calls only ``oracle.thermo``; the
 JSON file is data that the input generators read, so no product code executes
@@ -60,6 +61,12 @@ def main() -> None:
         "coexistence": coex,
         "shock": shocks,
         "supercritical_1.10": {"dt": dt_rule(sup_rho, 1.1 * Tc)},
+        # sound-pulse experiments: the time step of a uniform saturated vapour or liquid
+        # (each by the rule at its own state), and of the critical state
+        "sound": dict({"%.2f" % (k / 100.0): {
+            "dt_v": dt_rule(coex["%.2f" % (k / 100.0)]["rho_v"], k / 100.0 * Tc),
+            "dt_l": coex["%.2f" % (k / 100.0)]["dt"]} for k in range(70, 96)},
+            critical={"dt": dt_rule(rc, Tc)}),
     }
     with open(OUT, "w") as fh:
         json.dump(data, fh, indent=1, sort_keys=True)

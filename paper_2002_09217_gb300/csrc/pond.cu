@@ -477,6 +477,13 @@ pond_status pond_get_state(pond_ctx *c, double *state)
         for (size_t n = 0; n < N; ++n)
             state[(size_t)p * N + n] = mixed(c) ? (double)f[n * SL + o] : d[n * SL + o];
     }
+    // the rest populations with their kept low parts (the momentum low parts, below one
+    // ulp of the populations, are not part of the exchanged state)
+    for (int k = 0; k < 2; ++k) {
+        const int p = k == 0 ? P_F + 4 : P_G + 4, lo = k == 0 ? P_F4LO : P_G4LO;
+        for (size_t n = 0; n < N; ++n)
+            state[(size_t)p * N + n] += mixed(c) ? (double)f[n * SL + lo] : d[n * SL + lo];
+    }
     return POND_OK;
 }
 
@@ -495,6 +502,13 @@ pond_status pond_set_state(pond_ctx *c, const double *state)
             else d[n * SL + o] = state[(size_t)p * N + n];
         }
     }
+    // FP32 form: the rest populations keep the part below their float as the low word
+    if (mixed(c))
+        for (int k = 0; k < 2; ++k) {
+            const int p = k == 0 ? P_F + 4 : P_G + 4, lo = k == 0 ? P_F4LO : P_G4LO;
+            for (size_t n = 0; n < N; ++n)
+                f[n * SL + lo] = (float)(state[(size_t)p * N + n] - (double)f[n * SL + p]);
+        }
     const void *src = mixed(c) ? (const void *)f.data() : (const void *)d.data();
     CK(cudaMemcpyAsync(c->state[c->cur], src, rec * c->esize, cudaMemcpyHostToDevice, c->stream),
        "cudaMemcpyAsync H2D");

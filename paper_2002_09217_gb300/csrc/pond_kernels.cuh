@@ -4,7 +4,14 @@
 // 128 bytes in FP32 so that a node is one cache line and its 21 streamed values are read
 // with six 16-byte loads:
 //   [0..8] f_0..f_8, [9..17] g_0..g_8, [18] theta, [19] u_x, [20] u_y, [21] spare,
-//   [22] rho, [23] T, [24] uhat_x, [25] uhat_y, [26..31] unused
+//   [22] rho, [23] T, [24] uhat_x, [25] uhat_y, [26] f_4 lo, [27] g_4 lo, [28] j_x lo,
+//   [29] j_y lo, [30..31] unused
+// where the lo values are what storage rounding took from the conserved sums: f_4 lo and
+// g_4 lo the remainders of the rest populations (which hold the exact remainder of mass
+// and energy), j lo the difference between the exact post-collision momentum and that of
+// the stored populations.  The next step's exact sums add them back, so changes smaller
+// than half an ulp of the populations (which FP32 storage alone would drop every step at
+// the weak edge of a wave) are kept.
 // with population index i = 3*(cy+1) + (cx+1).  R = float (mixed form) or double.
 // The ABI's state planes (f, g, theta, u_x, u_y, rho, T, uhat_x, uhat_y) map to record
 // offsets by rec_off().
@@ -18,7 +25,8 @@ namespace pond {
 constexpr int NPL = 25;   // planes of the ABI state
 constexpr int SL = 32;    // values per node record on the device
 enum : int { P_F = 0, P_G = 9, P_TH = 18, P_UX = 19, P_UY = 20, P_SQ = 21, P_RHO = 22, P_T = 23,
-             P_UHX = 24, P_UHY = 25 };   // P_SQ: spare value, sqrt(theta) in staged copies
+             P_UHX = 24, P_UHY = 25, P_F4LO = 26, P_G4LO = 27, P_JXLO = 28, P_JYLO = 29 };
+// (P_SQ: sqrt(theta) in the staged copies)
 __host__ __device__ constexpr int rec_off(int plane) { return plane < 21 ? plane : plane + 1; }
 // value `off` of node n's record
 #define REC(buf, n, off) (buf)[(size_t)(n) * SL + (off)]
@@ -143,6 +151,10 @@ __global__ void k_init(DevParams p, const double *__restrict__ rho, const double
     REC(st, n, P_T) = (R)t;
     REC(st, n, P_UHX) = (R)ux[n];
     REC(st, n, P_UHY) = (R)uy[n];
+    REC(st, n, P_F4LO) = (R)0;
+    REC(st, n, P_G4LO) = (R)0;
+    REC(st, n, P_JXLO) = (R)0;
+    REC(st, n, P_JYLO) = (R)0;
 }
 
 template <typename T>
@@ -200,6 +212,7 @@ __global__ void k_conserve1(DevParams p, const R *__restrict__ st, double *part)
         double r = (double)REC(st, n, P_RHO);
         double eg = 0.0;
         for (int i = 0; i < 9; ++i) eg += (double)REC(st, n, P_G + i);
+        eg += (double)REC(st, n, P_G4LO);
         double v[4] = {r, r * (double)REC(st, n, P_UHX), r * (double)REC(st, n, P_UHY), 0.5 * eg};
         for (int k = 0; k < 4; ++k) pair_add(s[k], c[k], v[k], 0.0);
     }

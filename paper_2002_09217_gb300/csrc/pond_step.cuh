@@ -98,6 +98,7 @@ struct StepShared {
     R mac[STEP_NB][10];        // rho, u*x, u*y, uhx, uhy, E, T, P, theta*, p
     R dlam[STEP_NB][3];        // theta* - theta, u*x - ux, u*y - uy (from FP64)
     R hilo[STEP_NB][4];        // rho and sum g~ as (hi, lo) pairs of R
+    R mom[STEP_NB][4];         // sum f~ c_x, sum f~ c_y (gauge units) as (hi, lo) pairs
     R bhi[STEP_NB][4];         // sums of the node's stored f, f cx, f cy, g, error-free as
     R blo[STEP_NB][4];         //   unevaluated (hi, lo) pairs of R
     int active[STEP_NB];
@@ -362,6 +363,7 @@ struct EosOut {
     R E, T, P, pr;      // total energy per mass, temperature, floored and vdW pressure
     R ths;              // theta* = P / (rho T_L)
     R dth, dux, duy;    // theta* - theta, u* - u (the gauge change)
+    R mx_hi, mx_lo, my_hi, my_lo;   // sum f~ c_x, sum f~ c_y as (hi, lo) pairs
 };
 
 // FP64 form: the streamed moments are the stored sums (hi + lo, rounded to FP64) plus the
@@ -376,8 +378,10 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const double *bhi
     const double thd = lam[0], uxd = lam[1], uyd = lam[2];
     const double rho = (bhi[0] + blo[0]) + dsum[0];
     const double irho = rcp_d(rho);
-    const double dux = sr * ((bhi[1] + blo[1]) + dsum[1]) * irho;
-    const double duy = sr * ((bhi[2] + blo[2]) + dsum[2]) * irho;
+    const double mx = (bhi[1] + blo[1]) + dsum[1], my = (bhi[2] + blo[2]) + dsum[2];
+    const double dux = sr * mx * irho;
+    const double duy = sr * my * irho;
+    o.mx_hi = mx; o.mx_lo = 0.0; o.my_hi = my; o.my_lo = 0.0;
     const double uxs = uxd + dux, uys = uyd + duy;
     const double uhx = uxs + 0.5 * Fxd * dt * irho, uhy = uys + 0.5 * Fyd * dt * irho;
     const double gs = (bhi[3] + blo[3]) + dsum[3];
@@ -423,6 +427,7 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const float *bhi,
     const ffv P = floored ? ffv{p.ff_pfl[0], p.ff_pfl[1]} : pr;
     const ffv ths = ff_mul(ff_mul(P, irho), 3.0f);
     o.rho_hi = rho.hi; o.rho_lo = rho.lo; o.gs_hi = gs.hi; o.gs_lo = gs.lo;
+    o.mx_hi = mx.hi; o.mx_lo = mx.lo; o.my_hi = my.hi; o.my_lo = my.lo;
     o.uxs = uxs.hi; o.uys = uys.hi; o.uhx = uhx.hi; o.uhy = uhy.hi;
     o.E = E.hi; o.T = T.hi; o.P = P.hi; o.pr = pr.hi; o.ths = ths.hi;
     o.dth = (ths.hi - lam[0]) + ths.lo;
@@ -462,9 +467,12 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     {
         constexpr int CH = Slot<R>::chunks;
         const int total = WT * HT * CH;
+        // k / WT through the float reciprocal: exact for k < 2^20 (the quotient's fraction
+        // stays >= 0.5 / WT away from an integer)
+        const float iwt = 1.0f / (float)WT;
         for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
             const int k = idx / CH, ch = idx - k * CH;
-            const int cu = k % WT, cv = k / WT;
+            const int cv = (int)(((float)k + 0.5f) * iwt), cu = k - cv * WT;
             const int gxw = bc_wrap(X0 - HALO + cu, p.nx, p.bcx);
             const int gyw = bc_wrap(Y0 - HALO + cv, p.ny, p.bcy);
             const R *src = in + ((size_t)gyw * p.nx + gxw) * SL + ch * (16 / sizeof(R));
@@ -476,7 +484,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         // vdW pressure and p/rho of the stored rho, T (for the non-local terms) into the
         // slot words past the staged values
         for (int k = threadIdx.x; k < WT * HT; k += blockDim.x) {
-            R *sl = tile + ((k / WT) * PT + k % WT) * TS;
+            const int cv = (int)(((float)k + 0.5f) * iwt);
+            R *sl = tile + (cv * PT + (k - cv * WT)) * TS;
             sl[P_SQ] = sqrt_(sl[P_TH]);
             const R r = sl[P_RHO], t = sl[P_T];
             const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
@@ -573,7 +582,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         // (error-free in R: TwoSum cascades, each sum kept as an unevaluated (hi, lo) pair
         // and rounded once to FP64, which keeps the FP64 pipe free in the FP32 form)
         const R *rj = tile + slot_of(X0 + threadIdx.x % TX, Y0 + threadIdx.x / TX) * TS;
-        R hi[4] = {R(0), R(0), R(0), R(0)}, lo[4] = {R(0), R(0), R(0), R(0)};
+        // the stored low parts of mass, momentum and energy (not staged) start the error terms
+        const R *gj = in + ((size_t)min(Y0 + (int)threadIdx.x / TX, p.ny - 1) * p.nx +
+                            min(X0 + (int)threadIdx.x % TX, p.nx - 1)) * SL;
+        R hi[4] = {R(0), R(0), R(0), R(0)}, lo[4] = {gj[P_F4LO], gj[P_JXLO], gj[P_JYLO], gj[P_G4LO]};
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const R f = rj[P_F + i], gv = rj[P_G + i];
@@ -706,6 +718,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     sh.dlam[j][0] = o.dth; sh.dlam[j][1] = o.dux; sh.dlam[j][2] = o.duy;
                     sh.hilo[j][0] = o.rho_hi; sh.hilo[j][1] = o.rho_lo;
                     sh.hilo[j][2] = o.gs_hi; sh.hilo[j][3] = o.gs_lo;
+                    sh.mom[j][0] = o.mx_hi; sh.mom[j][1] = o.mx_lo;
+                    sh.mom[j][2] = o.my_hi; sh.mom[j][3] = o.my_lo;
                 } else {
                     sh.lam[j][0] = o.ths;
                     sh.lam[j][1] = o.uxs;
@@ -720,22 +734,21 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 
     // ---------------- phase 2: collision (one population per lane) -----------------
     if (valid) {
-        // increments of population `lane` (and of population 8 on lane 0 when a group has
-        // 8 lanes) from the node's final stream: the sum of its lanes' partials, read in a
-        // lane-rotated order so that the rows fall on different banks
-        R my_df = 0, my_dg = 0, my_df8 = 0, my_dg8 = 0;
+        // Population `pop` of this lane.  The rest population (4) is stored as the exact
+        // remainder of mass and energy, so with 8 lanes per node lane 4 takes population 8
+        // instead; with 16, lanes 0..8 take their own index (lane 4's result is replaced).
+        const int pop = (LPN == 8 && lane == 4) ? 8 : (lane < 9 ? lane : 8);
+        const bool owner = lane < 9 && pop != 4;
+        // its increment from the node's final stream: the sum of the lanes' partials, read
+        // in a lane-rotated order so that the rows fall on different banks
+        R my_df = 0, my_dg = 0;
         {
             const R *row = part - lane;
-            const int d = lane < 9 ? lane : 8;
 #pragma unroll
             for (int l = 0; l < LPN; ++l) {
                 const int ll = (l + lane) & (LPN - 1);
-                my_df += row[d * LPN + ll];
-                my_dg += row[(9 + d) * LPN + ll];
-                if (LPN == 8) {
-                    my_df8 += row[8 * LPN + ll];
-                    my_dg8 += row[17 * LPN + ll];
-                }
+                my_df += row[pop * LPN + ll];
+                my_dg += row[(9 + pop) * LPN + ll];
             }
         }
         const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
@@ -796,28 +809,32 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                                    - rr * (vx * vx + vy * vy) * iP2 + R(1));
             return om * geq + dtr * (gc + w * work);
         };
-        const R my_x = xstar(lane < 9 ? lane : 8);
-        const R my_x8 = xstar(8);
+        const R my_x = xstar(pop);
+        const R x4 = LPN == 8 ? xstar(4) : R(0);   // no lane holds population 4 then
         R Xs[9];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) Xs[k] = __shfl_sync(gmask, my_x, k, LPN);
-        Xs[8] = LPN > 8 ? __shfl_sync(gmask, my_x, 8, LPN) : my_x8;
-        R fo[2] = {R(0), R(0)}, go[2] = {R(0), R(0)};
-        constexpr int REPS = (9 + LPN - 1) / LPN;
-#pragma unroll
-        for (int rep = 0; rep < REPS; ++rep) {
-            const int i = lane + rep * LPN;
-            if (i < 9) {
+        for (int k = 0; k < 9; ++k) {
+            if (LPN == 8) Xs[k] = k == 4 ? x4 : __shfl_sync(gmask, my_x, k == 8 ? 4 : k, LPN);
+            else Xs[k] = __shfl_sync(gmask, my_x, k, LPN);
+        }
+        R fo, go;
+        {
+            {
+                const int i = pop;
                 const int kx = i % 3, ky = i / 3;
-                const R dfi = rep == 0 ? my_df : my_df8, dgi = rep == 0 ? my_dg : my_dg8;
-                const R ft = pick(fx, i) + dfi, gt = pick(gx, i) + dgi;
+                const R ft = pick(fx, i) + my_df, gt = pick(gx, i) + my_dg;
                 R exk[3], eyl[3], Wsk, Wsl, Whk, Whl;
                 row(kx, wsx, dvx, exk, Wsk, Whk);
                 row(ky, wsy, dvy, eyl, Wsl, Whl);
-                const R Wx = pick(W1, kx) + Wsk, Wy = pick(W1, ky) + Wsl;
-                const R feq = rr * Wx * Wy;
+                const R W1k = pick(W1, kx), W1l = pick(W1, ky);
+                const R Wx = W1k + Wsk, Wy = W1l + Wsl;
+                // f^eq - f~ with the frame-offset increments kept apart from the O(1)
+                // weights: W + Ws rounded in FP32 would keep only the increment's leading
+                // bits (Ws ~ the gauge change of one step, a few ulps of W), and always the
+                // same way, since W is a constant
+                const R dfeq = (rr * W1k * W1l - ft) + rr * (Wsk * W1l + W1k * Wsl + Wsk * Wsl);
                 const R S = rr * (Whk * (Wy + Whl) + Wx * Whl);
-                fo[rep] = ft + om * (feq - ft) + S;
+                fo = ft + om * dfeq + S;
                 // carry X* into the streaming gauge: X = X* + (G* - I) X*
                 R acc = pick(Xs, i);
 #pragma unroll
@@ -833,45 +850,66 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     xcol[b] = kx == 0 ? Xs[3 * b] : (kx == 1 ? Xs[3 * b + 1] : Xs[3 * b + 2]);
 #pragma unroll
                 for (int b = 0; b < 3; ++b) acc += eyl[b] * xcol[b];
-                go[rep] = (R(1) - om) * gt + acc;
+                go = (R(1) - om) * gt + acc;
             }
         }
         // The collision conserves mass exactly and changes the energy by dt (M_0 + 2 uhat.F);
         // the rest population (i = 4) takes the remainder, summed error-free as (hi, lo)
         // pairs, so that the stored populations keep these sums up to one rounding.
+        // The stored momentum (exact pair sums of the stored populations) falls short of the
+        // exact post-collision momentum sum f~ c + F dt / s by its storage rounding; that
+        // difference is kept beside the populations too.
+        R f4 = 0, g4 = 0, f4lo = 0, g4lo = 0, jxlo = 0, jylo = 0;
         {
-            R fh = (lane != 4 ? fo[0] : R(0)), fl = (REPS > 1 && lane == 0 ? fo[1] : R(0));
-            R gh = (lane != 4 ? go[0] : R(0)), gl = (REPS > 1 && lane == 0 ? go[1] : R(0));
-            two_sum_(fh, fl, fh, fl);
-            two_sum_(gh, gl, gh, gl);
+            R fh = owner ? fo : R(0), fl = 0;
+            R gh = owner ? go : R(0), gl = 0;
+            R xh = owner ? R(pop % 3 - 1) * fo : R(0), xl = 0;
+            R yh = owner ? R(pop / 3 - 1) * fo : R(0), yl = 0;
 #pragma unroll
             for (int o = LPN / 2; o > 0; o >>= 1) {
                 const R fh2 = __shfl_xor_sync(gmask, fh, o, LPN), fl2 = __shfl_xor_sync(gmask, fl, o, LPN);
                 const R gh2 = __shfl_xor_sync(gmask, gh, o, LPN), gl2 = __shfl_xor_sync(gmask, gl, o, LPN);
+                const R xh2 = __shfl_xor_sync(gmask, xh, o, LPN), xl2 = __shfl_xor_sync(gmask, xl, o, LPN);
+                const R yh2 = __shfl_xor_sync(gmask, yh, o, LPN), yl2 = __shfl_xor_sync(gmask, yl, o, LPN);
                 R e;
                 two_sum_(fh, fh2, fh, e);
                 fl = fl + fl2 + e;
                 two_sum_(gh, gh2, gh, e);
                 gl = gl + gl2 + e;
+                two_sum_(xh, xh2, xh, e);
+                xl = xl + xl2 + e;
+                two_sum_(yh, yh2, yh, e);
+                yl = yl + yl2 + e;
             }
             if (lane == 4) {
                 // target sums: rho (hi, lo) and sum g~ + dt (M_0 + work)
                 R th_, tl_;
                 two_sum_(sh.hilo[grp][2], dtr * (M0 + work), th_, tl_);
                 tl_ += sh.hilo[grp][3];
-                fo[0] = (sh.hilo[grp][0] - fh) + (sh.hilo[grp][1] - fl);
-                go[0] = (th_ - gh) + (tl_ - gl);
+                // the remainders as (hi, lo) pairs: hi is stored as the population, lo
+                // beside it for the next step's sums
+                R s1, e1;
+                two_sum_(sh.hilo[grp][0], -fh, s1, e1);
+                two_sum_(s1, e1 + (sh.hilo[grp][1] - fl), f4, f4lo);
+                two_sum_(th_, -gh, s1, e1);
+                two_sum_(s1, e1 + (tl_ - gl), g4, g4lo);
+                jxlo = ((sh.mom[grp][0] - xh) + (sh.mom[grp][1] - xl)) + Fx * dtr * inv_s;
+                jylo = ((sh.mom[grp][2] - yh) + (sh.mom[grp][3] - yl)) + Fy * dtr * inv_s;
             }
         }
-        if (lane < 9) {
-            REC(out, n, P_F + lane) = fo[0];
-            REC(out, n, P_G + lane) = go[0];
+        if (owner) {
+            REC(out, n, P_F + pop) = fo;
+            REC(out, n, P_G + pop) = go;
+        }
+        if (lane == 4) {
+            REC(out, n, P_F + 4) = f4;
+            REC(out, n, P_G + 4) = g4;
+            REC(out, n, P_F4LO) = f4lo;
+            REC(out, n, P_G4LO) = g4lo;
+            REC(out, n, P_JXLO) = jxlo;
+            REC(out, n, P_JYLO) = jylo;
         }
         if (lane == 0) {
-            if (REPS > 1) {
-                REC(out, n, P_F + 8) = fo[1];
-                REC(out, n, P_G + 8) = go[1];
-            }
             REC(out, n, P_TH) = th;
             REC(out, n, P_UX) = ux;
             REC(out, n, P_UY) = uy;

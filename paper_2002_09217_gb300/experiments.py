@@ -1,0 +1,60 @@
+"""Experiments of the paper run through the GPU path.
+
+Speed of sound (main text, Fig. 1; SM "Speed of sound"): a small density bump in a
+uniform state (``inputs.sound_pulse``) splits into two sound pulses; the speed of the
+right-going one is the slope of its pressure centroid against time.  The measurement
+uses only the simulated fields, so it can be set against the closed form
+sqrt((dp/drho)_T + T (dp/dT)_rho^2 / (rho^2 C_v)) independently.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import pond
+
+
+def pulse_centroid(p: np.ndarray, x0: float) -> float:
+    """Centroid of the pressure excess of the right-going pulse: positive part of
+    p - p_far over the half domain [x0, x0 + nx/2), where p_far is the pressure at the
+    antipode x0 + nx/2 (not yet reached by either pulse).  p: one row of nx values."""
+    nx = p.shape[0]
+    xs = np.arange(nx, dtype=np.float64)
+    far = p[int(round(x0 + nx / 2)) % nx]
+    sel = (xs >= x0) & (xs < x0 + nx / 2)
+    d = np.clip(p[sel] - far, 0.0, None)
+    tot = d.sum()
+    return float((xs[sel] * d).sum() / tot) if tot > 0 else float("nan")
+
+
+def sound_speed(w, precision: str = "mixed", travel=(0.08, 0.3), stream=None, **kw) -> dict:
+    """Steps the sound-pulse workload `w` on the GPU, samples the right-going pulse's
+    centroid X(t) every ~nx/400 time units until it has travelled travel[1] * nx nodes
+    (or w.steps are done), and fits X = X_0 + c t over the samples with
+    travel[0] * nx <= X - x0 <= travel[1] * nx.  Returns c and the run's bookkeeping."""
+    x0 = w.nx / 4.0
+    chunk = max(1, int(math.ceil(w.nx / 400.0 / w.dt)))
+    ts, xs = [], []
+    done = 0
+    with pond.from_workload(w, precision=precision, stream=stream, **kw) as sim:
+        sim.init_fields(*w.fields())
+        while done < w.steps:
+            n = min(chunk, w.steps - done)
+            sim.step(n)
+            done += n
+            p = sim.moments()["p"].mean(axis=0)
+            X = pulse_centroid(p, x0)
+            ts.append(done * w.dt)
+            xs.append(X)
+            if X - x0 >= travel[1] * w.nx:
+                break
+        stats = sim.stats()
+    t = np.array(ts)
+    X = np.array(xs)
+    m = (X - x0 >= travel[0] * w.nx) & (X - x0 <= travel[1] * w.nx)
+    if m.sum() < 3:
+        raise RuntimeError("sound pulse: too few samples in the fit window (%d)" % m.sum())
+    c, _ = np.polyfit(t[m], X[m], 1)
+    return {"c": float(c), "samples": int(m.sum()), "steps": done, "time": float(t[-1]),
+            "nonfinite": int(stats["nonfinite"])}

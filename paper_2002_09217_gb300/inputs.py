@@ -124,6 +124,33 @@ def droplet(n=512, Tr=0.85, radius=64.0, width=4.0, amp=1e-4, steps=20000, seed=
                     z.copy(), np.full((ny, n), Tr * t_cr()))
 
 
+def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, steps=40000, tau=1.0):
+    """Uniform saturated vapour or liquid at T = Tr T_cr (phase "vapour" / "liquid"), or
+    the critical state (phase "critical"), periodic and at rest, with a Gaussian density
+    bump of relative amplitude `amp` and width `width` nodes at x = nx/4 and the
+    temperature left uniform: the bump splits into two sound pulses and a standing
+    entropy mode (the speed-of-sound benchmark of the main text, Fig. 1).  kappa = 0: a
+    single phase has no interface."""
+    tab = table()
+    if phase == "critical":
+        rho0, T0, dt = tab["critical"]["rho"], tab["critical"]["T"], tab["sound"]["critical"]["dt"]
+        Tr = 1.0
+        name = "soundcrit%dx%d" % (nx, ny)
+    elif phase in ("vapour", "liquid"):
+        rv, rl, _ = coexistence(Tr)
+        row = tab["sound"]["%.2f" % round(Tr, 2)]
+        rho0, dt = (rv, row["dt_v"]) if phase == "vapour" else (rl, row["dt_l"])
+        T0 = Tr * t_cr()
+        name = "sound%s%.2f_%dx%d" % (phase[0], Tr, nx, ny)
+    else:
+        raise ValueError("phase must be vapour, liquid or critical")
+    x = np.arange(nx) + 0.0
+    prof = rho0 * (1.0 + amp * np.exp(-((x - nx / 4) / width) ** 2))
+    rho = np.tile(prof, (ny, 1))
+    z = np.zeros((ny, nx))
+    return Workload(name, nx, ny, 0, 0, Tr, 0.0, tau, dt, steps, rho, z, z.copy(), np.full((ny, nx), T0))
+
+
 def droplet_shock(nx=2048, ny=1024, Tr=0.8, radius=80.0, xc=600.0, x_shock=300.0, Mach=1.5,
                   width=4.0, steps=10000, kappa=0.02, tau=1.0):
     """Droplet at coexistence in its vapour, hit by a planar shock (post-shock state

@@ -43,6 +43,8 @@ def small_cases():
     yield "column1x33", inputs.slab(nx=1, ny=33, Tr=0.9, steps=10)
     yield "single_node", inputs.slab(nx=1, ny=1, Tr=0.9, steps=5)
     yield "strong_shock_Tr0.7_Ma3", inputs.shock_in_vapour(n=20, Tr=0.7, Mach=3.0, steps=12)
+    yield "sound_liquid_96x1", inputs.sound_pulse(0.9, "liquid", nx=96, width=4.0, steps=60)
+    yield "sound_critical_64x2", inputs.sound_pulse(phase="critical", nx=64, ny=2, width=4.0, steps=40)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

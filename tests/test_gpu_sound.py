@@ -1,0 +1,67 @@
+"""Speed-of-sound benchmark (main text, Fig. 1) through the GPU path: the pulse speed
+measured from the simulated pressure field against the closed-form isentropic speed of
+the van der Waals fluid (delta = 1/3), in saturated vapour and liquid over the reduced
+temperatures of the figure and at the critical point.
+
+The FP64 form meets 5e-4.  The mixed form stores the populations in FP32; a pulse of
+relative amplitude 1e-3 changes them by only tens of ulps per step, so the library keeps
+what storage rounding takes from mass, momentum and energy beside each record (without
+that the pulse slows by percents, see `test_oracle_physics.py`); its bar here is 3e-3."""
+import math
+
+import pytest
+
+from oracle import thermo
+from paper_2002_09217_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def experiments():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2002_09217_gb300 import experiments as mod
+    from paper_2002_09217_gb300 import pond
+    pond.load()
+    return mod
+
+
+def closed_form(Tr, phase):
+    rc, Tc, pc = thermo.critical()
+    if phase == "critical":
+        return math.sqrt(2.0 * pc / rc)
+    rv, rl = thermo.maxwell(Tr)
+    return thermo.sound_speed(rv if phase == "vapour" else rl, Tr * Tc, 1.0 / 3.0)
+
+
+@pytest.mark.parametrize("phase", ["vapour", "liquid"])
+@pytest.mark.parametrize("Tr", [0.75, 0.85, 0.95])
+def test_pulse_speed_matches_closed_form_fp64(experiments, Tr, phase):
+    w = inputs.sound_pulse(Tr, phase, nx=2048, width=12.0)
+    res = experiments.sound_speed(w, "fp64")
+    assert res["nonfinite"] == 0
+    assert res["c"] == pytest.approx(closed_form(Tr, phase), rel=5e-4), res
+
+
+@pytest.mark.parametrize("phase", ["vapour", "liquid"])
+@pytest.mark.parametrize("dt_scale", [1.0, 0.25])
+def test_pulse_speed_mixed_form(experiments, phase, dt_scale):
+    """Also at a quarter of the time step, where each step's change is 4x fewer ulps."""
+    import dataclasses
+    w = inputs.sound_pulse(0.85, phase, nx=2048, width=12.0)
+    w = dataclasses.replace(w, dt=w.dt * dt_scale, steps=int(w.steps / dt_scale))
+    res = experiments.sound_speed(w, "mixed")
+    assert res["nonfinite"] == 0
+    assert res["c"] == pytest.approx(closed_form(0.85, phase), rel=3e-3), res
+
+
+def test_critical_point_speed(experiments):
+    """Finite at the critical point although (dp/drho)_T = 0; the wide pulse comes within
+    1.5 % of sqrt(2 p_cr v_cr), a narrower one is slower (dissipation)."""
+    want = closed_form(1.0, "critical")
+    wide = experiments.sound_speed(inputs.sound_pulse(phase="critical", nx=4096, width=24.0), "fp64")
+    narrow = experiments.sound_speed(inputs.sound_pulse(phase="critical", nx=2048, width=8.0), "fp64")
+    assert wide["c"] == pytest.approx(want, rel=0.015), wide
+    assert narrow["c"] < wide["c"] < want * 1.005

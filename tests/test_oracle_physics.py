@@ -8,6 +8,9 @@ independently of the scheme.
   of the energy population that falls at high order under refinement;
 - flat liquid-vapour interface: bulk densities against Maxwell's equal-area rule
   (main text, Fig. 2);
+- speed of sound (main text, Fig. 1): a pressure pulse in saturated vapour and liquid
+  travels at the closed-form isentropic speed; at the critical point the measured speed
+  converges to sqrt(2 p_cr v_cr) as the pulse widens;
 - lagged interface / heat-flux terms against 1-D finite differences written here;
 - thermodynamics: critical point, equal-area rule by quadrature, Rankine-Hugoniot
   closed form against a direct root solve.
@@ -80,6 +83,92 @@ def test_galilean_boost_is_a_shift():
     for k in ("rho", "ux", "T", "p"):
         assert fine[k] < coarse[k] / 16.0, (k, coarse, fine)
     assert coarse["T"] < 1e-7 and coarse["uy"] < 1e-13, coarse
+
+
+def _oracle_pulse_speed(w, travel=0.3):
+    """Speed of the right-going pressure pulse of an oracle run: slope of its centroid
+    between the times it has travelled ~travel/3 and ~travel of the box."""
+    P = oracle.Params(nx=w.nx, ny=w.ny, dt=w.dt, tau=w.tau, kappa=w.kappa, delta=w.delta,
+                      p_floor=w.p_floor)
+    st = oracle.init_state(P, *w.fields())
+    x0 = w.nx / 4.0
+    c_guess = thermo.sound_speed(w.rho[0, w.nx // 2], w.T[0, 0], w.delta)
+    n2 = int(round(travel * w.nx / c_guess / w.dt))
+    n1 = n2 // 3
+    xs = np.arange(w.nx)
+    sel = (xs >= x0) & (xs < x0 + w.nx / 2)
+    cents = []
+    done = 0
+    for n in (n1, n2):
+        st = oracle.step(P, st, n - done)
+        done = n
+        p = oracle.moments(P, st)["p"].mean(axis=0)
+        d = np.clip(p[sel] - p[int(x0 + w.nx / 2) % w.nx], 0.0, None)
+        cents.append((xs[sel] * d).sum() / d.sum())
+    return (cents[1] - cents[0]) / ((n2 - n1) * w.dt), c_guess
+
+
+@pytest.mark.parametrize("phase", ["vapour", "liquid"])
+def test_sound_pulse_travels_at_the_isentropic_speed(phase):
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.sound_pulse(0.9, phase, nx=400, width=6.0)
+    c, c_th = _oracle_pulse_speed(w)
+    # the closed form at the tabulated state (not the measurement's own guess)
+    rv, rl = thermo.maxwell(0.9)
+    want = thermo.sound_speed(rv if phase == "vapour" else rl, 0.9 * thermo.critical()[1], 1.0 / 3.0)
+    assert c == pytest.approx(want, rel=1e-3)
+    # the isothermal speed is clearly lower: the pulse is adiabatic, as it must be
+    rho0 = rv if phase == "vapour" else rl
+    T0 = 0.9 * thermo.critical()[1]
+    c_T = math.sqrt(T0 / (1 - thermo.B_VDW * rho0) ** 2 - 2 * thermo.A_VDW * rho0)
+    assert c > c_T * 1.05
+
+
+def test_fp32_population_storage_slows_a_weak_pulse():
+    """Why the mixed form's pulse is slower: rounding only the stored populations to FP32
+    after every step (all arithmetic FP64) already slows a 1e-3 pulse by about a
+    percent to a few percent, the more the smaller dt (a smaller per-step change is fewer
+    ulps of the populations); rounding the stored gauge alone changes nothing."""
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.sound_pulse(0.85, "vapour", nx=256, width=6.0)
+    want = thermo.sound_speed(w.rho[0, w.nx // 2], w.T[0, 0], w.delta)
+
+    def run(planes, dt):
+        P = oracle.Params(nx=w.nx, ny=1, dt=dt, tau=w.tau, kappa=0.0, delta=w.delta, p_floor=w.p_floor)
+        st = oracle.init_state(P, *w.fields())
+        x0 = w.nx / 4.0
+        xs = np.arange(w.nx)
+        sel = (xs >= x0) & (xs < x0 + w.nx / 2)
+        cents, done = [], 0
+        n2 = int(round(0.3 * w.nx / want / dt))
+        for n in (n2 // 3, n2):
+            for _ in range(n - done):
+                st = oracle.step(P, st, 1)
+                st[planes] = st[planes].astype(np.float32).astype(np.float64)
+            done = n
+            p = oracle.moments(P, st)["p"][0]
+            d = np.clip(p[sel] - p[int(x0 + w.nx / 2)], 0.0, None)
+            cents.append((xs[sel] * d).sum() / d.sum())
+        return (cents[1] - cents[0]) / ((n2 - n2 // 3) * dt) / want - 1.0
+
+    pops, gauge = slice(0, 18), slice(18, 21)
+    assert abs(run(gauge, 0.125)) < 1e-3
+    e_quarter, e_eighth = run(pops, 0.25), run(pops, 0.125)
+    assert -0.05 < e_quarter < -0.005, e_quarter
+    assert e_eighth < e_quarter, (e_quarter, e_eighth)
+
+
+def test_sound_speed_at_the_critical_point_converges_with_pulse_width():
+    """(dp/drho)_T = 0 at the critical point, yet the adiabatic speed is finite,
+    sqrt(2 p_cr v_cr); a finite pulse is slowed by dissipation, less so when wider."""
+    from paper_2002_09217_gb300 import inputs
+    rc, Tc, pc = thermo.critical()
+    want = math.sqrt(2.0 * pc / rc)
+    errs = []
+    for nx, width in ((400, 6.0), (800, 12.0)):
+        c, _ = _oracle_pulse_speed(inputs.sound_pulse(phase="critical", nx=nx, width=width))
+        errs.append(abs(c / want - 1.0))
+    assert errs[1] < 0.05 and errs[1] < errs[0] / 2.5, errs
 
 
 def test_flat_interface_coexistence_matches_maxwell():
