@@ -304,6 +304,14 @@ def other_configs(pond, torch, stream) -> dict:
     el = time.perf_counter() - t0
     out["%s/mixed" % w.name] = {"c_measured": res["c"], "steps": res["steps"], "wall_s": el,
                                 "mlups_incl_sampling": w.nodes * res["steps"] / el / 1e6}
+    # the coexistence experiment (flat slab at 0.9 T_cr, delta = 1/3): saturated densities
+    # from the relaxed field (Maxwell: 1.490096 / 5.800446)
+    w = inputs.coexistence_slab(0.9, nx=256, steps=4000)
+    t0 = time.perf_counter()
+    res = experiments.coexistence(w, "mixed", stream=stream)
+    el = time.perf_counter() - t0
+    out["%s/mixed" % w.name] = {"rho_v": res["rho_v"], "rho_l": res["rho_l"], "steps": res["steps"],
+                                "wall_s": el}
     return out
 
 

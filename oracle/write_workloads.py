@@ -1,7 +1,8 @@
 """Writes ``paper_2002_09217_gb300/workloads.json``: the thermodynamic constants
 that the synthetic workloads are built from (coexistence densities by Maxwell's
 rule, Rankine-Hugoniot post-shock states, the per-temperature time step, the time step of
-uniform saturated states and of the critical state for the sound-pulse experiments).
+uniform saturated states and of the critical state for the sound-pulse experiments, the
+time steps of the coexistence-curve cases of Fig. 2).
 
 Run: ``python -m oracle.write_workloads``.  It calls only ``oracle.thermo``; the
 JSON file is data that the input generators read, so no product code executes
@@ -54,6 +55,16 @@ def main() -> None:
                 coex["%.2f" % Tr]["dt"], dt_rule(r1, T1), 0.5 / (1.0 + abs(u1)))}
         shocks["%.2f" % Tr] = row
     sup_rho = 2.0 * rc
+    # the coexistence curve of the main text's Fig. 2: delta = 2/3 (time step by the rule at
+    # the liquid density for that delta) and delta = 1/3 advected at U = 5 U_ch with
+    # U_ch = sqrt(p_cr / rho_cr) (time step also capped at 0.5 / (1 + U))
+    u_ch = math.sqrt(pc / rc)
+    fig2 = {"U_ch": u_ch, "U": 5.0 * u_ch, "dt_delta_2_3": {}, "dt_advected": {}}
+    for k in range(70, 96):
+        key = "%.2f" % (k / 100.0)
+        rl = coex[key]["rho_l"]
+        fig2["dt_delta_2_3"][key] = dt_rule(rl, k / 100.0 * Tc, 2.0 / 3.0)
+        fig2["dt_advected"][key] = min(coex[key]["dt"], 0.5 / (1.0 + 5.0 * u_ch))
     data = {
         "note": "written by oracle/write_workloads.py from oracle/thermo.py (vdW a=2/49, b=2/21, R=1, delta=1/3)",
         "critical": {"rho": rc, "T": Tc, "p": pc},
@@ -61,6 +72,7 @@ def main() -> None:
         "coexistence": coex,
         "shock": shocks,
         "supercritical_1.10": {"dt": dt_rule(sup_rho, 1.1 * Tc)},
+        "figure2": fig2,
         # sound-pulse experiments: the time step of a uniform saturated vapour or liquid
         # (each by the rule at its own state), and of the critical state
         "sound": dict({"%.2f" % (k / 100.0): {

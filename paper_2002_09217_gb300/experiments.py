@@ -1,5 +1,10 @@
 """Experiments of the paper run through the GPU path.
 
+Coexistence (main text, Fig. 2): a liquid slab in its vapour (``inputs.coexistence_slab``)
+relaxes to the saturated densities; they are read as the means of the lowest and highest
+quarter of the density field, which is independent of where the slab is (it moves in the
+advected case).
+
 Speed of sound (main text, Fig. 1; SM "Speed of sound"): a small density bump in a
 uniform state (``inputs.sound_pulse``) splits into two sound pulses; the speed of the
 right-going one is the slope of its pressure centroid against time.  The measurement
@@ -58,3 +63,32 @@ def sound_speed(w, precision: str = "mixed", travel=(0.08, 0.3), stream=None, **
     c, _ = np.polyfit(t[m], X[m], 1)
     return {"c": float(c), "samples": int(m.sum()), "steps": done, "time": float(t[-1]),
             "nonfinite": int(stats["nonfinite"])}
+
+
+def bulk_densities(rho: np.ndarray) -> tuple[float, float]:
+    """(vapour, liquid) bulk densities of a field holding half of each phase: the means
+    of its lowest and highest quarter of values (interfaces take a small share)."""
+    r = np.sort(rho.ravel())
+    q = max(1, r.size // 4)
+    return float(r[:q].mean()), float(r[-q:].mean())
+
+
+def coexistence(w, precision: str = "mixed", settle: float = 0.75, samples: int = 8, stream=None,
+                **kw) -> dict:
+    """Steps the slab workload `w` for settle * w.steps, then averages the bulk densities
+    over `samples` snapshots spread over the remaining steps."""
+    n_settle = int(settle * w.steps)
+    per = max(1, (w.steps - n_settle) // samples)
+    rv, rl = [], []
+    with pond.from_workload(w, precision=precision, stream=stream, **kw) as sim:
+        sim.init_fields(*w.fields())
+        sim.step(n_settle)
+        for _ in range(samples):
+            sim.step(per)
+            v, l = bulk_densities(sim.moments()["rho"])
+            rv.append(v)
+            rl.append(l)
+        stats = sim.stats()
+    return {"rho_v": float(np.mean(rv)), "rho_l": float(np.mean(rl)),
+            "steps": n_settle + samples * per, "nonfinite": int(stats["nonfinite"]),
+            "clamped": int(stats["clamped"])}

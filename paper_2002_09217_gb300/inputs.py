@@ -124,6 +124,36 @@ def droplet(n=512, Tr=0.85, radius=64.0, width=4.0, amp=1e-4, steps=20000, seed=
                     z.copy(), np.full((ny, n), Tr * t_cr()))
 
 
+def coexistence_slab(Tr=0.9, delta=1.0 / 3.0, advected=False, nx=256, ny=1, width=4.0, steps=8000,
+                     kappa=0.02, tau=1.0):
+    """A liquid slab over the middle half of a periodic box in its vapour at the Maxwell
+    densities, T uniform: the coexistence curve of the main text's Fig. 2 for delta = 1/3
+    or 2/3, and for delta = 1/3 advected with the uniform velocity U = 5 U_ch
+    (``advected=True``).  The time step comes from the workload table for each case."""
+    rv, rl, dt = coexistence(Tr)
+    fig = table()["figure2"]
+    key = "%.2f" % round(Tr, 2)
+    U = 0.0
+    if advected:
+        if abs(delta - 1.0 / 3.0) > 1e-12:
+            raise ValueError("the advected case is tabulated for delta = 1/3")
+        U, dt = fig["U"], fig["dt_advected"][key]
+        tag = "adv"
+    elif abs(delta - 2.0 / 3.0) < 1e-12:
+        dt = fig["dt_delta_2_3"][key]
+        tag = "d23"
+    elif abs(delta - 1.0 / 3.0) < 1e-12:
+        tag = "d13"
+    else:
+        raise ValueError("delta must be 1/3 or 2/3")
+    x = np.arange(nx) + 0.5
+    prof = rv + (rl - rv) * 0.5 * (np.tanh((x - nx / 4) / width) - np.tanh((x - 3 * nx / 4) / width))
+    rho = np.tile(prof, (ny, 1))
+    z = np.zeros((ny, nx))
+    return Workload("coex%s%.2f_%dx%d" % (tag, Tr, nx, ny), nx, ny, 0, 0, Tr, kappa, tau, dt, steps, rho,
+                    z + U, z.copy(), np.full((ny, nx), Tr * t_cr()), delta=delta)
+
+
 def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, steps=40000, tau=1.0):
     """Uniform saturated vapour or liquid at T = Tr T_cr (phase "vapour" / "liquid"), or
     the critical state (phase "critical"), periodic and at rest, with a Gaussian density

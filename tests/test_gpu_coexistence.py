@@ -1,0 +1,38 @@
+"""Coexistence curve (main text, Fig. 2) through the GPU path: a flat liquid slab in its
+vapour relaxes to bulk densities on Maxwell's equal-area values, for C_v = R/delta with
+delta = 1/3 and 2/3 (the saturated densities do not depend on delta)."""
+import math
+
+import pytest
+
+from oracle import thermo
+from paper_2002_09217_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def experiments():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2002_09217_gb300 import experiments as mod
+    from paper_2002_09217_gb300 import pond
+    pond.load()
+    return mod
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("delta", [1.0 / 3.0, 2.0 / 3.0])
+@pytest.mark.parametrize("Tr", [0.85, 0.9, 0.95])
+def test_bulk_densities_on_maxwell(experiments, Tr, delta, precision):
+    probe = inputs.coexistence_slab(Tr, delta, nx=256)
+    steps = int(math.ceil(1500.0 / probe.dt))          # the same relaxation time for every dt
+    if precision == "fp64":
+        steps = min(steps, 6000)
+    w = inputs.coexistence_slab(Tr, delta, nx=256, steps=steps)
+    res = experiments.coexistence(w, precision)
+    rv, rl = thermo.maxwell(Tr)
+    assert res["nonfinite"] == 0
+    assert res["rho_v"] == pytest.approx(rv, rel=0.01), res
+    assert res["rho_l"] == pytest.approx(rl, rel=0.01), res

@@ -7,7 +7,7 @@ independently of the scheme.
   nodes) equals the unboosted run shifted by U*dt per step, up to an interpolation error
   of the energy population that falls at high order under refinement;
 - flat liquid-vapour interface: bulk densities against Maxwell's equal-area rule
-  (main text, Fig. 2);
+  (main text, Fig. 2), for delta = 1/3 and 2/3;
 - speed of sound (main text, Fig. 1): a pressure pulse in saturated vapour and liquid
   travels at the closed-form isentropic speed; at the critical point the measured speed
   converges to sqrt(2 p_cr v_cr) as the pulse widens;
@@ -193,6 +193,25 @@ def test_flat_interface_coexistence_matches_maxwell():
         n += 1
     assert acc_v / (2 * n) == pytest.approx(rv, rel=0.01)
     assert acc_l / n == pytest.approx(rl, rel=0.01)
+
+
+def test_coexistence_does_not_depend_on_delta():
+    """Fig. 2: the saturated densities are those of Maxwell's rule also for C_v = 3R/2
+    (delta = 2/3), with its own (smaller) time step."""
+    from paper_2002_09217_gb300 import experiments, inputs
+    w = inputs.coexistence_slab(0.9, 2.0 / 3.0, nx=128, steps=4000)
+    P = oracle.Params(nx=w.nx, ny=w.ny, dt=w.dt, tau=w.tau, kappa=w.kappa, delta=w.delta,
+                      p_floor=w.p_floor)
+    st = oracle.step(P, oracle.init_state(P, *w.fields()), 3000)
+    rv_acc = rl_acc = 0.0
+    for _ in range(5):
+        st = oracle.step(P, st, 200)
+        v, l = experiments.bulk_densities(oracle.moments(P, st)["rho"])
+        rv_acc += v / 5
+        rl_acc += l / 5
+    rv, rl = thermo.maxwell(0.9)
+    assert rv_acc == pytest.approx(rv, rel=0.01)
+    assert rl_acc == pytest.approx(rl, rel=0.01)
 
 
 def test_nonlocal_terms_match_one_dimensional_differences():
