@@ -62,7 +62,7 @@ typedef enum {
 
 enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
 enum { POND_D2Q9 = 0 };                            /* lattice                         */
-enum { POND_VDW = 0, POND_IDEAL = 1 };             /* EoS: IDEAL forces a = b = 0     */
+enum { POND_VDW = 0, POND_IDEAL = 1, POND_DIETERICI = 2 };   /* EoS kind (see pond_eos) */
 enum { POND_FP64 = 0, POND_MIXED = 1 };            /* arithmetic / storage form       */
 
 /* Grid: nx, ny >= 1; bc_x, bc_y: POND_PERIODIC, or POND_ZEROGRAD (index clamp). */
@@ -70,9 +70,19 @@ typedef struct { int32_t nx, ny; int32_t bc_x, bc_y; } pond_grid;
 
 typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9               */
 
-/* van der Waals EoS p = rho R T/(1 - b rho) - a rho^2 with e = (R/delta) T - a rho
- * (main text; SM "Thermodynamics"); 0 < delta <= 2/3. */
-typedef struct { int32_t kind; double a, b, R, delta; } pond_eos;
+/* Equation of state.  POND_VDW: van der Waals p = rho R T/(1 - b rho) - a rho^2 with
+ * e = (R/delta) T - a rho (main text; SM "Thermodynamics"); 0 < delta <= 2/3.
+ * POND_IDEAL: the same with a = b = 0 forced.  POND_DIETERICI: p = rho R T/(1 - b rho)
+ * exp(-a rho/(R T)) (SM "Coexistence curve"); it has no closed caloric equation here, so
+ * it requires isothermal = 1.  isothermal = 1 holds T at T_iso > 0 everywhere (the SM's
+ * isothermal runs): the gauge temperature comes from p(rho, T_iso) and the energy
+ * population then plays no part in the flow; the initial T field should equal T_iso. */
+typedef struct {
+    int32_t kind;
+    double a, b, R, delta;
+    int32_t isothermal;
+    double T_iso;
+} pond_eos;
 
 /* Options.  precision: POND_FP64 (all FP64) or POND_MIXED (FP32 populations and
  * streaming/collision arithmetic; FP64 e->T, EoS, frame residual and sums).

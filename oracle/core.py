@@ -41,7 +41,8 @@ class _CParams(C.Structure):
                 ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("delta", C.c_double),
                 ("kappa", C.c_double), ("tau", C.c_double), ("k_cond", C.c_double),
                 ("p_floor", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
-                ("pad", C.c_int32), ("dt", C.c_double)]
+                ("eos_kind", C.c_int32), ("dt", C.c_double), ("isothermal", C.c_int32),
+                ("pad", C.c_int32), ("T_iso", C.c_double)]
 
 
 @dataclasses.dataclass
@@ -61,11 +62,19 @@ class Params:
     tol: float = 1e-12
     max_iter: int = 20
     dt: float = 1.0
+    eos: str = "vdw"          # "vdw" or "dieterici" (the latter with isothermal only)
+    isothermal: bool = False  # hold T at T_iso
+    T_iso: float = 0.0
 
     def c(self) -> _CParams:
+        if self.eos not in ("vdw", "dieterici"):
+            raise ValueError("eos must be vdw or dieterici")
+        if self.eos == "dieterici" and not self.isothermal:
+            raise ValueError("the Dieterici EoS is used isothermally (no caloric closure)")
         return _CParams(self.nx, self.ny, self.bc_x, self.bc_y, self.a, self.b, self.R,
                         self.delta, self.kappa, self.tau, self.k_cond, self.p_floor, self.tol,
-                        self.max_iter, 0, self.dt)
+                        self.max_iter, 1 if self.eos == "dieterici" else 0, self.dt,
+                        1 if self.isothermal else 0, 0, self.T_iso)
 
 
 def _load():

@@ -68,20 +68,26 @@ static double weight(int i) { return w1d(cx_of(i)) * w1d(cy_of(i)); }
 typedef struct {
     int32_t nx, ny;
     int32_t bc_x, bc_y;      /* 0 = periodic, 1 = zero-gradient (index clamp) */
-    double a, b, R, delta;   /* vdW EoS p = rho R T/(1 - b rho) - a rho^2, C_v = R/delta */
+    double a, b, R, delta;   /* EoS constants (see eos_kind), C_v = R/delta */
     double kappa;            /* Korteweg coefficient */
     double tau;              /* BGK relaxation time, omega = 1/tau */
     double k_cond;           /* conductivity; < 0 selects k = mu (C_v + R) */
     double p_floor;          /* pressure floor for the gauge temperature */
     double tol;              /* frame-search tolerance */
     int32_t max_iter;        /* maximum number of streams per node and step */
-    int32_t pad;
+    int32_t eos_kind;        /* 0: van der Waals p = rho R T/(1 - b rho) - a rho^2;
+                                1: Dieterici p = rho R T/(1 - b rho) exp(-a rho/(R T)) (SM) */
     double dt;               /* time step delta t (lattice spacing Delta x = 1) */
+    int32_t isothermal;      /* 1: T is held at T_iso (the SM's isothermal runs) */
+    int32_t pad;
+    double T_iso;
 } orc_params;
 
 /* ------------------------------ EoS ------------------------------------- */
 static double eos_p(const orc_params *P, double rho, double T)
 {
+    if (P->eos_kind == 1)   /* Dieterici (SM "Coexistence curve") */
+        return rho * P->R * T / (1.0 - P->b * rho) * exp(-P->a * rho / (P->R * T));
     return rho * P->R * T / (1.0 - P->b * rho) - P->a * rho * rho;
 }
 static double eos_e(const orc_params *P, double rho, double T)
@@ -413,7 +419,8 @@ void orc_macro(const orc_params *P, const double lam[3], const double ft[9], con
     double uhx = ux + Fx * P->dt / (2.0 * rho), uhy = uy + Fy * P->dt / (2.0 * rho);
     double E = sg / (2.0 * rho);
     double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEl / rho;
-    double T = eos_T_of_e(P, rho, e);
+    /* isothermal runs hold T; the energy moments then play no part in theta */
+    double T = P->isothermal ? P->T_iso : eos_T_of_e(P, rho, e);
     double p = eos_p(P, rho, T);
     double Pg = p > P->p_floor ? p : P->p_floor;
     out[0] = rho; out[1] = ux; out[2] = uy; out[3] = uhx; out[4] = uhy;

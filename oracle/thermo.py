@@ -131,3 +131,65 @@ def post_shock_for_mach(rho0: float, T0: float, Mach: float, delta: float,
     M0, u1, p1 = rh_closed_form(rho0, p0, r1, delta, a, b, R)
     T1 = (p1 + a * r1 * r1) * (1.0 - b * r1) / (r1 * R)
     return float(r1), float(u1), float(p1), float(T1)
+
+
+# ---------------------------------------------------------------------------------------
+# Dieterici fluid (SM "Coexistence curve", used isothermally there):
+#   p = rho R T / (1 - b rho) exp(-a rho / (R T)),
+# critical point rho_cr = 1/(2b), T_cr = a/(4 R b), p_cr = a / (2 e b)^2.  The workloads
+# take b = 1/7, a = 32/441, which put the critical point at rho_cr = 3.5, T_cr = 8/63 as
+# for the van der Waals constants above.
+A_DIE = 32.0 / 441.0
+B_DIE = 1.0 / 7.0
+
+
+def dieterici_critical(a=A_DIE, b=B_DIE, R=R_GAS):
+    return 1.0 / (2.0 * b), a / (4.0 * R * b), a / (2.0 * math.e * b) ** 2
+
+
+def dieterici_pressure(rho, T, a=A_DIE, b=B_DIE, R=R_GAS):
+    return rho * R * T / (1.0 - b * rho) * np.exp(-a * rho / (R * T))
+
+
+def dieterici_dp_drho_T(rho, T, a=A_DIE, b=B_DIE, R=R_GAS):
+    """(dp/drho)_T = p (1/rho + b/(1 - b rho) - a/(R T))."""
+    return dieterici_pressure(rho, T, a, b, R) * (1.0 / rho + b / (1.0 - b * rho) - a / (R * T))
+
+
+def dieterici_spinodals(T, a=A_DIE, b=B_DIE, R=R_GAS):
+    """Densities where (dp/drho)_T = 0: roots of rho^2 - rho/b + R T/(a b) = 0."""
+    disc = 1.0 / (b * b) - 4.0 * R * T / (a * b)
+    if disc <= 0.0:
+        raise ValueError("no spinodal above the critical temperature")
+    r = math.sqrt(disc)
+    return 0.5 * (1.0 / b - r), 0.5 * (1.0 / b + r)
+
+
+def dieterici_maxwell(Tr: float, a=A_DIE, b=B_DIE, R=R_GAS):
+    """Coexisting (rho_v, rho_l) at T = Tr T_cr: equal pressure p_s and equal areas,
+    integral_{rho_v}^{rho_l} p / rho^2 drho = p_s (1/rho_v - 1/rho_l) (Maxwell's rule in
+    the p-v plane), the saturation pressure found between the spinodal pressures."""
+    from scipy import integrate
+    rc, Tc, pc = dieterici_critical(a, b, R)
+    T = Tr * Tc
+    lo, hi = dieterici_spinodals(T, a, b, R)
+    p_max = dieterici_pressure(lo, T, a, b, R)   # local maximum (vapour spinodal)
+    p_min = dieterici_pressure(hi, T, a, b, R)   # local minimum (liquid spinodal)
+
+    def roots(ps):
+        rv = optimize.brentq(lambda r: dieterici_pressure(r, T, a, b, R) - ps, 1e-12 * lo, lo,
+                             xtol=1e-15, rtol=1e-15)
+        rl = optimize.brentq(lambda r: dieterici_pressure(r, T, a, b, R) - ps, hi,
+                             (1.0 - 1e-12) / b, xtol=1e-15, rtol=1e-15)
+        return rv, rl
+
+    def area(ps):
+        rv, rl = roots(ps)
+        val, _ = integrate.quad(lambda r: dieterici_pressure(r, T, a, b, R) / (r * r), rv, rl,
+                                epsabs=0.0, epsrel=1e-13, limit=200)
+        return val - ps * (1.0 / rv - 1.0 / rl)
+
+    span = p_max - p_min
+    ps = optimize.brentq(area, p_min + 1e-9 * span, p_max - 1e-9 * span, xtol=1e-16, rtol=1e-15)
+    rv, rl = roots(ps)
+    return float(rv), float(rl)

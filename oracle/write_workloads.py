@@ -2,7 +2,8 @@
 that the synthetic workloads are built from (coexistence densities by Maxwell's
 rule, Rankine-Hugoniot post-shock states, the per-temperature time step, the time step of
 uniform saturated states and of the critical state for the sound-pulse experiments, the
-time steps of the coexistence-curve cases of Fig. 2).
+time steps of the coexistence-curve cases of Fig. 2, and the isothermal Dieterici
+coexistence of the SM).
 
 Run: ``python -m oracle.write_workloads``.  It calls only ``oracle.thermo``; the
 JSON file is data that the input generators read, so no product code executes
@@ -36,6 +37,14 @@ def dt_rule(rho: float, T: float, delta: float = DELTA) -> float:
     return float(min(0.5, 0.45 * math.sqrt(theta) / c2))
 
 
+def dt_rule_isothermal_dieterici(rho: float, T: float) -> float:
+    """The same rule with the Dieterici pressure and its isothermal sound speed (the
+    isothermal model carries sound at sqrt((dp/drho)_T))."""
+    p = thermo.dieterici_pressure(rho, T)
+    theta = p / (rho * T_L)
+    return float(min(0.5, 0.45 * math.sqrt(theta) / thermo.dieterici_dp_drho_T(rho, T)))
+
+
 def main() -> None:
     rc, Tc, pc = thermo.critical()
     coex = {}
@@ -55,6 +64,17 @@ def main() -> None:
                 coex["%.2f" % Tr]["dt"], dt_rule(r1, T1), 0.5 / (1.0 + abs(u1)))}
         shocks["%.2f" % Tr] = row
     sup_rho = 2.0 * rc
+    # isothermal Dieterici coexistence (SM "Coexistence curve"): constants, critical point,
+    # Maxwell densities and time step per reduced temperature
+    drc, dTc, dpc = thermo.dieterici_critical()
+    dcoex = {}
+    for k in range(70, 96):
+        Tr = k / 100.0
+        rv, rl = thermo.dieterici_maxwell(Tr)
+        dcoex["%.2f" % Tr] = {"rho_v": rv, "rho_l": rl,
+                              "dt": dt_rule_isothermal_dieterici(rl, Tr * dTc)}
+    dieterici = {"a": thermo.A_DIE, "b": thermo.B_DIE, "critical": {"rho": drc, "T": dTc, "p": dpc},
+                 "coexistence": dcoex}
     # the coexistence curve of the main text's Fig. 2: delta = 2/3 (time step by the rule at
     # the liquid density for that delta) and delta = 1/3 advected at U = 5 U_ch with
     # U_ch = sqrt(p_cr / rho_cr) (time step also capped at 0.5 / (1 + U))
@@ -73,6 +93,7 @@ def main() -> None:
         "shock": shocks,
         "supercritical_1.10": {"dt": dt_rule(sup_rho, 1.1 * Tc)},
         "figure2": fig2,
+        "dieterici": dieterici,
         # sound-pulse experiments: the time step of a uniform saturated vapour or liquid
         # (each by the rule at its own state), and of the critical state
         "sound": dict({"%.2f" % (k / 100.0): {

@@ -262,7 +262,11 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
         (grid->bc_y != POND_PERIODIC && grid->bc_y != POND_ZEROGRAD))
         return POND_EINVAL;
     if (lattice->kind != POND_D2Q9) return POND_EINVAL;
-    if (eos->kind != POND_VDW && eos->kind != POND_IDEAL) return POND_EINVAL;
+    if (eos->kind != POND_VDW && eos->kind != POND_IDEAL && eos->kind != POND_DIETERICI) return POND_EINVAL;
+    if (eos->isothermal != 0 && eos->isothermal != 1) return POND_EINVAL;
+    if (eos->isothermal && !(eos->T_iso > 0.0 && std::isfinite(eos->T_iso))) return POND_EINVAL;
+    if (eos->kind == POND_DIETERICI && (!eos->isothermal || !(eos->a > 0.0) || !(eos->b > 0.0)))
+        return POND_EINVAL;
     if (!(eos->R > 0.0) || !(eos->delta > 0.0) || !(eos->delta <= 2.0 / 3.0 + 1e-12)) return POND_EINVAL;
     if (eos->kind == POND_VDW && (!(eos->a >= 0.0) || !(eos->b >= 0.0))) return POND_EINVAL;
     if (!(kappa >= 0.0) || !(tau > 0.5) || !std::isfinite(tau) || !std::isfinite(kappa)) return POND_EINVAL;
@@ -320,6 +324,10 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     split(d.a, d.ff_a); split(d.b, d.ff_b); split(d.R, d.ff_R); split(d.pd.inv_cv, d.ff_icv);
     split(d.p_floor, d.ff_pfl);
     d.tol_f = (float)d.tol;
+    d.eos_kind = c->eos.kind == POND_DIETERICI ? 2 : 0;
+    d.isothermal = c->eos.isothermal;
+    d.T_iso = c->eos.isothermal ? c->eos.T_iso : 0.0;
+    split(d.T_iso, d.ff_Tiso);
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
     size_t sb = (size_t)SL * c->N * c->esize;

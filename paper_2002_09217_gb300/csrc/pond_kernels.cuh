@@ -54,7 +54,26 @@ struct DevParams {
     // FP64 value to ~2^-48), and its tolerance
     float ff_a[2], ff_b[2], ff_R[2], ff_icv[2], ff_pfl[2];
     float tol_f;
+    // equation of state: 0 van der Waals, 2 Dieterici (isothermal only); isothermal runs
+    // hold T at T_iso (and ff_Tiso, its float pair)
+    int eos_kind, isothermal;
+    double T_iso;
+    float ff_Tiso[2];
 };
+
+template <typename R> __device__ __forceinline__ R exp_(R x);
+template <> __device__ __forceinline__ float exp_(float x) { return expf(x); }
+template <> __device__ __forceinline__ double exp_(double x) { return exp(x); }
+
+// Pressure p(rho, T) of the run's equation of state in type R: van der Waals
+// rho R T/(1 - b rho) - a rho^2 (main text) or Dieterici rho R T/(1 - b rho) exp(-a rho/(R T))
+// (SM "Coexistence curve").
+template <typename R>
+__device__ __forceinline__ R eos_pressure(int kind, R a, R b, R Rg, R r, R t)
+{
+    if (kind == 2) return r * Rg * t / (R(1) - b * r) * exp_(-a * r / (Rg * t));
+    return r * Rg * t / (R(1) - b * r) - a * r * r;
+}
 
 template <typename R> __device__ __forceinline__ const TypedParams<R> &typed(const DevParams &p);
 template <> __device__ __forceinline__ const TypedParams<float> &typed<float>(const DevParams &p) { return p.pf; }
@@ -132,7 +151,7 @@ __global__ void k_init(DevParams p, const double *__restrict__ rho, const double
     gy *= 3.0;
     double r = rho[n], t = T[n];
     if (!(r > 0.0) || !(p.b * r < 1.0) || !(t > 0.0)) atomicAdd(&stats->bad_init, 1ull);
-    double pr = r * p.R * t / (1.0 - p.b * r) - p.a * r * r;
+    double pr = eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t);
     double P = pr > p.p_floor ? pr : p.p_floor;
     double th = P / (r * POND_TL), s = sqrt(th);
     double e = p.cv * t - p.a * r;
@@ -180,7 +199,7 @@ __global__ void k_moments(DevParams p, const R *__restrict__ st, double *rho, do
     if (ux) ux[n] = (double)REC(st, n, P_UHX);
     if (uy) uy[n] = (double)REC(st, n, P_UHY);
     if (T) T[n] = t;
-    if (pr) pr[n] = r * p.R * t / (1.0 - p.b * r) - p.a * r * r;
+    if (pr) pr[n] = eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t);
 }
 
 // Error-free sum of two doubles (Knuth TwoSum).

@@ -387,8 +387,10 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const double *bhi
     const double gs = (bhi[3] + blo[3]) + dsum[3];
     const double E = 0.5 * gs * irho;
     const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEd * irho;
-    const double T = (e + p.a * rho) * p.pd.inv_cv;
-    const double pr = rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho;
+    const double T = p.isothermal ? p.T_iso : (e + p.a * rho) * p.pd.inv_cv;
+    const double pr = p.eos_kind == 2
+        ? rho * p.R * T * rcp_d(1.0 - p.b * rho) * exp(-p.a * rho * rcp_d(p.R * T))
+        : rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho;
     const double P = pr > p.p_floor ? pr : p.p_floor;
     const double ths = P * irho * 3.0;
     o.rho_hi = rho; o.rho_lo = 0.0; o.gs_hi = gs; o.gs_lo = 0.0;
@@ -419,10 +421,14 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const float *bhi,
     const ffv E = ff_mul(ff_mul(gs, irho), 0.5f);
     const ffv kin = ff_mul(ff_add(ff_mul(uhx, uhx), ff_mul(uhy, uhy)), 0.5f);
     const ffv e = ff_add(ff_add(E, ff_neg(kin)), ff_neg(ff_mul(irho, nl[2])));
-    const ffv T = ff_mul(ff_add(e, ff_mul(rho, a)), icv);
+    const ffv T = p.isothermal ? ffv{p.ff_Tiso[0], p.ff_Tiso[1]} : ff_mul(ff_add(e, ff_mul(rho, a)), icv);
     const ffv den = ff_add(ff_neg(ff_mul(rho, b)), 1.0f);
-    const ffv pr = ff_add(ff_mul(ff_mul(ff_mul(rho, Rg), T), ff_rcp(den)),
-                          ff_neg(ff_mul(ff_mul(rho, rho), a)));
+    const ffv pre = ff_mul(ff_mul(ff_mul(rho, Rg), T), ff_rcp(den));
+    // Dieterici: a product with no cancellation, so its exponential factor in FP32 (a few
+    // ulps) is enough; van der Waals: the difference in float-float
+    const ffv pr = p.eos_kind == 2
+        ? ff_mul(pre, expf(-(p.pf.a * rho.hi) / (p.pf.R * T.hi)))
+        : ff_add(pre, ff_neg(ff_mul(ff_mul(rho, rho), a)));
     const bool floored = !(pr.hi > p.ff_pfl[0] || (pr.hi == p.ff_pfl[0] && pr.lo > p.ff_pfl[1]));
     const ffv P = floored ? ffv{p.ff_pfl[0], p.ff_pfl[1]} : pr;
     const ffv ths = ff_mul(ff_mul(P, irho), 3.0f);
@@ -488,7 +494,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             R *sl = tile + (cv * PT + (k - cv * WT)) * TS;
             sl[P_SQ] = sqrt_(sl[P_TH]);
             const R r = sl[P_RHO], t = sl[P_T];
-            const R pr = r * q.R * t / (R(1) - q.b * r) - q.a * r * r;
+            const R pr = eos_pressure<R>(p.eos_kind, q.a, q.b, q.R, r, t);
             sl[S_PR] = pr;
             sl[S_PRR] = pr / r;
         }

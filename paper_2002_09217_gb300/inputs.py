@@ -77,6 +77,8 @@ class Workload:
     delta: float = 1.0 / 3.0
     k_cond: float = -1.0
     p_floor: float = 0.05 / 6.0     # 5 % of p_cr
+    eos: str = "vdw"                # or "dieterici" (isothermal)
+    isothermal: bool = False        # T held at its (uniform) initial value
 
     @property
     def nodes(self) -> int:
@@ -154,13 +156,33 @@ def coexistence_slab(Tr=0.9, delta=1.0 / 3.0, advected=False, nx=256, ny=1, widt
                     z + U, z.copy(), np.full((ny, nx), Tr * t_cr()), delta=delta)
 
 
-def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, steps=40000, tau=1.0):
+def dieterici_slab(Tr=0.9, nx=256, ny=1, width=4.0, steps=None, kappa=0.02, tau=1.0):
+    """Isothermal coexistence with the Dieterici EoS (SM "Coexistence curve"): a liquid
+    slab over the middle half of a periodic box in its vapour at the Maxwell densities of
+    that EoS, T held at Tr T_cr; p_floor at 5 % of its p_cr (never reached: the Dieterici
+    pressure is positive).  Default steps: a relaxation time of 1500."""
+    d = table()["dieterici"]
+    row = d["coexistence"]["%.2f" % round(Tr, 2)]
+    rv, rl, dt = row["rho_v"], row["rho_l"], row["dt"]
+    steps = int(math.ceil(1500.0 / dt)) if steps is None else steps
+    x = np.arange(nx) + 0.5
+    prof = rv + (rl - rv) * 0.5 * (np.tanh((x - nx / 4) / width) - np.tanh((x - 3 * nx / 4) / width))
+    rho = np.tile(prof, (ny, 1))
+    z = np.zeros((ny, nx))
+    return Workload("dieterici%.2f_%dx%d" % (Tr, nx, ny), nx, ny, 0, 0, Tr, kappa, tau, dt, steps, rho,
+                    z, z.copy(), np.full((ny, nx), Tr * d["critical"]["T"]), a=d["a"], b=d["b"],
+                    p_floor=0.05 * d["critical"]["p"], eos="dieterici", isothermal=True)
+
+
+def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, steps=40000, tau=1.0,
+                isothermal=False):
     """Uniform saturated vapour or liquid at T = Tr T_cr (phase "vapour" / "liquid"), or
     the critical state (phase "critical"), periodic and at rest, with a Gaussian density
     bump of relative amplitude `amp` and width `width` nodes at x = nx/4 and the
     temperature left uniform: the bump splits into two sound pulses and a standing
     entropy mode (the speed-of-sound benchmark of the main text, Fig. 1).  kappa = 0: a
-    single phase has no interface."""
+    single phase has no interface.  isothermal=True holds T (the SM's isothermal speed of
+    sound)."""
     tab = table()
     if phase == "critical":
         rho0, T0, dt = tab["critical"]["rho"], tab["critical"]["T"], tab["sound"]["critical"]["dt"]
@@ -178,7 +200,8 @@ def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, ste
     prof = rho0 * (1.0 + amp * np.exp(-((x - nx / 4) / width) ** 2))
     rho = np.tile(prof, (ny, 1))
     z = np.zeros((ny, nx))
-    return Workload(name, nx, ny, 0, 0, Tr, 0.0, tau, dt, steps, rho, z, z.copy(), np.full((ny, nx), T0))
+    return Workload(name + ("_iso" if isothermal else ""), nx, ny, 0, 0, Tr, 0.0, tau, dt, steps, rho, z,
+                    z.copy(), np.full((ny, nx), T0), isothermal=isothermal)
 
 
 def droplet_shock(nx=2048, ny=1024, Tr=0.8, radius=80.0, xc=600.0, x_shock=300.0, Mach=1.5,

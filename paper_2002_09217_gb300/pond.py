@@ -17,7 +17,7 @@ from . import build_lib
 
 POND_PERIODIC, POND_ZEROGRAD = 0, 1
 POND_D2Q9 = 0
-POND_VDW, POND_IDEAL = 0, 1
+POND_VDW, POND_IDEAL, POND_DIETERICI = 0, 1, 2
 POND_FP64, POND_MIXED = 0, 1
 NPLANES = 25
 STATUS = {0: "POND_OK", 1: "POND_EINVAL", 2: "POND_ENOMEM", 3: "POND_ECUDA", 4: "POND_ENONCONV",
@@ -37,7 +37,7 @@ class Lattice(C.Structure):
 
 class Eos(C.Structure):
     _fields_ = [("kind", C.c_int32), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
-                ("delta", C.c_double)]
+                ("delta", C.c_double), ("isothermal", C.c_int32), ("T_iso", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -144,7 +144,8 @@ class Simulation:
                  precision: str = "mixed", dt: float = 0.5, tol: float | None = None,
                  max_iter: int = 20, k_cond: float = -1.0, p_floor: float = 1e-3 / 6.0,
                  stream=None, torch_alloc: bool = True, ideal: bool = False,
-                 lanes_per_node: int = 0, tile_x: int = 0):
+                 lanes_per_node: int = 0, tile_x: int = 0, eos: str = "vdw",
+                 isothermal: bool = False, T_iso: float = 0.0):
         torch = _torch()
         self._lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -178,17 +179,21 @@ class Simulation:
             self._cb_alloc, self._cb_free = _ALLOC(), _FREE()
         grid = Grid(self.nx, self.ny, bc_x, bc_y)
         lat = Lattice(POND_D2Q9)
-        eos = Eos(POND_IDEAL if ideal else POND_VDW, a, b, R, delta)
+        if eos not in ("vdw", "dieterici"):
+            raise ValueError("eos must be 'vdw' or 'dieterici'")
+        kind = POND_DIETERICI if eos == "dieterici" else (POND_IDEAL if ideal else POND_VDW)
+        eos_c = Eos(kind, a, b, R, delta, 1 if isothermal else 0, float(T_iso))
         opts = Opts(POND_MIXED if precision == "mixed" else POND_FP64, max_iter, tol, dt, k_cond,
                     p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None,
                     lanes_per_node, tile_x)
         self.params = dict(nx=nx, ny=ny, bc_x=bc_x, bc_y=bc_y, a=a, b=b, R=R, delta=delta,
                            kappa=kappa, tau=tau, precision=precision, dt=dt, tol=tol,
                            max_iter=max_iter, k_cond=k_cond, p_floor=p_floor,
-                           lanes_per_node=lanes_per_node, tile_x=tile_x)
+                           lanes_per_node=lanes_per_node, tile_x=tile_x, eos=eos,
+                           isothermal=isothermal, T_iso=T_iso)
         ctx = C.c_void_p()
         with torch.cuda.device(self._device):
-            st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos), kappa, tau,
+            st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos_c), kappa, tau,
                                        C.byref(opts), C.byref(ctx))
         if st != 0:
             raise PondError(st, "pond_create failed")
@@ -343,6 +348,8 @@ class Batch:
 
 def from_workload(w, precision: str = "mixed", **kw) -> Simulation:
     """Simulation for an ``inputs.Workload`` (parameters only; call init_fields)."""
+    iso = dict(eos=w.eos, isothermal=w.isothermal, T_iso=float(w.T.flat[0]) if w.isothermal else 0.0)
+    iso.update(kw)
     return Simulation(w.nx, w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R, delta=w.delta,
                       kappa=w.kappa, tau=w.tau, precision=precision, dt=w.dt, k_cond=w.k_cond,
-                      p_floor=w.p_floor, **kw)
+                      p_floor=w.p_floor, **iso)

@@ -62,6 +62,11 @@ def test_invalid_parameters_are_rejected_on_the_host(lib):
     bad = pond.Eos(0, 2 / 49, 2 / 21, 1.0, 0.9)                           # delta > 2/3
     assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(bad), 0.0, 1.0,
                          ctypes.byref(opts), ctypes.byref(out)) == 1
+    for bad in (pond.Eos(pond.POND_DIETERICI, 32 / 441, 1 / 7, 1.0, 1 / 3, 0, 0.0),   # not isothermal
+                pond.Eos(0, 2 / 49, 2 / 21, 1.0, 1 / 3, 1, 0.0),                      # T_iso <= 0
+                pond.Eos(5, 2 / 49, 2 / 21, 1.0, 1 / 3)):                             # unknown kind
+        assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(bad), 0.0, 1.0,
+                             ctypes.byref(opts), ctypes.byref(out)) == 1
     assert not out.value
     L.pond_destroy(None)
 

@@ -1,6 +1,7 @@
-"""Coexistence curve (main text, Fig. 2) through the GPU path: a flat liquid slab in its
-vapour relaxes to bulk densities on Maxwell's equal-area values, for C_v = R/delta with
-delta = 1/3 and 2/3 (the saturated densities do not depend on delta)."""
+"""Coexistence curves through the GPU path: a flat liquid slab in its vapour relaxes to
+bulk densities on Maxwell's equal-area values, for the van der Waals fluid with
+C_v = R/delta, delta = 1/3 and 2/3 (main text, Fig. 2: the saturated densities do not
+depend on delta), and for the Dieterici fluid held isothermal (SM "Coexistence curve")."""
 import math
 
 import pytest
@@ -34,5 +35,16 @@ def test_bulk_densities_on_maxwell(experiments, Tr, delta, precision):
     res = experiments.coexistence(w, precision)
     rv, rl = thermo.maxwell(Tr)
     assert res["nonfinite"] == 0
+    assert res["rho_v"] == pytest.approx(rv, rel=0.01), res
+    assert res["rho_l"] == pytest.approx(rl, rel=0.01), res
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("Tr", [0.7, 0.8, 0.9])
+def test_isothermal_dieterici_on_maxwell(experiments, Tr, precision):
+    w = inputs.dieterici_slab(Tr, nx=256, steps=3000)
+    res = experiments.coexistence(w, precision)
+    rv, rl = thermo.dieterici_maxwell(Tr)
+    assert res["nonfinite"] == 0 and res["clamped"] == 0
     assert res["rho_v"] == pytest.approx(rv, rel=0.01), res
     assert res["rho_l"] == pytest.approx(rl, rel=0.01), res

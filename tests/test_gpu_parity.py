@@ -45,6 +45,9 @@ def small_cases():
     yield "strong_shock_Tr0.7_Ma3", inputs.shock_in_vapour(n=20, Tr=0.7, Mach=3.0, steps=12)
     yield "sound_liquid_96x1", inputs.sound_pulse(0.9, "liquid", nx=96, width=4.0, steps=60)
     yield "sound_critical_64x2", inputs.sound_pulse(phase="critical", nx=64, ny=2, width=4.0, steps=40)
+    yield "isothermal_sound_80x1", inputs.sound_pulse(0.9, "vapour", nx=80, width=4.0, steps=50,
+                                                      isothermal=True)
+    yield "dieterici_iso_48x3", inputs.dieterici_slab(0.8, nx=48, ny=3, steps=40)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

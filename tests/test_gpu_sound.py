@@ -65,3 +65,13 @@ def test_critical_point_speed(experiments):
     narrow = experiments.sound_speed(inputs.sound_pulse(phase="critical", nx=2048, width=8.0), "fp64")
     assert wide["c"] == pytest.approx(want, rel=0.015), wide
     assert narrow["c"] < wide["c"] < want * 1.005
+
+
+@pytest.mark.parametrize("precision,bar", [("fp64", 5e-4), ("mixed", 3e-3)])
+def test_isothermal_pulse_speed(experiments, precision, bar):
+    """Held at constant T the fluid carries sound at sqrt((dp/drho)_T) (SM figure of the
+    isothermal speed of sound)."""
+    w = inputs.sound_pulse(0.9, "vapour", nx=2048, width=12.0, isothermal=True)
+    res = experiments.sound_speed(w, precision)
+    cT = math.sqrt(thermo.dp_drho_T(w.rho[0, w.nx // 2], w.T[0, 0]))
+    assert res["c"] == pytest.approx(cT, rel=bar), res

@@ -13,7 +13,11 @@ independently of the scheme.
   converges to sqrt(2 p_cr v_cr) as the pulse widens;
 - lagged interface / heat-flux terms against 1-D finite differences written here;
 - thermodynamics: critical point, equal-area rule by quadrature, Rankine-Hugoniot
-  closed form against a direct root solve.
+  closed form against a direct root solve;
+- the Dieterici EoS (SM "Coexistence curve"): its critical point, the SM's reduced form,
+  Maxwell densities that obey corresponding states and equal chemical potentials, and the
+  oracle's isothermal flat interface on those densities;
+- isothermal runs carry sound at the isothermal speed sqrt((dp/drho)_T) (SM figure).
 """
 import math
 
@@ -294,3 +298,76 @@ def test_sound_speed_at_critical_point():
     delta = 1.0 / 3.0
     dpdT = rc / (1 - thermo.B_VDW * rc)
     assert thermo.sound_speed(rc, Tc, delta) ** 2 == pytest.approx(Tc * dpdT ** 2 * delta / rc ** 2, rel=1e-12)
+
+
+# ------------------------------------------------------------ Dieterici, isothermal
+def test_dieterici_critical_point_and_reduced_form():
+    rc, Tc, pc = thermo.dieterici_critical()
+    h = 1e-4 * rc
+    p = lambda r: thermo.dieterici_pressure(r, Tc)
+    assert p(rc) == pytest.approx(pc, rel=1e-14)
+    assert abs((p(rc + h) - p(rc - h)) / (2 * h)) < 1e-7 * pc / rc
+    assert abs((p(rc + h) - 2 * p(rc) + p(rc - h)) / h ** 2) < 1e-5 * pc / rc ** 2
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        rr, Tr = rng.uniform(0.1, 1.9), rng.uniform(0.6, 1.4)
+        reduced = rr * Tr * math.e ** 2 / (2.0 - rr) * math.exp(-2.0 * rr / Tr)
+        assert thermo.dieterici_pressure(rr * rc, Tr * Tc) / pc == pytest.approx(reduced, rel=1e-13)
+
+
+@pytest.mark.parametrize("Tr", [0.7, 0.85, 0.95])
+def test_dieterici_maxwell_equal_chemical_potential_and_corresponding_states(Tr):
+    rv, rl = thermo.dieterici_maxwell(Tr)
+    rc, Tc, pc = thermo.dieterici_critical()
+    T = Tr * Tc
+    assert thermo.dieterici_pressure(rv, T) == pytest.approx(thermo.dieterici_pressure(rl, T), rel=1e-12)
+    # mu(rho_l) - mu(rho_v) = integral of (dp/drho)_T / rho, by Simpson's rule on the
+    # analytic derivative (a different integrand from the equal-area solve)
+    r = np.linspace(rv, rl, 20001)
+    f = thermo.dieterici_dp_drho_T(r, T) / r
+    dmu = integrate.simpson(f, x=r)
+    assert abs(dmu) < 1e-9 * thermo.dieterici_pressure(rv, T) / rv
+    # other constants, same reduced coexistence
+    a2, b2 = 0.2, 0.05
+    rv2, rl2 = thermo.dieterici_maxwell(Tr, a=a2, b=b2)
+    rc2 = thermo.dieterici_critical(a2, b2)[0]
+    assert rv2 / rc2 == pytest.approx(rv / rc, rel=1e-9)
+    assert rl2 / rc2 == pytest.approx(rl / rc, rel=1e-9)
+
+
+@pytest.mark.parametrize("Tr", [0.75, 0.9])
+def test_isothermal_dieterici_flat_interface_on_maxwell(Tr):
+    from paper_2002_09217_gb300 import experiments, inputs
+    w = inputs.dieterici_slab(Tr, nx=128, steps=3000)
+    P = oracle.Params(nx=w.nx, ny=w.ny, dt=w.dt, tau=w.tau, kappa=w.kappa, a=w.a, b=w.b,
+                      p_floor=w.p_floor, eos="dieterici", isothermal=True, T_iso=w.T[0, 0])
+    st = oracle.step(P, oracle.init_state(P, *w.fields()), w.steps)
+    m = oracle.moments(P, st)
+    v, l = experiments.bulk_densities(m["rho"])
+    rv, rl = thermo.dieterici_maxwell(Tr)
+    assert v == pytest.approx(rv, rel=0.01) and l == pytest.approx(rl, rel=0.01)
+    np.testing.assert_allclose(m["T"], w.T[0, 0], rtol=1e-15)   # held
+
+
+def test_isothermal_pulse_travels_at_the_isothermal_speed():
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.sound_pulse(0.9, "vapour", nx=400, width=6.0, isothermal=True)
+    P = oracle.Params(nx=w.nx, ny=w.ny, dt=w.dt, tau=w.tau, kappa=0.0, delta=w.delta,
+                      p_floor=w.p_floor, isothermal=True, T_iso=w.T[0, 0])
+    rho0, T0 = w.rho[0, w.nx // 2], w.T[0, 0]
+    cT = math.sqrt(thermo.dp_drho_T(rho0, T0))
+    st = oracle.init_state(P, *w.fields())
+    x0 = w.nx / 4.0
+    xs = np.arange(w.nx)
+    sel = (xs >= x0) & (xs < x0 + w.nx / 2)
+    n2 = int(round(0.3 * w.nx / cT / w.dt))
+    cents, done = [], 0
+    for n in (n2 // 3, n2):
+        st = oracle.step(P, st, n - done)
+        done = n
+        p = oracle.moments(P, st)["p"][0]
+        d = np.clip(p[sel] - p[int(x0 + w.nx / 2)], 0.0, None)
+        cents.append((xs[sel] * d).sum() / d.sum())
+    c = (cents[1] - cents[0]) / ((n2 - n2 // 3) * w.dt)
+    assert c == pytest.approx(cT, rel=1e-3)
+    assert c < 0.7 * thermo.sound_speed(rho0, T0, w.delta)
