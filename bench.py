@@ -296,6 +296,19 @@ def other_configs(pond, torch, stream) -> dict:
             sim.close()
             out["%s/%s" % (name, prec)] = {"mlups": w.nodes / ms / 1e3, "ms_per_step": ms,
                                            "streams_per_node": st["streams"] / max(1, st["node_updates"])}
+    # the two-pass step (current-time non-local terms) on the slab: two launches per step
+    w = inputs.config("slab128x4")
+    sim = pond.from_workload(w, precision="mixed", stream=stream, nonlocal_="current")
+    sim.init_fields(*w.fields())
+    sim.step(3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(200)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / 200
+    sim.close()
+    out["slab128x4/mixed/current_time"] = {"mlups": w.nodes / ms / 1e3, "ms_per_step": ms}
     # the speed-of-sound experiment (saturated liquid at 0.9 T_cr): pulse speed from the
     # simulated pressure field, sampled every ~5 time units (closed form: 0.53588)
     from paper_2002_09217_gb300 import experiments

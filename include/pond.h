@@ -64,6 +64,7 @@ enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis         
 enum { POND_D2Q9 = 0 };                            /* lattice                         */
 enum { POND_VDW = 0, POND_IDEAL = 1, POND_DIETERICI = 2 };   /* EoS kind (see pond_eos) */
 enum { POND_FP64 = 0, POND_MIXED = 1 };            /* arithmetic / storage form       */
+enum { POND_NONLOCAL_LAGGED = 0, POND_NONLOCAL_CURRENT = 1 };   /* see pond_opts.nonlocal */
 
 /* Grid: nx, ny >= 1; bc_x, bc_y: POND_PERIODIC, or POND_ZEROGRAD (index clamp). */
 typedef struct { int32_t nx, ny; int32_t bc_x, bc_y; } pond_grid;
@@ -94,7 +95,13 @@ typedef struct {
  * lanes_per_node: threads cooperating on one node in the step kernel, 8 or 16 (0 = 8).
  * tile_x: width of the step kernel's tile of 16 nodes, 1, 2, 4, 8 or 16 (tile height
  * 16 / tile_x; 0 = 16 for grids of fewer than 4 rows, else 4).  Both are performance
- * knobs (autotuning); results are the same to rounding. */
+ * knobs (autotuning); results are the same to rounding.
+ * nonlocal: time level of the Korteweg force, interface energy and heat-flux source,
+ * which the paper leaves open.  POND_NONLOCAL_LAGGED (0): from rho, T at t - dt (one
+ * launch per step).  POND_NONLOCAL_CURRENT (1): two passes per step, the first a lagged
+ * step predicting rho, T at t, the second the step redone from the same state with the
+ * terms of that prediction; it holds a third state buffer, and such a context cannot join
+ * a batch. */
 typedef struct {
     int32_t precision;
     int32_t max_iter;
@@ -108,6 +115,7 @@ typedef struct {
     void *alloc_ctx;
     int32_t lanes_per_node;
     int32_t tile_x;
+    int32_t nonlocal;
 } pond_opts;
 
 /* Device counters accumulated since the last pond_stats() call that reset them. */

@@ -65,6 +65,8 @@ class Params:
     eos: str = "vdw"          # "vdw" or "dieterici" (the latter with isothermal only)
     isothermal: bool = False  # hold T at T_iso
     T_iso: float = 0.0
+    nonlocal_: str = "lagged"  # non-local terms from t - dt ("lagged") or from a first
+                               # pass's prediction of t ("current", two passes per step)
 
     def c(self) -> _CParams:
         if self.eos not in ("vdw", "dieterici"):
@@ -98,6 +100,8 @@ def _load():
         lib.orc_collide.restype = C.c_int
         lib.orc_step.argtypes = [pp, dp, dp, dp]
         lib.orc_step.restype = C.c_int
+        lib.orc_step_nl.argtypes = [pp, dp, dp, dp, dp]
+        lib.orc_step_nl.restype = C.c_int
         lib.orc_step_nodes.argtypes = [pp, dp, C.POINTER(C.c_int64), C.c_int64, dp, dp]
         lib.orc_step_nodes.restype = C.c_int
         lib.orc_moments.argtypes = [pp, dp, dp, dp, dp, dp, dp]
@@ -203,8 +207,17 @@ def step(P: Params, state, n: int = 1, stats=None) -> np.ndarray:
     st = np.zeros(4)
     cp = P.c()
     lib = _load()
+    if P.nonlocal_ not in ("lagged", "current"):
+        raise ValueError("nonlocal_ must be lagged or current")
+    pred = np.empty_like(cur) if P.nonlocal_ == "current" else None
     for _ in range(n):
-        rc = lib.orc_step(C.byref(cp), _p(cur), _p(nxt), _p(st))
+        if pred is None:
+            rc = lib.orc_step(C.byref(cp), _p(cur), _p(nxt), _p(st))
+        else:
+            # pass 1: the lagged step predicts rho, T at t; pass 2 redoes the step from the
+            # same state with the non-local terms of that prediction
+            rc = lib.orc_step(C.byref(cp), _p(cur), _p(pred), None)
+            rc = rc or lib.orc_step_nl(C.byref(cp), _p(cur), _p(pred), _p(nxt), _p(st))
         if rc:
             raise FloatingPointError("oracle step failed (singular moment matrix)")
         cur, nxt = nxt, cur

@@ -536,16 +536,19 @@ int orc_stream_node(const orc_params *P, const double *state, int X, int Y, cons
     return rc;
 }
 
-/* Full time step of the whole grid.  stats[0] += streams, stats[1] += non-converged
- * nodes, stats[2] += nodes with p < p_floor, stats[3] += numerical failures.
- * Returns 0 on success. */
-int orc_step(const orc_params *P, const double *in, double *out, double stats[4])
+/* Full time step of the whole grid from the state `in`, with the non-local terms (F,
+ * rho E_lambda, M_0) built from the rho and T planes of the state `nl_src`: `in` itself
+ * for the lagged reading, or a first pass's result for the current-time one.
+ * stats[0] += streams, stats[1] += non-converged nodes, stats[2] += nodes with
+ * p < p_floor, stats[3] += numerical failures.  Returns 0 on success. */
+int orc_step_nl(const orc_params *P, const double *in, const double *nl_src, double *out,
+                double stats[4])
 {
     int64_t N = (int64_t)P->nx * P->ny;
     double *mf = malloc(sizeof(double) * 9 * N), *mg = malloc(sizeof(double) * 9 * N);
     double *nl = malloc(sizeof(double) * 4 * N);
     node_moments(P, in, mf, mg);
-    orc_nonlocal(P, in + PL_RHO * N, in + PL_T * N, nl);
+    orc_nonlocal(P, nl_src + PL_RHO * N, nl_src + PL_T * N, nl);
     double its = 0.0, nonconv = 0.0, clamp = 0.0, fail = 0.0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : its, nonconv, clamp, fail)
     for (int64_t n = 0; n < N; ++n) {
@@ -562,6 +565,12 @@ int orc_step(const orc_params *P, const double *in, double *out, double stats[4]
     free(mf); free(mg); free(nl);
     if (stats) { stats[0] += its; stats[1] += nonconv; stats[2] += clamp; stats[3] += fail; }
     return fail > 0.0;
+}
+
+/* Full time step with the lagged non-local terms (reading R10). */
+int orc_step(const orc_params *P, const double *in, double *out, double stats[4])
+{
+    return orc_step_nl(P, in, in, out, stats);
 }
 
 /* Step only the listed nodes (flat indices y*nx + x) from the full previous state.

@@ -42,6 +42,9 @@ struct pond_ctx {
     int lanes = 8;                 // lanes per node of the step kernel (8 or 16)
     bool initialised = false;
     pond_batch *batch = nullptr;   // batch that steps this context, if any
+    int nonlocal = 0;              // 1: current-time non-local terms (two passes per step)
+    void *pred = nullptr;          // first pass's state (nonlocal = 1)
+    DevStats *dstats_pred = nullptr;
     std::string err;
     size_t bytes = 0;
     DevParams dp{};
@@ -127,8 +130,17 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
     const unsigned nb = (unsigned)(c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty));
     const size_t smem = step_smem_bytes(tx, Slot<R>::stride, (int)sizeof(R), c->lanes);
     if (ev) cudaEventRecord(ev[0], c->stream);
-    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats);
-    else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats);
+    const R *nl = in;
+    if (c->nonlocal) {
+        // pass 1: the lagged step predicts rho, T at t (its counters kept apart); pass 2
+        // redoes the step from the same state with the non-local terms of that prediction
+        R *pred = (R *)c->pred;
+        if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, pred, c->dstats_pred, in);
+        else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, pred, c->dstats_pred, in);
+        nl = pred;
+    }
+    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats, nl);
+    else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats, nl);
     if (ev) cudaEventRecord(ev[1], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
@@ -277,6 +289,8 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     if ((opts->dalloc == nullptr) != (opts->dfree == nullptr)) return POND_EINVAL;
     if (opts->lanes_per_node != 0 && opts->lanes_per_node != 8 && opts->lanes_per_node != 16)
         return POND_EINVAL;
+    if (opts->nonlocal != POND_NONLOCAL_LAGGED && opts->nonlocal != POND_NONLOCAL_CURRENT)
+        return POND_EINVAL;
     if (opts->tile_x != 0 && opts->tile_x != 1 && opts->tile_x != 2 && opts->tile_x != 4 &&
         opts->tile_x != 8 && opts->tile_x != 16)
         return POND_EINVAL;
@@ -336,7 +350,13 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
     c->part = (double *)dev_alloc(c, (8 * (size_t)c->red_blocks + 8) * sizeof(double));
     c->dstats = (DevStats *)dev_alloc(c, sizeof(DevStats));
-    if (!c->state[0] || !c->state[1] || !c->stage || !c->part || !c->dstats) {
+    c->nonlocal = opts->nonlocal;
+    if (c->nonlocal) {
+        c->pred = dev_alloc(c, sb);
+        c->dstats_pred = (DevStats *)dev_alloc(c, sizeof(DevStats));
+    }
+    if (!c->state[0] || !c->state[1] || !c->stage || !c->part || !c->dstats ||
+        (c->nonlocal && (!c->pred || !c->dstats_pred))) {
         pond_destroy(c);
         return POND_ENOMEM;
     }
@@ -360,6 +380,8 @@ void pond_destroy(pond_ctx *c)
     dev_free(c, c->stage);
     dev_free(c, c->part);
     dev_free(c, c->dstats);
+    dev_free(c, c->pred);
+    dev_free(c, c->dstats_pred);
     delete c;
 }
 
@@ -706,6 +728,7 @@ pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
     b->err.clear();
     if (c->batch) return bfail(b, POND_EINVAL, "context already belongs to a batch");
     if (!c->initialised) return bfail(b, POND_EINVAL, "context state not initialised");
+    if (c->nonlocal) return bfail(b, POND_EINVAL, "two-pass (current-time) contexts are stepped alone");
     if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
     // the context's queued work (its initialisation) completes before the batch uses it

@@ -443,7 +443,8 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const float *bhi,
 // One time step of one tile (block) of a simulation: the body of both step kernels.
 template <typename R, int LPN>
 __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restrict__ in,
-                                          R *__restrict__ out, DevStats *stats, int tile_idx)
+                                          R *__restrict__ out, DevStats *stats, int tile_idx,
+                                          const R *nlsrc)
 {
     static_assert(LPN == 8 || LPN == 16, "8 or 16 lanes per node");
     constexpr int PPL = 16 / LPN;   // stencil positions per lane and direction
@@ -490,10 +491,19 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         // vdW pressure and p/rho of the stored rho, T (for the non-local terms) into the
         // slot words past the staged values
         for (int k = threadIdx.x; k < WT * HT; k += blockDim.x) {
-            const int cv = (int)(((float)k + 0.5f) * iwt);
-            R *sl = tile + (cv * PT + (k - cv * WT)) * TS;
+            const int cv = (int)(((float)k + 0.5f) * iwt), cu = k - cv * WT;
+            R *sl = tile + (cv * PT + cu) * TS;
             sl[P_SQ] = sqrt_(sl[P_TH]);
-            const R r = sl[P_RHO], t = sl[P_T];
+            R r = sl[P_RHO], t = sl[P_T];
+            if (nlsrc != in) {
+                // current-time non-local terms: rho, T of the first pass's prediction
+                const size_t g = ((size_t)bc_wrap(Y0 - HALO + cv, p.ny, p.bcy) * p.nx +
+                                  bc_wrap(X0 - HALO + cu, p.nx, p.bcx)) * SL;
+                r = nlsrc[g + P_RHO];
+                t = nlsrc[g + P_T];
+                sl[P_RHO] = r;
+                sl[P_T] = t;
+            }
             const R pr = eos_pressure<R>(p.eos_kind, q.a, q.b, q.R, r, t);
             sl[S_PR] = pr;
             sl[S_PRR] = pr / r;
@@ -946,9 +956,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 // One time step of one simulation: one block per tile.
 template <typename R, int LPN>
 __global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(R, LPN)) k_pond_step(DevParams p, const R *__restrict__ in,
-                                                             R *__restrict__ out, DevStats *stats)
+                                                             R *__restrict__ out, DevStats *stats,
+                                                             const R *nlsrc)
 {
-    step_tile<R, LPN>(p, in, out, stats, blockIdx.x);
+    step_tile<R, LPN>(p, in, out, stats, blockIdx.x, nlsrc);
 }
 
 // A simulation of a batch as one launch sees it: parameters, the buffers this step reads
@@ -979,7 +990,7 @@ __global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(R, LPN)) k_pond_
         s_stats = descs[w.x].stats;
     }
     __syncthreads();
-    step_tile<R, LPN>(sp, s_in, s_out, s_stats, w.y);
+    step_tile<R, LPN>(sp, s_in, s_out, s_stats, w.y, s_in);
 }
 
 }  // namespace pond

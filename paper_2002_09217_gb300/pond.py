@@ -44,7 +44,8 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("dt", C.c_double), ("k_cond", C.c_double), ("p_floor", C.c_double),
                 ("stream", C.c_void_p), ("dalloc", _ALLOC), ("dfree", _FREE),
-                ("alloc_ctx", C.c_void_p), ("lanes_per_node", C.c_int32), ("tile_x", C.c_int32)]
+                ("alloc_ctx", C.c_void_p), ("lanes_per_node", C.c_int32), ("tile_x", C.c_int32),
+                ("nonlocal_", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -145,7 +146,7 @@ class Simulation:
                  max_iter: int = 20, k_cond: float = -1.0, p_floor: float = 1e-3 / 6.0,
                  stream=None, torch_alloc: bool = True, ideal: bool = False,
                  lanes_per_node: int = 0, tile_x: int = 0, eos: str = "vdw",
-                 isothermal: bool = False, T_iso: float = 0.0):
+                 isothermal: bool = False, T_iso: float = 0.0, nonlocal_: str = "lagged"):
         torch = _torch()
         self._lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -185,12 +186,12 @@ class Simulation:
         eos_c = Eos(kind, a, b, R, delta, 1 if isothermal else 0, float(T_iso))
         opts = Opts(POND_MIXED if precision == "mixed" else POND_FP64, max_iter, tol, dt, k_cond,
                     p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None,
-                    lanes_per_node, tile_x)
+                    lanes_per_node, tile_x, {"lagged": 0, "current": 1}[nonlocal_])
         self.params = dict(nx=nx, ny=ny, bc_x=bc_x, bc_y=bc_y, a=a, b=b, R=R, delta=delta,
                            kappa=kappa, tau=tau, precision=precision, dt=dt, tol=tol,
                            max_iter=max_iter, k_cond=k_cond, p_floor=p_floor,
                            lanes_per_node=lanes_per_node, tile_x=tile_x, eos=eos,
-                           isothermal=isothermal, T_iso=T_iso)
+                           isothermal=isothermal, T_iso=T_iso, nonlocal_=nonlocal_)
         ctx = C.c_void_p()
         with torch.cuda.device(self._device):
             st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos_c), kappa, tau,

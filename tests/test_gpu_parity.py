@@ -219,3 +219,31 @@ def test_tile_shapes_match_oracle(pond, tile_x):
     got, _ = gpu_run(pond, fast, "fp64", tile_x=tile_x)
     err = rel_linf(got, ref)
     assert max(err.values()) <= TOL["fp64"], err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_current_time_variant_matches_oracle(pond, precision):
+    """The two-pass step with current-time non-local terms against the oracle's two-pass
+    step (a moving slab and a droplet, where the terms change within a step)."""
+    slab = inputs.slab(nx=40, ny=6, Tr=0.9, steps=20)
+    slab.ux = np.full_like(slab.rho, 0.05)
+    for w in (slab, inputs.droplet(n=24, ny=20, Tr=0.9, radius=5.0, steps=12)):
+        P, st, _ = oracle_run(w, nonlocal_="current")
+        ref = oracle.moments(P, st)
+        got, gstats = gpu_run(pond, w, precision, nonlocal_="current")
+        err = rel_linf(got, ref)
+        assert max(err.values()) <= TOL[precision], (w.name, err)
+        if precision == "fp64":
+            lag, _ = gpu_run(pond, w, precision)
+            assert max(rel_linf(lag, ref).values()) > 10 * TOL["fp64"]   # the variant matters
+
+
+def test_current_time_context_is_stepped_alone(pond):
+    w = inputs.slab(nx=16, ny=4, steps=2)
+    with pond.from_workload(w, precision="mixed", nonlocal_="current") as sim:
+        sim.init_fields(*w.fields())
+        batch = pond.Batch()
+        with pytest.raises(pond.PondError):
+            batch.add(sim)
+        batch.close()
+        sim.step(2)

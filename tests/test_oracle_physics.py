@@ -19,6 +19,7 @@ independently of the scheme.
   oracle's isothermal flat interface on those densities;
 - isothermal runs carry sound at the isothermal speed sqrt((dp/drho)_T) (SM figure).
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -371,3 +372,43 @@ def test_isothermal_pulse_travels_at_the_isothermal_speed():
     c = (cents[1] - cents[0]) / ((n2 - n2 // 3) * w.dt)
     assert c == pytest.approx(cT, rel=1e-3)
     assert c < 0.7 * thermo.sound_speed(rho0, T0, w.delta)
+
+
+# ------------------------------------------------- current-time non-local terms
+def test_current_time_nonlocal_terms_differ_from_lagged_at_second_order():
+    """One step of the two-pass (current-time) variant differs from the lagged step by
+    dt x (the force's change over dt) ~ dt^2 in the velocity, so halving dt divides the
+    difference by ~4; the two coincide where the non-local terms vanish."""
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.slab(nx=64, ny=1, Tr=0.9, amp=0.0, steps=1)
+    base = oracle.Params(nx=w.nx, ny=1, tau=1.0, kappa=0.02, p_floor=w.p_floor)
+    # a relaxed interface moving slowly: lagged and current terms differ by its motion
+    st0 = oracle.init_state(dataclasses.replace(base, dt=0.25), w.rho, 0 * w.rho + 0.05, 0 * w.rho, w.T)
+    st0 = oracle.step(dataclasses.replace(base, dt=0.25), st0, 40)
+    gaps = []
+    for dt in (0.2, 0.1):
+        lag = oracle.moments(dataclasses.replace(base, dt=dt), oracle.step(dataclasses.replace(base, dt=dt), st0, 1))
+        cur = oracle.moments(dataclasses.replace(base, dt=dt, nonlocal_="current"),
+                             oracle.step(dataclasses.replace(base, dt=dt, nonlocal_="current"), st0, 1))
+        gaps.append(np.abs(cur["ux"] - lag["ux"]).max())
+    assert gaps[0] > 0.0
+    assert 3.0 < gaps[0] / gaps[1] < 5.5, gaps
+    # no interface, no heat flux: nothing to lag
+    ideal = oracle.Params(nx=16, ny=1, a=0.0, b=0.0, delta=0.4, tau=1.0, dt=0.5, p_floor=1e-6)
+    x = np.arange(16)[None, :]
+    st = oracle.init_state(ideal, 1.0 + 0.1 * np.sin(2 * np.pi * x / 16), 0 * x + 0.0, 0 * x + 0.0,
+                           np.full((1, 16), 0.1))
+    a1 = oracle.step(ideal, st, 3)
+    a2 = oracle.step(dataclasses.replace(ideal, nonlocal_="current"), st, 3)
+    np.testing.assert_array_equal(a1, a2)
+
+
+def test_current_time_variant_keeps_coexistence():
+    from paper_2002_09217_gb300 import experiments, inputs
+    w = inputs.coexistence_slab(0.9, nx=128, steps=3000)
+    P = oracle.Params(nx=w.nx, ny=1, dt=w.dt, tau=w.tau, kappa=w.kappa, p_floor=w.p_floor,
+                      nonlocal_="current")
+    st = oracle.step(P, oracle.init_state(P, *w.fields()), w.steps)
+    v, l = experiments.bulk_densities(oracle.moments(P, st)["rho"])
+    rv, rl = thermo.maxwell(0.9)
+    assert v == pytest.approx(rv, rel=0.01) and l == pytest.approx(rl, rel=0.01)
