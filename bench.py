@@ -140,8 +140,9 @@ FLOPS_COLLIDE = 1300
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the bench workload; they hold only for the kernel source they were
 # taken on (sha256 over the two kernel headers), any other source reports null.
-NCU_TRAFFIC = {"kernel_sha256": "271249139da9695b6538223b6555fba98c863a30e7e5a978d2824349e0b554f1",
-               "bytes": {"shocktube2048x4/mixed": 1119232.0}}
+NCU_TRAFFIC = {"kernel_sha256": "fbbd25901a2833e0db9ed83b636be704b16489f54f0c292b088e7c13b5322b7f",
+               "bytes": {"shocktube2048x4/mixed": 1117184.0,
+                         "dropletshock2048x1024/mixed": 636516864.0}}
 
 
 def kernel_sha256() -> str:
@@ -360,6 +361,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 form and the other workloads / experiments")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -435,7 +438,7 @@ def main():
     }
     line["e2e"] = end_to_end(w, pond, torch, stream, args.precision, shape, n_seg=100, reps=5)
 
-    if args.precision == "mixed":
+    if args.precision == "mixed" and not args.no_extras:
         # the plain FP64 form of the same workload (fewer steps: the FP64 pipes are 1/64)
         shape64 = shape_for("fp64")
         ms64, st64, kms64 = run_form(w, pond, torch, stream, flush, "fp64", 30, 3, shape64, 1)
@@ -445,7 +448,7 @@ def main():
                         "frame_search_streams_per_node": its64,
                         "roofline": roofline(w, "fp64", its64, kms64, pk)}
 
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         line["other_configs"] = other_configs(pond, torch, stream)
 
     if not args.no_serving:
