@@ -319,6 +319,14 @@ def other_configs(pond, torch, stream) -> dict:
     el = time.perf_counter() - t0
     out["%s/mixed" % w.name] = {"c_measured": res["c"], "steps": res["steps"], "wall_s": el,
                                 "mlups_incl_sampling": w.nodes * res["steps"] / el / 1e6}
+    # the anomalous shock tube (delta = 0.0125): steepness of the left (rarefaction shock)
+    # and right fronts at t*/2 and t*
+    w = inputs.nonclassical_tube("fig4", nx=1024)
+    t0 = time.perf_counter()
+    res = experiments.wave_steepness(w, "mixed", stream=stream)
+    el = time.perf_counter() - t0
+    out["%s/mixed" % w.name] = {"left_peak_half": res["half"]["left_peak"], "left_peak_end": res["end"]["left_peak"],
+                                "steps": w.steps, "wall_s": el, "mlups_incl_reads": w.nodes * w.steps / el / 1e6}
     # the coexistence experiment (flat slab at 0.9 T_cr, delta = 1/3): saturated densities
     # from the relaxed field (Maxwell: 1.490096 / 5.800446)
     w = inputs.coexistence_slab(0.9, nx=256, steps=4000)

@@ -193,3 +193,20 @@ def dieterici_maxwell(Tr: float, a=A_DIE, b=B_DIE, R=R_GAS):
     ps = optimize.brentq(area, p_min + 1e-9 * span, p_max - 1e-9 * span, xtol=1e-16, rtol=1e-15)
     rv, rl = roots(ps)
     return float(rv), float(rl)
+
+
+# ---------------------------------------------------------------------------------------
+# Non-classical gas dynamics (main text, Fig. 4; SM "Shock tube").
+def temperature(rho, p, a=A_VDW, b=B_VDW, R=R_GAS):
+    """T of the van der Waals fluid at (rho, p): (p + a rho^2)(1 - b rho)/(rho R)."""
+    return (p + a * rho * rho) * (1.0 - b * rho) / (rho * R)
+
+
+def fundamental_derivative(p, rho, delta, a=A_VDW, b=B_VDW):
+    """Gamma = (v^3 / (2 c^2)) (d^2 p / d v^2)_s of the vdW fluid with C_v = R/delta, in
+    the closed form of the SM (v = 1/rho; any consistent units)."""
+    v = 1.0 / rho
+    q = p + a / v ** 2
+    num = (delta + 1.0) * (delta + 2.0) * q / (v - b) ** 2 - 6.0 * a / v ** 4
+    den = 2.0 * (delta + 1.0) * q / (v * (v - b)) - 4.0 * a / v ** 4
+    return num / den

@@ -3,7 +3,7 @@ that the synthetic workloads are built from (coexistence densities by Maxwell's
 rule, Rankine-Hugoniot post-shock states, the per-temperature time step, the time step of
 uniform saturated states and of the critical state for the sound-pulse experiments, the
 time steps of the coexistence-curve cases of Fig. 2, and the isothermal Dieterici
-coexistence of the SM).
+coexistence of the SM, the non-classical shock-tube states).
 
 Run: ``python -m oracle.write_workloads``.  It calls only ``oracle.thermo``; the
 JSON file is data that the input generators read, so no product code executes
@@ -75,6 +75,20 @@ def main() -> None:
                               "dt": dt_rule_isothermal_dieterici(rl, Tr * dTc)}
     dieterici = {"a": thermo.A_DIE, "b": thermo.B_DIE, "critical": {"rho": drc, "T": dTc, "p": dpc},
                  "coexistence": dcoex}
+    # shock tubes of non-classical gas dynamics: the anomalous case of the main text's
+    # Fig. 4 and the SM's cases I, II, states given in reduced units (p/p_cr, rho/rho_cr);
+    # snapshot times t* = (t / L) sqrt(p_cr / rho_cr)
+    nonclassical = {"U_ch": math.sqrt(pc / rc), "cases": {}}
+    for name, (pl, rl_), (pr_, rr_), dlt, tstar in (
+            ("fig4", (1.09, 0.879), (0.885, 0.562), 0.0125, 0.45),
+            ("I", (1.6077, 1.01), (0.8957, 0.594), 0.329, 0.2),
+            ("II", (3.00, 1.818), (0.575, 0.275), 0.0125, 0.15)):
+        sides = {}
+        for side, (pp, rr) in (("left", (pl, rl_)), ("right", (pr_, rr_))):
+            rho = rr * rc
+            sides[side] = {"rho": rho, "T": thermo.temperature(rho, pp * pc)}
+        dt = min(dt_rule(sides[k]["rho"], sides[k]["T"], dlt) for k in sides)
+        nonclassical["cases"][name] = dict(sides, delta=dlt, t_star=tstar, dt=dt)
     # the coexistence curve of the main text's Fig. 2: delta = 2/3 (time step by the rule at
     # the liquid density for that delta) and delta = 1/3 advected at U = 5 U_ch with
     # U_ch = sqrt(p_cr / rho_cr) (time step also capped at 0.5 / (1 + U))
@@ -94,6 +108,7 @@ def main() -> None:
         "supercritical_1.10": {"dt": dt_rule(sup_rho, 1.1 * Tc)},
         "figure2": fig2,
         "dieterici": dieterici,
+        "nonclassical": nonclassical,
         # sound-pulse experiments: the time step of a uniform saturated vapour or liquid
         # (each by the rule at its own state), and of the critical state
         "sound": dict({"%.2f" % (k / 100.0): {

@@ -1,5 +1,10 @@
 """Experiments of the paper run through the GPU path.
 
+Non-classical waves (main text, Fig. 4; SM "Shock tube"): a shock keeps its steepness as
+it travels, an expansion fan spreads, so the peak density gradient of each half of the
+tube at t*/2 and at t* tells a rarefaction shock (steepness kept) from a rarefaction fan
+(steepness halved).
+
 Coexistence (main text, Fig. 2): a liquid slab in its vapour (``inputs.coexistence_slab``)
 relaxes to the saturated densities; they are read as the means of the lowest and highest
 quarter of the density field, which is independent of where the slab is (it moves in the
@@ -92,3 +97,26 @@ def coexistence(w, precision: str = "mixed", settle: float = 0.75, samples: int 
     return {"rho_v": float(np.mean(rv)), "rho_l": float(np.mean(rl)),
             "steps": n_settle + samples * per, "nonfinite": int(stats["nonfinite"]),
             "clamped": int(stats["clamped"])}
+
+
+def wave_steepness(w, precision: str = "mixed", stream=None, **kw) -> dict:
+    """Steps the tube workload `w` to half its steps and to all of them; at both times
+    returns, for the left and the right half of the tube, the peak |rho(x+1) - rho(x)| and
+    where it is, plus the density on both sides of the left half's front (10 nodes
+    away)."""
+    out = {}
+    with pond.from_workload(w, precision=precision, stream=stream, **kw) as sim:
+        sim.init_fields(*w.fields())
+        done = 0
+        for tag, n in (("half", w.steps // 2), ("end", w.steps)):
+            sim.step(n - done)
+            done = n
+            r = sim.moments()["rho"].mean(axis=0)
+            g = np.abs(np.diff(r))
+            h = w.nx // 2
+            il, ir = int(np.argmax(g[:h])), h + int(np.argmax(g[h:]))
+            out[tag] = {"left_peak": float(g[il]), "left_at": il, "right_peak": float(g[ir]),
+                        "right_at": ir, "left_outer": float(r[max(0, il - 10)]),
+                        "left_inner": float(r[min(w.nx - 1, il + 11)])}
+        out["nonfinite"] = int(sim.stats()["nonfinite"])
+    return out

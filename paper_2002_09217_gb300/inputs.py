@@ -174,6 +174,25 @@ def dieterici_slab(Tr=0.9, nx=256, ny=1, width=4.0, steps=None, kappa=0.02, tau=
                     p_floor=0.05 * d["critical"]["p"], eos="dieterici", isothermal=True)
 
 
+def nonclassical_tube(case="fig4", nx=1024, ny=1, width=2.0, tau=1.0):
+    """Shock tubes of non-classical gas dynamics in the van der Waals fluid: the anomalous
+    case of the main text's Fig. 4 (delta = 0.0125, both states with Gamma < 0) and the
+    SM's cases "I" (delta = 0.329, classical) and "II" (delta = 0.0125, Gamma changes sign
+    during the flow).  Left / right states at rest from the workload table, a tanh step of
+    `width` nodes at the middle, zero-gradient ends in x, periodic in y, kappa = 0; steps
+    up to the case's snapshot time t* = (t / nx) sqrt(p_cr / rho_cr)."""
+    tab = table()["nonclassical"]
+    c = tab["cases"][case]
+    x = np.arange(nx) + 0.5
+    sw = 0.5 * (1.0 - np.tanh((x - nx / 2) / width))
+    rho = np.tile(c["right"]["rho"] + (c["left"]["rho"] - c["right"]["rho"]) * sw, (ny, 1))
+    T = np.tile(c["right"]["T"] + (c["left"]["T"] - c["right"]["T"]) * sw, (ny, 1))
+    z = np.zeros((ny, nx))
+    steps = int(round(c["t_star"] * nx / tab["U_ch"] / c["dt"]))
+    return Workload("nonclassical_%s_%dx%d" % (case, nx, ny), nx, ny, 1, 0, 1.0, 0.0, tau, c["dt"],
+                    steps, rho, z, z.copy(), T, delta=c["delta"])
+
+
 def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, steps=40000, tau=1.0,
                 isothermal=False):
     """Uniform saturated vapour or liquid at T = Tr T_cr (phase "vapour" / "liquid"), or

@@ -7,6 +7,8 @@ one-step checks at sampled nodes (the oracle steps those nodes from the GPU's
 own previous state).  Bars: FP64 <= 1e-11, mixed FP32/FP64 <= 1e-5 relative
 L-infinity per field (rho, uhat_x, uhat_y, T, p).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -48,6 +50,7 @@ def small_cases():
     yield "isothermal_sound_80x1", inputs.sound_pulse(0.9, "vapour", nx=80, width=4.0, steps=50,
                                                       isothermal=True)
     yield "dieterici_iso_48x3", inputs.dieterici_slab(0.8, nx=48, ny=3, steps=40)
+    yield "anomalous_tube_64x2", dataclasses.replace(inputs.nonclassical_tube("fig4", nx=64, ny=2), steps=40)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

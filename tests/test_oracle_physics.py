@@ -17,10 +17,15 @@ independently of the scheme.
 - the Dieterici EoS (SM "Coexistence curve"): its critical point, the SM's reduced form,
   Maxwell densities that obey corresponding states and equal chemical potentials, and the
   oracle's isothermal flat interface on those densities;
-- isothermal runs carry sound at the isothermal speed sqrt((dp/drho)_T) (SM figure).
+- isothermal runs carry sound at the isothermal speed sqrt((dp/drho)_T) (SM figure);
+- non-classical gas dynamics (main text, Fig. 4; SM "Shock tube"): the fundamental
+  derivative against the SM's printed table and against finite differences along an
+  isentrope; the anomalous tube's rarefaction keeps its steepness (a rarefaction shock)
+  while the classical case's rarefaction spreads.
 """
 import dataclasses
 import math
+import os
 
 import numpy as np
 import pytest
@@ -412,3 +417,74 @@ def test_current_time_variant_keeps_coexistence():
     v, l = experiments.bulk_densities(oracle.moments(P, st)["rho"])
     rv, rl = thermo.maxwell(0.9)
     assert v == pytest.approx(rv, rel=0.01) and l == pytest.approx(rl, rel=0.01)
+
+
+# ------------------------------------------------------------ non-classical dynamics
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "shock_tube_gamma.txt")
+
+
+def test_fundamental_derivative_matches_the_printed_table():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 4
+    rc, Tc, pc = thermo.critical()
+    for case, side, p, r, d, want in rows:
+        p, r, d, want = float(p), float(r), float(d), float(want)
+        # reduced van der Waals constants (a = 3, b = 1/3) and the dimensional ones agree
+        g_red = thermo.fundamental_derivative(p, r, d, a=3.0, b=1.0 / 3.0)
+        g_dim = thermo.fundamental_derivative(p * pc, r * rc, d)
+        assert g_red == pytest.approx(want, abs=6e-4), (case, side)
+        assert g_dim == pytest.approx(g_red, rel=1e-12)
+
+
+@pytest.mark.parametrize("p,r,d", [(1.09, 0.879, 0.0125), (0.885, 0.562, 0.0125), (1.6077, 1.01, 0.329)])
+def test_fundamental_derivative_from_an_isentrope(p, r, d):
+    """Gamma = (v^3 / 2c^2) p''(v) along the isentrope T (v - b)^delta = const of the vdW
+    fluid with constant C_v, by finite differences: the same number as the closed form;
+    the anomalous states of Fig. 4 have Gamma < 0."""
+    rc, Tc, pc = thermo.critical()
+    a, b, R = thermo.A_VDW, thermo.B_VDW, thermo.R_GAS
+    v0 = 1.0 / (r * rc)
+    K = thermo.temperature(r * rc, p * pc) * (v0 - b) ** d
+    ps = lambda v: R * K * (v - b) ** (-d) / (v - b) - a / (v * v)
+    h = 1e-4 * v0
+    d1 = (ps(v0 + h) - ps(v0 - h)) / (2 * h)
+    d2 = (ps(v0 + h) - 2 * ps(v0) + ps(v0 - h)) / (h * h)
+    gamma = v0 ** 3 * d2 / (2.0 * (-v0 * v0 * d1))
+    assert gamma == pytest.approx(thermo.fundamental_derivative(p * pc, r * rc, d), rel=1e-5, abs=1e-6)
+    if d < 0.05 and p < 1.1:
+        assert gamma < 0.0
+
+
+def _oracle_steepness(case, nx=400):
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.nonclassical_tube(case, nx=nx)
+    P = oracle.Params(nx=w.nx, ny=1, bc_x=1, delta=w.delta, tau=w.tau, dt=w.dt, kappa=0.0,
+                      p_floor=w.p_floor)
+    st = oracle.init_state(P, *w.fields())
+    out, done = [], 0
+    for n in (w.steps // 2, w.steps):
+        st = oracle.step(P, st, n - done)
+        done = n
+        r = oracle.moments(P, st)["rho"][0]
+        g = np.abs(np.diff(r))
+        il = int(np.argmax(g[: nx // 2]))
+        out.append((g[il], il, g[nx // 2:].max(), r[max(0, il - 10)], r[il + 11]))
+    return out
+
+
+def test_anomalous_tube_has_a_rarefaction_shock():
+    """Fig. 4 (delta = 0.0125, Gamma < 0 on both sides): the left-moving wave expands the
+    fluid yet stays as steep from t*/2 to t* (a shock, not a fan)."""
+    (g1, x1, _, _, _), (g2, x2, _, outer, inner) = _oracle_steepness("fig4")
+    assert x2 < x1                       # it moves left
+    assert outer > inner                 # the fluid behind it is less dense: an expansion
+    assert g2 > 0.75 * g1, (g1, g2)
+
+
+def test_classical_tube_has_a_rarefaction_fan():
+    """Case I (delta = 0.329 > delta_BZT): the rarefaction spreads (its peak gradient
+    about halves from t*/2 to t*) while the compression shock keeps its steepness."""
+    (g1, x1, s1, _, _), (g2, x2, s2, _, _) = _oracle_steepness("I")
+    assert x2 < x1
+    assert g2 < 0.65 * g1, (g1, g2)
+    assert s2 > 0.85 * s1, (s1, s2)
