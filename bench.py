@@ -168,6 +168,7 @@ def oracle_mlups(w, steps: int) -> dict:
     P = oracle.Params(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R,
                       delta=w.delta, kappa=w.kappa, tau=w.tau, dt=w.dt, k_cond=w.k_cond,
                       p_floor=w.p_floor, tol=1e-12, max_iter=20, eos=w.eos, isothermal=w.isothermal,
+                      eos_params=tuple(w.eos_params),
                       T_iso=float(w.T.flat[0]) if w.isothermal else 0.0)
     st = oracle.init_state(P, *w.fields())
     st = oracle.step(P, st, 1)          # warm-up (page-in, thread pool)

@@ -62,7 +62,7 @@ typedef enum {
 
 enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
 enum { POND_D2Q9 = 0 };                            /* lattice                         */
-enum { POND_VDW = 0, POND_IDEAL = 1, POND_DIETERICI = 2 };   /* EoS kind (see pond_eos) */
+enum { POND_VDW = 0, POND_IDEAL = 1, POND_DIETERICI = 2, POND_SIMPLIFIED = 3 };   /* see pond_eos */
 enum { POND_FP64 = 0, POND_MIXED = 1 };            /* arithmetic / storage form       */
 enum { POND_NONLOCAL_LAGGED = 0, POND_NONLOCAL_CURRENT = 1 };   /* see pond_opts.nonlocal */
 
@@ -74,15 +74,20 @@ typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9          
 /* Equation of state.  POND_VDW: van der Waals p = rho R T/(1 - b rho) - a rho^2 with
  * e = (R/delta) T - a rho (main text; SM "Thermodynamics"); 0 < delta <= 2/3.
  * POND_IDEAL: the same with a = b = 0 forced.  POND_DIETERICI: p = rho R T/(1 - b rho)
- * exp(-a rho/(R T)) (SM "Coexistence curve"); it has no closed caloric equation here, so
- * it requires isothermal = 1.  isothermal = 1 holds T at T_iso > 0 everywhere (the SM's
- * isothermal runs): the gauge temperature comes from p(rho, T_iso) and the energy
- * population then plays no part in the flow; the initial T field should equal T_iso. */
+ * exp(-a rho/(R T)) (SM "Coexistence curve").  POND_SIMPLIFIED: the near-critical
+ * double well of the SM's speed-of-sound study, p = p0 + rho E0' - E0 with
+ * E0 = beta (rho - rho_l)^2 (rho - rho_v)^2 (fields beta, rho_l, rho_v, p0; p0 > 0 is a
+ * background pressure the printed form lacks, which keeps theta = p/(rho T_L) positive).
+ * Neither has a closed caloric equation here, so both require isothermal = 1.
+ * isothermal = 1 holds T at T_iso > 0 everywhere (the SM's isothermal runs): the gauge
+ * temperature comes from p(rho, T_iso) and the energy population then plays no part in
+ * the flow; the initial T field should equal T_iso. */
 typedef struct {
     int32_t kind;
     double a, b, R, delta;
     int32_t isothermal;
     double T_iso;
+    double beta, rho_l, rho_v, p0;
 } pond_eos;
 
 /* Options.  precision: POND_FP64 (all FP64) or POND_MIXED (FP32 populations and

@@ -42,7 +42,8 @@ class _CParams(C.Structure):
                 ("kappa", C.c_double), ("tau", C.c_double), ("k_cond", C.c_double),
                 ("p_floor", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("eos_kind", C.c_int32), ("dt", C.c_double), ("isothermal", C.c_int32),
-                ("pad", C.c_int32), ("T_iso", C.c_double)]
+                ("pad", C.c_int32), ("T_iso", C.c_double), ("sp_beta", C.c_double),
+                ("sp_rho_l", C.c_double), ("sp_rho_v", C.c_double), ("sp_p0", C.c_double)]
 
 
 @dataclasses.dataclass
@@ -62,21 +63,23 @@ class Params:
     tol: float = 1e-12
     max_iter: int = 20
     dt: float = 1.0
-    eos: str = "vdw"          # "vdw" or "dieterici" (the latter with isothermal only)
+    eos: str = "vdw"          # "vdw", or "dieterici" / "simplified" (isothermal only)
     isothermal: bool = False  # hold T at T_iso
     T_iso: float = 0.0
+    eos_params: tuple = ()    # (beta, rho_l, rho_v, p0) of the "simplified" double well
     nonlocal_: str = "lagged"  # non-local terms from t - dt ("lagged") or from a first
                                # pass's prediction of t ("current", two passes per step)
 
     def c(self) -> _CParams:
-        if self.eos not in ("vdw", "dieterici"):
-            raise ValueError("eos must be vdw or dieterici")
-        if self.eos == "dieterici" and not self.isothermal:
-            raise ValueError("the Dieterici EoS is used isothermally (no caloric closure)")
+        if self.eos not in ("vdw", "dieterici", "simplified"):
+            raise ValueError("eos must be vdw, dieterici or simplified")
+        if self.eos != "vdw" and not self.isothermal:
+            raise ValueError("the %s EoS is used isothermally (no caloric closure)" % self.eos)
+        sp = tuple(self.eos_params) if self.eos == "simplified" else (0.0, 0.0, 0.0, 0.0)
         return _CParams(self.nx, self.ny, self.bc_x, self.bc_y, self.a, self.b, self.R,
                         self.delta, self.kappa, self.tau, self.k_cond, self.p_floor, self.tol,
-                        self.max_iter, 1 if self.eos == "dieterici" else 0, self.dt,
-                        1 if self.isothermal else 0, 0, self.T_iso)
+                        self.max_iter, {"vdw": 0, "dieterici": 1, "simplified": 2}[self.eos], self.dt,
+                        1 if self.isothermal else 0, 0, self.T_iso, *sp)
 
 
 def _load():

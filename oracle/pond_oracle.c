@@ -76,11 +76,14 @@ typedef struct {
     double tol;              /* frame-search tolerance */
     int32_t max_iter;        /* maximum number of streams per node and step */
     int32_t eos_kind;        /* 0: van der Waals p = rho R T/(1 - b rho) - a rho^2;
-                                1: Dieterici p = rho R T/(1 - b rho) exp(-a rho/(R T)) (SM) */
+                                1: Dieterici p = rho R T/(1 - b rho) exp(-a rho/(R T)) (SM);
+                                2: near-critical double well (SM "Speed of sound"):
+                                   p = p0 + rho E0' - E0, E0 = beta (rho - rho_l)^2 (rho - rho_v)^2 */
     double dt;               /* time step delta t (lattice spacing Delta x = 1) */
     int32_t isothermal;      /* 1: T is held at T_iso (the SM's isothermal runs) */
     int32_t pad;
     double T_iso;
+    double sp_beta, sp_rho_l, sp_rho_v, sp_p0;   /* constants of eos_kind 2 */
 } orc_params;
 
 /* ------------------------------ EoS ------------------------------------- */
@@ -88,6 +91,12 @@ static double eos_p(const orc_params *P, double rho, double T)
 {
     if (P->eos_kind == 1)   /* Dieterici (SM "Coexistence curve") */
         return rho * P->R * T / (1.0 - P->b * rho) * exp(-P->a * rho / (P->R * T));
+    if (P->eos_kind == 2) { /* double well: E0 = beta (rho - rho_l)^2 (rho - rho_v)^2 */
+        double dl = rho - P->sp_rho_l, dv = rho - P->sp_rho_v;
+        double E0 = P->sp_beta * dl * dl * dv * dv;
+        double dE0 = 2.0 * P->sp_beta * dl * dv * (dl + dv);
+        return P->sp_p0 + rho * dE0 - E0;
+    }
     return rho * P->R * T / (1.0 - P->b * rho) - P->a * rho * rho;
 }
 static double eos_e(const orc_params *P, double rho, double T)

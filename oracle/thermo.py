@@ -210,3 +210,23 @@ def fundamental_derivative(p, rho, delta, a=A_VDW, b=B_VDW):
     num = (delta + 1.0) * (delta + 2.0) * q / (v - b) ** 2 - 6.0 * a / v ** 4
     den = 2.0 * (delta + 1.0) * q / (v * (v - b)) - 4.0 * a / v ** 4
     return num / den
+
+
+# ---------------------------------------------------------------------------------------
+# Simplified near-critical EoS (SM "Speed of sound"): free energy per volume
+# E0 = beta (rho - rho_l)^2 (rho - rho_v)^2, p = p0 + rho dE0/drho - E0.  The printed form
+# has no background pressure and gives p = 0 at both saturated densities, which leaves no
+# gauge temperature theta = p/(rho T_L); a constant p0 changes neither the coexistence
+# (equal pressure p0 and equal chemical potential at rho_v, rho_l) nor dp/drho.
+SIMP = {"beta": 1e-3, "rho_l": 5.0, "rho_v": 0.5, "p0": 0.1}   # rho_l / rho_v = 10 as in the SM
+
+
+def simplified_pressure(rho, beta=SIMP["beta"], rho_l=SIMP["rho_l"], rho_v=SIMP["rho_v"], p0=SIMP["p0"]):
+    dl, dv = rho - rho_l, rho - rho_v
+    return p0 + rho * 2.0 * beta * dl * dv * (dl + dv) - beta * dl * dl * dv * dv
+
+
+def simplified_sound_speed(rho, beta=SIMP["beta"], rho_l=SIMP["rho_l"], rho_v=SIMP["rho_v"]):
+    """sqrt(dp/drho) = sqrt(rho E0''); at rho_l, rho_v it is sqrt(2 beta rho) (rho_l - rho_v)."""
+    dl, dv = rho - rho_l, rho - rho_v
+    return math.sqrt(rho * 2.0 * beta * (dl * dl + 4.0 * dl * dv + dv * dv))

@@ -3,7 +3,8 @@ that the synthetic workloads are built from (coexistence densities by Maxwell's
 rule, Rankine-Hugoniot post-shock states, the per-temperature time step, the time step of
 uniform saturated states and of the critical state for the sound-pulse experiments, the
 time steps of the coexistence-curve cases of Fig. 2, and the isothermal Dieterici
-coexistence of the SM, the non-classical shock-tube states).
+coexistence of the SM, the non-classical shock-tube states, the simplified near-critical
+EoS).
 
 Run: ``python -m oracle.write_workloads``.  It calls only ``oracle.thermo``; the
 JSON file is data that the input generators read, so no product code executes
@@ -78,6 +79,14 @@ def main() -> None:
     # shock tubes of non-classical gas dynamics: the anomalous case of the main text's
     # Fig. 4 and the SM's cases I, II, states given in reduced units (p/p_cr, rho/rho_cr);
     # snapshot times t* = (t / L) sqrt(p_cr / rho_cr)
+    # the simplified near-critical EoS of the SM's speed-of-sound study (isothermal): its
+    # constants and the time step by the usual rule at each saturated density
+    sp = dict(thermo.SIMP)
+    dts = []
+    for rho in (sp["rho_l"], sp["rho_v"]):
+        theta = thermo.simplified_pressure(rho) / (rho * T_L)
+        dts.append(min(0.5, 0.45 * math.sqrt(theta) / thermo.simplified_sound_speed(rho) ** 2))
+    simplified = dict(sp, dt=min(dts))
     nonclassical = {"U_ch": math.sqrt(pc / rc), "cases": {}}
     for name, (pl, rl_), (pr_, rr_), dlt, tstar in (
             ("fig4", (1.09, 0.879), (0.885, 0.562), 0.0125, 0.45),
@@ -109,6 +118,7 @@ def main() -> None:
         "figure2": fig2,
         "dieterici": dieterici,
         "nonclassical": nonclassical,
+        "simplified": simplified,
         # sound-pulse experiments: the time step of a uniform saturated vapour or liquid
         # (each by the rule at its own state), and of the critical state
         "sound": dict({"%.2f" % (k / 100.0): {

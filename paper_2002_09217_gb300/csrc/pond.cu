@@ -274,7 +274,13 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
         (grid->bc_y != POND_PERIODIC && grid->bc_y != POND_ZEROGRAD))
         return POND_EINVAL;
     if (lattice->kind != POND_D2Q9) return POND_EINVAL;
-    if (eos->kind != POND_VDW && eos->kind != POND_IDEAL && eos->kind != POND_DIETERICI) return POND_EINVAL;
+    if (eos->kind != POND_VDW && eos->kind != POND_IDEAL && eos->kind != POND_DIETERICI &&
+        eos->kind != POND_SIMPLIFIED)
+        return POND_EINVAL;
+    if (eos->kind == POND_SIMPLIFIED &&
+        (!eos->isothermal || !(eos->beta > 0.0) || !(eos->rho_v > 0.0) || !(eos->rho_l > eos->rho_v) ||
+         !(eos->p0 > 0.0)))
+        return POND_EINVAL;
     if (eos->isothermal != 0 && eos->isothermal != 1) return POND_EINVAL;
     if (eos->isothermal && !(eos->T_iso > 0.0 && std::isfinite(eos->T_iso))) return POND_EINVAL;
     if (eos->kind == POND_DIETERICI && (!eos->isothermal || !(eos->a > 0.0) || !(eos->b > 0.0)))
@@ -338,7 +344,10 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     split(d.a, d.ff_a); split(d.b, d.ff_b); split(d.R, d.ff_R); split(d.pd.inv_cv, d.ff_icv);
     split(d.p_floor, d.ff_pfl);
     d.tol_f = (float)d.tol;
-    d.eos_kind = c->eos.kind == POND_DIETERICI ? 2 : 0;
+    d.eos_kind = c->eos.kind == POND_DIETERICI ? 2 : (c->eos.kind == POND_SIMPLIFIED ? 3 : 0);
+    d.sp[0] = c->eos.beta; d.sp[1] = c->eos.rho_l; d.sp[2] = c->eos.rho_v; d.sp[3] = c->eos.p0;
+    for (int k = 0; k < 4; ++k) d.spf[k] = (float)d.sp[k];
+    split(d.sp[3], d.ff_p0);
     d.isothermal = c->eos.isothermal;
     d.T_iso = c->eos.isothermal ? c->eos.T_iso : 0.0;
     split(d.T_iso, d.ff_Tiso);

@@ -59,19 +59,32 @@ struct DevParams {
     int eos_kind, isothermal;
     double T_iso;
     float ff_Tiso[2];
+    // double-well constants (eos_kind 3): beta, rho_l, rho_v, p0 (and float copies)
+    double sp[4];
+    float spf[4], ff_p0[2];
 };
 
 template <typename R> __device__ __forceinline__ R exp_(R x);
 template <> __device__ __forceinline__ float exp_(float x) { return expf(x); }
 template <> __device__ __forceinline__ double exp_(double x) { return exp(x); }
 
-// Pressure p(rho, T) of the run's equation of state in type R: van der Waals
-// rho R T/(1 - b rho) - a rho^2 (main text) or Dieterici rho R T/(1 - b rho) exp(-a rho/(R T))
-// (SM "Coexistence curve").
+// Pressure part rho E0' - E0 of the double well E0 = beta (rho - rho_l)^2 (rho - rho_v)^2
+// (SM "Speed of sound"), from sp = {beta, rho_l, rho_v, p0}.
 template <typename R>
-__device__ __forceinline__ R eos_pressure(int kind, R a, R b, R Rg, R r, R t)
+__device__ __forceinline__ R well_pressure(const R *sp, R r)
+{
+    const R dl = r - sp[1], dv = r - sp[2];
+    return r * (R(2) * sp[0] * dl * dv * (dl + dv)) - sp[0] * dl * dl * dv * dv;
+}
+
+// Pressure p(rho, T) of the run's equation of state in type R: van der Waals
+// rho R T/(1 - b rho) - a rho^2 (main text), Dieterici rho R T/(1 - b rho) exp(-a rho/(R T))
+// (SM "Coexistence curve") or the double well p0 + rho E0' - E0 (SM "Speed of sound").
+template <typename R>
+__device__ __forceinline__ R eos_pressure(int kind, R a, R b, R Rg, R r, R t, const R *sp)
 {
     if (kind == 2) return r * Rg * t / (R(1) - b * r) * exp_(-a * r / (Rg * t));
+    if (kind == 3) return sp[3] + well_pressure<R>(sp, r);
     return r * Rg * t / (R(1) - b * r) - a * r * r;
 }
 
@@ -151,7 +164,7 @@ __global__ void k_init(DevParams p, const double *__restrict__ rho, const double
     gy *= 3.0;
     double r = rho[n], t = T[n];
     if (!(r > 0.0) || !(p.b * r < 1.0) || !(t > 0.0)) atomicAdd(&stats->bad_init, 1ull);
-    double pr = eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t);
+    double pr = eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t, p.sp);
     double P = pr > p.p_floor ? pr : p.p_floor;
     double th = P / (r * POND_TL), s = sqrt(th);
     double e = p.cv * t - p.a * r;
@@ -199,7 +212,7 @@ __global__ void k_moments(DevParams p, const R *__restrict__ st, double *rho, do
     if (ux) ux[n] = (double)REC(st, n, P_UHX);
     if (uy) uy[n] = (double)REC(st, n, P_UHY);
     if (T) T[n] = t;
-    if (pr) pr[n] = eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t);
+    if (pr) pr[n] = eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t, p.sp);
 }
 
 // Error-free sum of two doubles (Knuth TwoSum).

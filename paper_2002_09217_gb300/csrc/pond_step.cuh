@@ -353,6 +353,11 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
     tg = sg;
 }
 
+// The double-well constants in the arithmetic type of a kernel.
+template <typename R> __device__ __forceinline__ const R *typed_sp(const DevParams &p);
+template <> __device__ __forceinline__ const float *typed_sp<float>(const DevParams &p) { return p.spf; }
+template <> __device__ __forceinline__ const double *typed_sp<double>(const DevParams &p) { return p.sp; }
+
 // Results of one corrector evaluation (moments, e -> T, EoS) of a node, in R.
 template <typename R>
 struct EosOut {
@@ -390,7 +395,8 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const double *bhi
     const double T = p.isothermal ? p.T_iso : (e + p.a * rho) * p.pd.inv_cv;
     const double pr = p.eos_kind == 2
         ? rho * p.R * T * rcp_d(1.0 - p.b * rho) * exp(-p.a * rho * rcp_d(p.R * T))
-        : rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho;
+        : (p.eos_kind == 3 ? p.sp[3] + well_pressure<double>(p.sp, rho)
+                           : rho * p.R * T * rcp_d(1.0 - p.b * rho) - p.a * rho * rho);
     const double P = pr > p.p_floor ? pr : p.p_floor;
     const double ths = P * irho * 3.0;
     o.rho_hi = rho; o.rho_lo = 0.0; o.gs_hi = gs; o.gs_lo = 0.0;
@@ -426,9 +432,11 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const float *bhi,
     const ffv pre = ff_mul(ff_mul(ff_mul(rho, Rg), T), ff_rcp(den));
     // Dieterici: a product with no cancellation, so its exponential factor in FP32 (a few
     // ulps) is enough; van der Waals: the difference in float-float
+    // double well: p0 (a float pair) plus a small polynomial part, which FP32 carries
     const ffv pr = p.eos_kind == 2
         ? ff_mul(pre, expf(-(p.pf.a * rho.hi) / (p.pf.R * T.hi)))
-        : ff_add(pre, ff_neg(ff_mul(ff_mul(rho, rho), a)));
+        : (p.eos_kind == 3 ? ff_add(ffv{p.ff_p0[0], p.ff_p0[1]}, well_pressure<float>(p.spf, rho.hi))
+                           : ff_add(pre, ff_neg(ff_mul(ff_mul(rho, rho), a))));
     const bool floored = !(pr.hi > p.ff_pfl[0] || (pr.hi == p.ff_pfl[0] && pr.lo > p.ff_pfl[1]));
     const ffv P = floored ? ffv{p.ff_pfl[0], p.ff_pfl[1]} : pr;
     const ffv ths = ff_mul(ff_mul(P, irho), 3.0f);
@@ -504,7 +512,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                 sl[P_RHO] = r;
                 sl[P_T] = t;
             }
-            const R pr = eos_pressure<R>(p.eos_kind, q.a, q.b, q.R, r, t);
+            const R pr = eos_pressure<R>(p.eos_kind, q.a, q.b, q.R, r, t, typed_sp<R>(p));
             sl[S_PR] = pr;
             sl[S_PRR] = pr / r;
         }

@@ -77,8 +77,9 @@ class Workload:
     delta: float = 1.0 / 3.0
     k_cond: float = -1.0
     p_floor: float = 0.05 / 6.0     # 5 % of p_cr
-    eos: str = "vdw"                # or "dieterici" (isothermal)
+    eos: str = "vdw"                # or "dieterici" / "simplified" (isothermal)
     isothermal: bool = False        # T held at its (uniform) initial value
+    eos_params: tuple = ()          # (beta, rho_l, rho_v, p0) of "simplified"
 
     @property
     def nodes(self) -> int:
@@ -191,6 +192,38 @@ def nonclassical_tube(case="fig4", nx=1024, ny=1, width=2.0, tau=1.0):
     steps = int(round(c["t_star"] * nx / tab["U_ch"] / c["dt"]))
     return Workload("nonclassical_%s_%dx%d" % (case, nx, ny), nx, ny, 1, 0, 1.0, 0.0, tau, c["dt"],
                     steps, rho, z, z.copy(), T, delta=c["delta"])
+
+
+def simplified_eos(kind="slab", phase="liquid", nx=256, ny=1, width=4.0, amp=1e-3, pulse_width=12.0,
+                   steps=None, kappa=0.1, tau=1.0):
+    """The SM's simplified near-critical EoS (double-well free energy, density ratio 10),
+    isothermal: kind "slab" is a liquid slab over the middle half of a periodic box in its
+    vapour at the two saturated densities; kind "pulse" a uniform saturated `phase` with
+    a Gaussian density bump of relative amplitude `amp` at x = nx/4 (kappa = 0).  T is a
+    placeholder (the EoS does not depend on it).  The slab takes dt <= 0.1: across its
+    interface the gauge temperature changes tenfold through the double well's spinodal,
+    and dt = 0.25 diverged there (the bulk-state rule gives 0.5)."""
+    sp = table()["simplified"]
+    rl, rv, dt = sp["rho_l"], sp["rho_v"], sp["dt"]
+    x = np.arange(nx) + 0.5
+    if kind == "slab":
+        prof = rv + (rl - rv) * 0.5 * (np.tanh((x - nx / 4) / width) - np.tanh((x - 3 * nx / 4) / width))
+        dt = min(dt, 0.1)
+        steps = int(math.ceil(1500.0 / dt)) if steps is None else steps
+        name = "simplified_slab_%dx%d" % (nx, ny)
+    elif kind == "pulse":
+        rho0 = rl if phase == "liquid" else rv
+        prof = rho0 * (1.0 + amp * np.exp(-((x - 0.0 - nx / 4) / pulse_width) ** 2))
+        kappa = 0.0
+        steps = 40000 if steps is None else steps
+        name = "simplified_%s_pulse_%dx%d" % (phase, nx, ny)
+    else:
+        raise ValueError("kind must be slab or pulse")
+    rho = np.tile(prof, (ny, 1))
+    z = np.zeros((ny, nx))
+    return Workload(name, nx, ny, 0, 0, 1.0, kappa, tau, dt, steps, rho, z, z.copy(), np.full((ny, nx), 0.1),
+                    p_floor=1e-4, eos="simplified", isothermal=True,
+                    eos_params=(sp["beta"], rl, rv, sp["p0"]))
 
 
 def sound_pulse(Tr=0.9, phase="vapour", nx=2048, ny=1, amp=1e-3, width=12.0, steps=40000, tau=1.0,

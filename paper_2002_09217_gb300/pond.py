@@ -17,7 +17,7 @@ from . import build_lib
 
 POND_PERIODIC, POND_ZEROGRAD = 0, 1
 POND_D2Q9 = 0
-POND_VDW, POND_IDEAL, POND_DIETERICI = 0, 1, 2
+POND_VDW, POND_IDEAL, POND_DIETERICI, POND_SIMPLIFIED = 0, 1, 2, 3
 POND_FP64, POND_MIXED = 0, 1
 NPLANES = 25
 STATUS = {0: "POND_OK", 1: "POND_EINVAL", 2: "POND_ENOMEM", 3: "POND_ECUDA", 4: "POND_ENONCONV",
@@ -37,7 +37,8 @@ class Lattice(C.Structure):
 
 class Eos(C.Structure):
     _fields_ = [("kind", C.c_int32), ("a", C.c_double), ("b", C.c_double), ("R", C.c_double),
-                ("delta", C.c_double), ("isothermal", C.c_int32), ("T_iso", C.c_double)]
+                ("delta", C.c_double), ("isothermal", C.c_int32), ("T_iso", C.c_double),
+                ("beta", C.c_double), ("rho_l", C.c_double), ("rho_v", C.c_double), ("p0", C.c_double)]
 
 
 class Opts(C.Structure):
@@ -146,7 +147,8 @@ class Simulation:
                  max_iter: int = 20, k_cond: float = -1.0, p_floor: float = 1e-3 / 6.0,
                  stream=None, torch_alloc: bool = True, ideal: bool = False,
                  lanes_per_node: int = 0, tile_x: int = 0, eos: str = "vdw",
-                 isothermal: bool = False, T_iso: float = 0.0, nonlocal_: str = "lagged"):
+                 isothermal: bool = False, T_iso: float = 0.0, nonlocal_: str = "lagged",
+                 eos_params: tuple = ()):
         torch = _torch()
         self._lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -180,10 +182,12 @@ class Simulation:
             self._cb_alloc, self._cb_free = _ALLOC(), _FREE()
         grid = Grid(self.nx, self.ny, bc_x, bc_y)
         lat = Lattice(POND_D2Q9)
-        if eos not in ("vdw", "dieterici"):
-            raise ValueError("eos must be 'vdw' or 'dieterici'")
-        kind = POND_DIETERICI if eos == "dieterici" else (POND_IDEAL if ideal else POND_VDW)
-        eos_c = Eos(kind, a, b, R, delta, 1 if isothermal else 0, float(T_iso))
+        if eos not in ("vdw", "dieterici", "simplified"):
+            raise ValueError("eos must be 'vdw', 'dieterici' or 'simplified'")
+        kind = {"dieterici": POND_DIETERICI, "simplified": POND_SIMPLIFIED}.get(
+            eos, POND_IDEAL if ideal else POND_VDW)
+        sp = tuple(float(v) for v in eos_params) if eos == "simplified" else (0.0, 0.0, 0.0, 0.0)
+        eos_c = Eos(kind, a, b, R, delta, 1 if isothermal else 0, float(T_iso), *sp)
         opts = Opts(POND_MIXED if precision == "mixed" else POND_FP64, max_iter, tol, dt, k_cond,
                     p_floor, C.c_void_p(self._stream.cuda_stream), self._cb_alloc, self._cb_free, None,
                     lanes_per_node, tile_x, {"lagged": 0, "current": 1}[nonlocal_])
@@ -349,7 +353,8 @@ class Batch:
 
 def from_workload(w, precision: str = "mixed", **kw) -> Simulation:
     """Simulation for an ``inputs.Workload`` (parameters only; call init_fields)."""
-    iso = dict(eos=w.eos, isothermal=w.isothermal, T_iso=float(w.T.flat[0]) if w.isothermal else 0.0)
+    iso = dict(eos=w.eos, isothermal=w.isothermal, T_iso=float(w.T.flat[0]) if w.isothermal else 0.0,
+               eos_params=tuple(w.eos_params))
     iso.update(kw)
     return Simulation(w.nx, w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R, delta=w.delta,
                       kappa=w.kappa, tau=w.tau, precision=precision, dt=w.dt, k_cond=w.k_cond,

@@ -13,7 +13,7 @@ FIELDS = ("rho", "ux", "uy", "T", "p")
 def params_of(w, **over) -> oracle.Params:
     kw = dict(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R, delta=w.delta,
               kappa=w.kappa, tau=w.tau, dt=w.dt, k_cond=w.k_cond, p_floor=w.p_floor, tol=1e-12,
-              max_iter=20, eos=w.eos, isothermal=w.isothermal,
+              max_iter=20, eos=w.eos, isothermal=w.isothermal, eos_params=tuple(w.eos_params),
               T_iso=float(w.T.flat[0]) if w.isothermal else 0.0)
     kw.update(over)
     return oracle.Params(**kw)

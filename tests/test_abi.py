@@ -64,7 +64,9 @@ def test_invalid_parameters_are_rejected_on_the_host(lib):
                          ctypes.byref(opts), ctypes.byref(out)) == 1
     for bad in (pond.Eos(pond.POND_DIETERICI, 32 / 441, 1 / 7, 1.0, 1 / 3, 0, 0.0),   # not isothermal
                 pond.Eos(0, 2 / 49, 2 / 21, 1.0, 1 / 3, 1, 0.0),                      # T_iso <= 0
-                pond.Eos(5, 2 / 49, 2 / 21, 1.0, 1 / 3)):                             # unknown kind
+                pond.Eos(5, 2 / 49, 2 / 21, 1.0, 1 / 3),                              # unknown kind
+                pond.Eos(pond.POND_SIMPLIFIED, 0, 0, 1, 1 / 3, 0, 0.0, 1e-3, 5.0, 0.5, 0.1),  # not isothermal
+                pond.Eos(pond.POND_SIMPLIFIED, 0, 0, 1, 1 / 3, 1, 0.1, 1e-3, 5.0, 0.5, 0.0)):  # p0 = 0
         assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(bad), 0.0, 1.0,
                              ctypes.byref(opts), ctypes.byref(out)) == 1
     assert not out.value

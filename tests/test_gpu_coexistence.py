@@ -48,3 +48,13 @@ def test_isothermal_dieterici_on_maxwell(experiments, Tr, precision):
     assert res["nonfinite"] == 0 and res["clamped"] == 0
     assert res["rho_v"] == pytest.approx(rv, rel=0.01), res
     assert res["rho_l"] == pytest.approx(rl, rel=0.01), res
+
+
+def test_double_well_slab_near_its_saturated_densities(experiments):
+    """The simplified EoS's slab oscillates slowly about its saturated densities; the
+    average of the last quarter sits within 3 %."""
+    sp = thermo.SIMP
+    res = experiments.coexistence(inputs.simplified_eos("slab", nx=256), "mixed")
+    assert res["nonfinite"] == 0
+    assert res["rho_v"] == pytest.approx(sp["rho_v"], rel=0.03), res
+    assert res["rho_l"] == pytest.approx(sp["rho_l"], rel=0.03), res

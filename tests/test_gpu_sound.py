@@ -75,3 +75,12 @@ def test_isothermal_pulse_speed(experiments, precision, bar):
     res = experiments.sound_speed(w, precision)
     cT = math.sqrt(thermo.dp_drho_T(w.rho[0, w.nx // 2], w.T[0, 0]))
     assert res["c"] == pytest.approx(cT, rel=bar), res
+
+
+@pytest.mark.parametrize("phase", ["liquid", "vapour"])
+@pytest.mark.parametrize("precision,bar", [("fp64", 5e-4), ("mixed", 3e-3)])
+def test_double_well_pulse_speed(experiments, phase, precision, bar):
+    """The SM's simplified near-critical EoS: sqrt(2 beta rho)(rho_l - rho_v) in each phase."""
+    w = inputs.simplified_eos("pulse", phase, nx=2048)
+    res = experiments.sound_speed(w, precision)
+    assert res["c"] == pytest.approx(thermo.simplified_sound_speed(w.rho[0, w.nx // 2]), rel=bar), res

@@ -488,3 +488,46 @@ def test_classical_tube_has_a_rarefaction_fan():
     assert x2 < x1
     assert g2 < 0.65 * g1, (g1, g2)
     assert s2 > 0.85 * s1, (s1, s2)
+
+
+# -------------------------------------------------- simplified near-critical EoS
+def test_double_well_coexistence_and_sound_speed_closed_forms():
+    """Equal pressure p0 and equal chemical potential at rho_v, rho_l (Simpson on
+    (dp/drho)/rho), and sqrt(dp/drho) = sqrt(2 beta rho) (rho_l - rho_v) there (SM)."""
+    sp = thermo.SIMP
+    rv, rl = sp["rho_v"], sp["rho_l"]
+    assert thermo.simplified_pressure(rv) == pytest.approx(sp["p0"], rel=1e-15)
+    assert thermo.simplified_pressure(rl) == pytest.approx(sp["p0"], rel=1e-15)
+    r = np.linspace(rv, rl, 20001)
+    h = 1e-6
+    dpdr = (thermo.simplified_pressure(r + h) - thermo.simplified_pressure(r - h)) / (2 * h)
+    assert abs(integrate.simpson(dpdr / r, x=r)) < 1e-9
+    for rho in (rv, rl):
+        want = math.sqrt(2 * sp["beta"] * rho) * (rl - rv)
+        assert thermo.simplified_sound_speed(rho) == pytest.approx(want, rel=1e-14)
+
+
+@pytest.mark.parametrize("phase", ["liquid", "vapour"])
+def test_double_well_pulse_speed(phase):
+    """Isothermal pulses in the saturated phases of the simplified EoS travel at the
+    closed-form speed (SM figure of the speed of sound with this EoS)."""
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.simplified_eos("pulse", phase, nx=400, pulse_width=6.0)
+    P = oracle.Params(nx=w.nx, ny=1, dt=w.dt, tau=w.tau, kappa=0.0, p_floor=w.p_floor,
+                      eos="simplified", isothermal=True, T_iso=w.T[0, 0], eos_params=w.eos_params)
+    rho0 = w.rho[0, w.nx // 2]
+    c_th = thermo.simplified_sound_speed(rho0)
+    st = oracle.init_state(P, *w.fields())
+    x0 = w.nx / 4.0
+    xs = np.arange(w.nx)
+    sel = (xs >= x0) & (xs < x0 + w.nx / 2)
+    n2 = int(round(0.3 * w.nx / c_th / w.dt))
+    cents, done = [], 0
+    for n in (n2 // 3, n2):
+        st = oracle.step(P, st, n - done)
+        done = n
+        p = oracle.moments(P, st)["p"][0]
+        d = np.clip(p[sel] - p[int(x0 + w.nx / 2)], 0.0, None)
+        cents.append((xs[sel] * d).sum() / d.sum())
+    c = (cents[1] - cents[0]) / ((n2 - n2 // 3) * w.dt)
+    assert c == pytest.approx(c_th, rel=1e-3)
