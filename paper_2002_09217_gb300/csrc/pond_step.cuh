@@ -586,12 +586,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         rEl = R(0.5) * kap * (gxn * gxn + gyn * gyn);
     }
     const R *own = tile + slot_of(X0 + tx, Y0 + ty) * TS;
-    R fx[9], gx[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        fx[i] = own[P_F + i];
-        gx[i] = own[P_G + i];
-    }
+    // the node's own populations are read from its staged slot where needed (holding
+    // them in 18 registers through the stream loop cost more than the shared loads)
     if (lane == 0) {
         sh.lam[grp][0] = own[P_TH];
         sh.lam[grp][1] = own[P_UX];
@@ -652,8 +648,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                 R fxr[3], gxr[3];   // own populations of this row of directions
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    fxr[a] = sel3(jy, fx[a], fx[3 + a], fx[6 + a]);
-                    gxr[a] = sel3(jy, gx[a], gx[3 + a], gx[6 + a]);
+                    fxr[a] = own[P_F + 3 * jy + a];
+                    gxr[a] = own[P_G + 3 * jy + a];
                 }
                 const R dy = -(s * R(jy - 1) + uy) * q.dt;
                 const R fly = floor(dy);
@@ -846,7 +842,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             {
                 const int i = pop;
                 const int kx = i % 3, ky = i / 3;
-                const R ft = pick(fx, i) + my_df, gt = pick(gx, i) + my_dg;
+                const R ft = own[P_F + i] + my_df, gt = own[P_G + i] + my_dg;
                 R exk[3], eyl[3], Wsk, Wsl, Whk, Whl;
                 row(kx, wsx, dvx, exk, Wsk, Whk);
                 row(ky, wsy, dvy, eyl, Wsl, Whl);
