@@ -98,3 +98,33 @@ def test_serving_results_equal_alone(pond):
         assert res.latency >= 0.0
     summary = serving.summarize(results, max(r.completed for r in results))
     assert summary["requests"] == len(reqs) and summary["p99_latency_s"] >= summary["p50_latency_s"]
+
+
+def test_batch_mixing_equations_of_state_equals_alone(pond):
+    """One batch group holding a van der Waals, an isothermal Dieterici, a double-well and
+    a non-classical (delta = 0.0125) simulation: each uses its own parameters from the
+    work list, so each result equals its alone run bit for bit."""
+    cases = [
+        (inputs.droplet(n=32, ny=24, Tr=0.9, radius=6.0), {}),
+        (inputs.dieterici_slab(0.8, nx=48, ny=4, steps=0), {}),
+        (inputs.simplified_eos("slab", nx=40, ny=4, steps=0), {}),
+        (dataclasses.replace(inputs.nonclassical_tube("fig4", nx=64, ny=2), steps=0), {}),
+    ]
+    steps = 9
+    batch = pond.Batch()
+    sims = []
+    for w, kw in cases:
+        s = pond.from_workload(w, precision="mixed", **kw)
+        s.init_fields(*w.fields())
+        batch.add(s)
+        sims.append(s)
+    batch.step(steps)
+    batch.synchronize()
+    for (w, kw), sim in zip(cases, sims):
+        got = sim.moments()
+        ref = _alone(pond, w, "mixed", kw, steps)
+        for key in ref:
+            np.testing.assert_array_equal(got[key], ref[key], err_msg="%s %s" % (w.name, key))
+    batch.close()
+    for s in sims:
+        s.close()
