@@ -2,11 +2,14 @@
 
 Requests (``inputs.Request``) arrive over time.  The server admits an arrived request
 when the device memory it needs fits the budget, initialises it on the GPU and adds it to
-the running batch; every scheduler turn advances all resident simulations together with
-``pond_batch_step`` (one launch per time step and kernel group, graph-replayed), retires
-those that reached their step count (fields back to the host), frees their memory and
-admits more.  Requests that arrive while others run join at the next turn, so their work
-overlaps on the device.  Latency of a request = completion time - arrival time.
+the running batch of its precision.  Each precision has its own batch on its own CUDA
+stream, the mixed one at higher priority, so the fast mixed-precision requests do not
+wait for the FP64 ones (which run at the FP64 pipe's 1/64 rate on GB300) and the two
+groups' kernels overlap on the device.  Whenever a batch's previous chunk of steps has finished (a CUDA event, polled
+without blocking), the server retires its requests that reached their step count (fields
+back to the host), frees their memory, admits more and launches the batch's next chunk
+with ``pond_batch_step`` (one launch per time step and kernel group, graph-replayed).
+Latency of a request = completion time - arrival time.
 
 The per-node arithmetic does not depend on the batch, so a request's result is the same
 stepped alone or in the mix (checked by the tests).
@@ -49,6 +52,8 @@ def footprint_bytes(nodes: int, precision: str) -> int:
 class Server:
     """Admits requests by device-memory footprint and steps them in one batch."""
 
+    PRECISIONS = ("mixed", "fp64")
+
     def __init__(self, hbm_budget: int, chunk: int = 50, max_resident: int = 64,
                  keep_fields: bool = True):
         import torch
@@ -57,55 +62,47 @@ class Server:
         self.chunk = int(chunk)
         self.max_resident = int(max_resident)
         self.keep_fields = keep_fields
-        self.stream = torch.cuda.Stream()
-        self.batch = pond.Batch(self.stream)
+        # the mixed stream at higher priority: an FP64 group launch holds tens of thousands
+        # of slow blocks, and the block scheduler would otherwise dispatch them ahead of the
+        # mixed group's
+        self.streams = {"mixed": torch.cuda.Stream(priority=-1), "fp64": torch.cuda.Stream(priority=0)}
+        self.batches = {k: pond.Batch(self.streams[k]) for k in self.PRECISIONS}
 
     def _start(self, req, now):
         w = inputs.request_workload(req)
-        sim = pond.from_workload(w, precision=req.precision, stream=self.stream)
+        sim = pond.from_workload(w, precision=req.precision, stream=self.streams[req.precision])
         sim.init_fields(*w.fields())
-        self.batch.add(sim)
+        self.batches[req.precision].add(sim)
         return {"req": req, "sim": sim, "left": req.steps, "admitted": now, "nodes": w.nodes,
                 "bytes": footprint_bytes(w.nodes, req.precision)}
 
     def run(self, requests, time_scale: float = 1.0) -> list[Result]:
         """Serve the requests; arrival times are in seconds after the start, multiplied
         by time_scale.  Returns one Result per request, in completion order."""
+        torch = self.torch
         pending = [(r.arrival * time_scale, r.rid, r) for r in requests]
         heapq.heapify(pending)
-        waiting = []          # arrived, not yet admitted (FIFO)
-        running = []
+        waiting = []                                   # arrived, not yet admitted (FIFO)
+        running = {k: [] for k in self.PRECISIONS}
+        inflight = {k: None for k in self.PRECISIONS}  # event after a batch's last chunk
         used = 0
         results = []
         t0 = time.perf_counter()
-        while pending or waiting or running:
+        while pending or waiting or any(running.values()):
             now = time.perf_counter() - t0
             while pending and pending[0][0] <= now:
                 waiting.append(heapq.heappop(pending)[2])
-            # admission by footprint, in arrival order
-            while waiting and len(running) < self.max_resident:
-                req = waiting[0]
-                need = footprint_bytes(req.side * req.side, req.precision)
-                if used + need > self.budget and running:
-                    break
-                waiting.pop(0)
-                item = self._start(req, now)
-                running.append(item)
-                used += item["bytes"]
-            if not running:
-                if pending:
-                    time.sleep(max(0.0, min(0.01, pending[0][0] - now)))
-                continue
-            n = min(self.chunk, min(it["left"] for it in running))
-            self.batch.step(n)
-            for it in running:
-                it["left"] -= n
-            done = [it for it in running if it["left"] == 0]
-            if done:
-                self.batch.synchronize()
-                for it in done:
+            busy = False
+            for k in self.PRECISIONS:
+                ev = inflight[k]
+                if ev is not None and not ev.query():
+                    busy = True
+                    continue
+                inflight[k] = None
+                # retire what the finished chunk completed (its stream is idle)
+                for it in [it for it in running[k] if it["left"] == 0]:
                     sim = it["sim"]
-                    self.batch.remove(sim)
+                    self.batches[k].remove(sim)
                     fields = sim.moments() if self.keep_fields else None
                     status = sim.stats()
                     sim.close()
@@ -114,17 +111,53 @@ class Server:
                                           time.perf_counter() - t0, req.steps, it["nodes"],
                                           req.precision, fields, status))
                     used -= it["bytes"]
-                    running.remove(it)
-        self.batch.synchronize()
+                    running[k].remove(it)
+            # admission by footprint, in arrival order
+            while waiting and sum(len(v) for v in running.values()) < self.max_resident:
+                req = waiting[0]
+                need = footprint_bytes(req.side * req.side, req.precision)
+                if used + need > self.budget and any(running.values()):
+                    break
+                k = req.precision
+                if inflight[k] is not None:
+                    break                  # its batch is stepping; it joins after the chunk
+                waiting.pop(0)
+                item = self._start(req, time.perf_counter() - t0)
+                running[k].append(item)
+                used += item["bytes"]
+            for k in self.PRECISIONS:
+                if inflight[k] is None and running[k]:
+                    n = min(self.chunk, min(it["left"] for it in running[k]))
+                    self.batches[k].step(n)
+                    for it in running[k]:
+                        it["left"] -= n
+                    ev = torch.cuda.Event()
+                    ev.record(self.streams[k])
+                    inflight[k] = ev
+                    busy = True
+            if not busy and not waiting:
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0][0] - (time.perf_counter() - t0))))
+            elif busy:
+                time.sleep(0.0002)
+        for k in self.PRECISIONS:
+            self.batches[k].synchronize()
         return results
 
     def close(self):
-        self.batch.close()
+        for b in self.batches.values():
+            b.close()
 
 
 def summarize(results: list[Result], wall: float) -> dict:
     lat = np.array([r.latency for r in results])
     nodes = sum(r.nodes * r.steps for r in results)
+    by = {}
+    for prec in sorted({r.precision for r in results}):
+        l = np.array([r.latency for r in results if r.precision == prec])
+        by[prec] = {"requests": int(l.size), "p50_latency_s": float(np.percentile(l, 50)),
+                    "p99_latency_s": float(np.percentile(l, 99))}
     return {"requests": len(results), "sims_per_s": len(results) / wall,
             "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "node_updates": int(nodes), "mlups": nodes / wall / 1e6, "wall_s": wall}
+            "node_updates": int(nodes), "mlups": nodes / wall / 1e6, "wall_s": wall,
+            "by_precision": by}
