@@ -91,7 +91,9 @@ typedef struct {
 } pond_eos;
 
 /* Options.  precision: POND_FP64 (all FP64) or POND_MIXED (FP32 populations and
- * streaming/collision arithmetic; FP64 e->T, EoS, frame residual and sums).
+ * streaming/collision arithmetic; e->T, EoS and the conserved sums in float-float, i.e.
+ * pairs of FP32 values carrying ~48 bits; the storage-rounding remainders of mass,
+ * momentum and energy kept beside each node).
  * dt: time step (Delta x = 1), 0 < dt <= 1.  tol / max_iter: frame search stop rule.
  * k_cond: conductivity; < 0 selects k = mu (C_v + R), mu = (tau - 1/2) P dt.
  * p_floor: pressure floor of the gauge temperature theta = max(p, p_floor)/(rho T_L).

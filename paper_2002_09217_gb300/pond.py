@@ -137,7 +137,8 @@ def _torch():
 class Simulation:
     """One PonD simulation on the current CUDA device (see include/pond.h).
 
-    precision: "mixed" (FP32 populations + FP64 EoS/residual) or "fp64".
+    precision: "mixed" (FP32 populations and arithmetic, float-float EoS and conserved
+    sums) or "fp64".
     """
 
     def __init__(self, nx: int, ny: int, *, bc_x: int = POND_PERIODIC, bc_y: int = POND_PERIODIC,
