@@ -4,15 +4,18 @@
 // of LPN = 8 or 16 lanes of one warp.  Per node:
 //   phase 0  non-local terms from the previous step's rho and T (radius 2): lane l of the
 //            group takes the l-th non-rest neighbour, builds the Korteweg stress K and the
-//            heat flux q there, and the group sums W c . K and W c . q into F = -div K and
-//            M_0 = 2 div q (Eq. korteweg, Eq. gtilde).
+//            heat flux q there from the 8 differences around it, and the group sums
+//            W c . K and W c . q into F = -div K and M_0 = 2 div q (Eq. korteweg, Eq. gtilde).
 //   phase 1  frame search (block lockstep): the group streams all 9 directions x 16 stencil
-//            nodes (each lane 16/LPN stencil positions of every direction), reduces each
-//            direction's increment with warp shuffles, and warp 0 (one lane per node, 32 nodes per
-//            instruction) takes the moments, inverts e -> T, evaluates the EoS and the
-//            residual in FP64.
+//            nodes (each lane 16/LPN stencil positions of every direction), keeps each
+//            lane's partial increments in shared memory and reduces only the four moment
+//            sums per stream; warp 0 (one lane per node) takes the moments, inverts
+//            e -> T, evaluates the EoS and the residual, in FP64 in the FP64 form and in
+//            float-float (pairs of FP32) in the mixed form.
 //   phase 2  BGK collision with the force source, heat-flux correction and forced g
-//            equilibrium, one population per lane.
+//            equilibrium, one population per lane; the rest population takes the exact
+//            remainder of mass and energy, and what storage rounding takes from the
+//            conserved sums is kept beside the record.
 //
 // Staging.  Each block owns a tile of tile_x x (16 / tile_x) nodes and first copies the
 // records of the tile plus a halo of HALO = 3 nodes (their first 24 values) into shared
