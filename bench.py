@@ -432,7 +432,9 @@ def main():
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        # the mixed form's step computes in FP32 (its EoS and conserved sums in float-float
+        # pairs of FP32); the FP64 form in FP64
+        "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt, "precision": args.precision,
                    "launch_shape": shape or "default",
                    "l2": "flushed between timed steps (512 MiB write)",
