@@ -220,12 +220,18 @@ def roofline(w, precision, its, kernel_ms, pk):
     fl = its * flops_per_stream() + FLOPS_NONLOCAL + FLOPS_COLLIDE
     achieved = w.nodes * fl / (kernel_ms * 1e-3) / 1e12
     peak = alu_peak_tflops(precision, pk["sm_max_mhz"])
-    return {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(w, precision),
-            "peak_src": "%s: 152 SM x 128 lanes x 2 flop x %.0f MHz%s" % (
-                "FP32" if precision == "mixed" else "FP64", pk["sm_max_mhz"],
-                "" if precision == "mixed" else " / 64"),
-            "flops_per_update": fl, "kernel_ms": kernel_ms}
+    out = {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(w, precision),
+           "peak_src": "%s: 152 SM x 128 lanes x 2 flop x %.0f MHz%s" % (
+               "FP32" if precision == "mixed" else "FP64", pk["sm_max_mhz"],
+               "" if precision == "mixed" else " / 64"),
+           "flops_per_update": fl, "kernel_ms": kernel_ms}
+    fma = pk.get("fma_" + precision)
+    if fma:
+        # the same GPU's FMA-chain microbenchmark (pond_fma_peak), beside the derived peak
+        out["peak_measured_fma"] = fma
+        out["frac_of_measured_fma"] = achieved / fma
+    return out
 
 
 def end_to_end(w, pond, torch, stream, precision, shape, n_seg: int, reps: int) -> dict:
@@ -407,6 +413,11 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     pk = peaks()
+    for prec, iters in (("mixed", 200000), ("fp64", 20000)):
+        try:
+            pk["fma_" + prec] = pond.fma_peak(prec, iters, stream)
+        except pond.PondError:
+            pk["fma_" + prec] = None
 
     def shape_for(prec):
         if args.no_autotune:

@@ -258,6 +258,16 @@ void pond_batch_destroy(pond_batch *batch);
 /* Library version string. */
 const char *pond_version(void);
 
+/* Measurement utility (no counterpart in the paper): the arithmetic peak of this GPU's
+ * fused multiply-add pipes, for the roofline of the step kernel, which is bound by plain
+ * FP32 (mixed form) or FP64 (FP64 form) arithmetic.  Runs a kernel of 8 independent FMA
+ * chains per thread, iters FMAs each, on 8 blocks of 256 threads per SM, timed with CUDA
+ * events on `stream` (NULL = default stream); *tflops_out = 2 x FMAs / time in TFLOP/s.
+ * precision: POND_MIXED (FP32) or POND_FP64.  It allocates and frees a small device
+ * buffer and synchronises the stream.  Errors: POND_EINVAL (bad precision, iters < 1,
+ * NULL output), POND_ECUDA. */
+pond_status pond_fma_peak(int32_t precision, int32_t iters, void *stream, double *tflops_out);
+
 #ifdef __cplusplus
 }
 #endif

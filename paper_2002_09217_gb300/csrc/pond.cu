@@ -235,6 +235,56 @@ cudaError_t noalloc_scratch(double **ptr)
 
 }  // namespace
 
+namespace {
+// 8 independent chains a = a * m + c per thread (m, c chosen so that values stay finite
+// and the compiler cannot fold them); one value per thread is written so that nothing
+// is eliminated.
+template <typename R>
+__global__ void k_fma_chains(R *out, int iters, R m, R c)
+{
+    R a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = R(threadIdx.x + k) * R(1e-3);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    }
+    R s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename R>
+pond_status fma_peak(int iters, cudaStream_t s, double *tflops)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return POND_ECUDA;
+    const int blocks = 8 * sms, threads = 256;
+    R *out = nullptr;
+    if (cudaMalloc((void **)&out, (size_t)blocks * threads * sizeof(R)) != cudaSuccess) return POND_ECUDA;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    k_fma_chains<R><<<blocks, threads, 0, s>>>(out, iters / 10 + 1, R(0.999999), R(1e-6));   // warm-up
+    cudaEventRecord(e0, s);
+    k_fma_chains<R><<<blocks, threads, 0, s>>>(out, iters, R(0.999999), R(1e-6));
+    cudaEventRecord(e1, s);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e != cudaSuccess || !(ms > 0.0f)) return POND_ECUDA;
+    *tflops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3) / 1e12;
+    return POND_OK;
+}
+}  // namespace
+
 extern "C" {
 
 pond_status pond_conservation_noalloc(const double *d_planes, int64_t n_nodes, double out[4],
@@ -258,6 +308,15 @@ pond_status pond_conservation_noalloc(const double *d_planes, int64_t n_nodes, d
 
 
 const char *pond_version(void) { return "pond-gb300 0.1 (sm_103a)"; }
+
+
+pond_status pond_fma_peak(int32_t precision, int32_t iters, void *stream, double *tflops_out)
+{
+    if (!tflops_out || iters < 1 || (precision != POND_MIXED && precision != POND_FP64)) return POND_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    return precision == POND_MIXED ? fma_peak<float>(iters, s, tflops_out)
+                                   : fma_peak<double>(iters, s, tflops_out);
+}
 
 const char *pond_last_error(const pond_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 

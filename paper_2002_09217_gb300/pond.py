@@ -103,6 +103,8 @@ def load() -> C.CDLL:
         lib.pond_device_bytes.argtypes = [P]
         lib.pond_device_bytes.restype = C.c_size_t
         lib.pond_version.restype = C.c_char_p
+        lib.pond_fma_peak.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double)]
+        lib.pond_fma_peak.restype = C.c_int
         lib.pond_conservation_noalloc.argtypes = [C.c_void_p, C.c_int64, dp, C.c_void_p]
         lib.pond_conservation_noalloc.restype = C.c_int
         lib.pond_batch_create.argtypes = [C.c_void_p, C.POINTER(C.c_void_p)]
@@ -360,3 +362,15 @@ def from_workload(w, precision: str = "mixed", **kw) -> Simulation:
     return Simulation(w.nx, w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R, delta=w.delta,
                       kappa=w.kappa, tau=w.tau, precision=precision, dt=w.dt, k_cond=w.k_cond,
                       p_floor=w.p_floor, **iso)
+
+
+def fma_peak(precision: str = "mixed", iters: int = 20000, stream=None) -> float:
+    """Measured FMA-pipe peak of the current GPU in TFLOP/s (FP32 for "mixed", FP64 for
+    "fp64"), from pond_fma_peak."""
+    lib = load()
+    out = C.c_double()
+    strm = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = lib.pond_fma_peak(POND_MIXED if precision == "mixed" else POND_FP64, int(iters), strm, C.byref(out))
+    if st != 0:
+        raise PondError(st, "pond_fma_peak failed")
+    return out.value

@@ -252,3 +252,14 @@ def test_current_time_context_is_stepped_alone(pond):
             batch.add(sim)
         batch.close()
         sim.step(2)
+
+
+def test_fma_peak_microbenchmark_is_plausible(pond):
+    """The measurement utility's FMA-chain peaks sit below the unit-count peaks of a
+    152-SM, 2.07 GHz GPU (FP32 80.5 TFLOP/s, FP64 at 1/64) and above half of them."""
+    import torch
+    n32 = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    fp32 = pond.fma_peak("mixed", 100000)
+    fp64 = pond.fma_peak("fp64", 10000)
+    assert 0.5 * n32 < fp32 < 1.05 * n32, (fp32, n32)
+    assert 0.3 * n32 / 64 < fp64 < 1.05 * n32 / 64, (fp64, n32 / 64)
