@@ -58,3 +58,37 @@ def test_double_well_slab_near_its_saturated_densities(experiments):
     assert res["nonfinite"] == 0
     assert res["rho_v"] == pytest.approx(sp["rho_v"], rel=0.03), res
     assert res["rho_l"] == pytest.approx(sp["rho_l"], rel=0.03), res
+
+
+def _laplace_dpR(pond, R, n, steps=120000, every=500):
+    """Pressure inside minus outside a droplet of radius R in an n x n periodic box at
+    0.9 T_cr, averaged over the second half of the run (the droplet and the box ring with
+    sound waves), times R."""
+    import numpy as np
+    w = inputs.droplet(n=n, Tr=0.9, radius=float(R), amp=0.0, steps=steps)
+    dps = []
+    with pond.from_workload(w, precision="mixed") as sim:
+        sim.init_fields(*w.fields())
+        sim.step(steps // 2)
+        for _ in range(steps // 2 // every):
+            sim.step(every)
+            p = sim.moments()["p"]
+            c = n // 2
+            inside = p[c - 4:c + 4, c - 4:c + 4].mean()
+            corners = np.concatenate([p[:6, :6].ravel(), p[-6:, -6:].ravel(), p[:6, -6:].ravel(),
+                                      p[-6:, :6].ravel()])
+            dps.append(inside - corners.mean())
+    return float(np.mean(dps)) * R
+
+
+def test_laplace_law_two_radii(experiments):
+    """Delta p = sigma / R: Delta p R is the same for droplets of radius 32 and 64 (the
+    interface is 4 nodes wide, so smaller droplets are not used).  The droplets and the
+    box keep ringing with sound and the temperature relaxes slowly, so the time averages
+    agree to ~12 % (measured 0.030 / 0.026); the bar, 20 %, still tells the 1/R law from
+    any other (a pressure jump independent of R would be 100 % off)."""
+    from paper_2002_09217_gb300 import pond
+    s32 = _laplace_dpR(pond, 32, 128)
+    s64 = _laplace_dpR(pond, 64, 256)
+    assert s32 > 0 and s64 > 0
+    assert s32 == pytest.approx(s64, rel=0.2), (s32, s64)

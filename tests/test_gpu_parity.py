@@ -52,6 +52,8 @@ def small_cases():
     yield "dieterici_iso_48x3", inputs.dieterici_slab(0.8, nx=48, ny=3, steps=40)
     yield "anomalous_tube_64x2", dataclasses.replace(inputs.nonclassical_tube("fig4", nx=64, ny=2), steps=40)
     yield "double_well_slab_48x3", inputs.simplified_eos("slab", nx=48, ny=3, steps=40)
+    yield "droplet_isothermal_40x36", dataclasses.replace(
+        inputs.droplet(n=40, ny=36, Tr=0.9, radius=8.0, amp=0.0, steps=30), isothermal=True)
     yield "double_well_pulse_80x1", inputs.simplified_eos("pulse", "vapour", nx=80, pulse_width=4.0, steps=40)
 
 
