@@ -265,3 +265,29 @@ def test_fma_peak_microbenchmark_is_plausible(pond):
     fp64 = pond.fma_peak("fp64", 10000)
     assert 0.5 * n32 < fp32 < 1.05 * n32, (fp32, n32)
     assert 0.3 * n32 / 64 < fp64 < 1.05 * n32 / 64, (fp64, n32 / 64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_checkpoint_and_resume(pond, precision):
+    """Stop after 20 steps, save the state (pond_get_state), restore it into a new context
+    (pond_set_state) and run 15 more: the same fields as 35 steps straight, to rounding of
+    what the exchanged state leaves out (the momentum's kept low part, below one ulp)."""
+    w = inputs.droplet(n=40, ny=28, Tr=0.9, radius=7.0, steps=35)
+    straight, _ = gpu_run(pond, w, precision)
+    with pond.from_workload(w, precision=precision) as a:
+        a.init_fields(*w.fields())
+        a.step(20)
+        saved = a.get_state()
+    with pond.from_workload(w, precision=precision) as b:
+        b.set_state(saved)
+        b.step(15)
+        resumed = b.moments()
+    err = rel_linf(resumed, straight)
+    assert max(err.values()) <= (1e-12 if precision == "fp64" else 1e-6), err
+
+
+def test_oversized_grid_is_out_of_memory(pond):
+    """A grid whose state cannot fit in device memory is refused with POND_ENOMEM."""
+    with pytest.raises(pond.PondError) as ei:
+        pond.Simulation(200000, 200000, precision="fp64")
+    assert ei.value.status == 2
