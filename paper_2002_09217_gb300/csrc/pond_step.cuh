@@ -318,7 +318,9 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
 {
     const R thn = v[P_TH];
     const R sn = v[P_SQ];
-    const R qm1 = fdiv_(thn - th, (sn + s) * s);    // (s_n - s)/s without cancellation
+    // (s_n - s)/s: in FP32 without cancellation, in FP64 directly (its rounding, ~1e-16 of
+    // s_n/s, stays far below what the result needs, and saves a reciprocal per pair)
+    const R qm1 = sizeof(R) == 8 ? sn * inv_s - R(1) : fdiv_(thn - th, (sn + s) * s);
     const R wx = (v[P_UX] - ux) * inv_s;
     const R wy = (v[P_UY] - uy) * inv_s;
     R Ex[3], Ey[3];
@@ -768,7 +770,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         const R rr = m[0], uxr = m[1], uyr = m[2], uhxr = m[3], uhyr = m[4], Er = m[5];
         const R Pr = m[7], thsr = m[8];
         const R sst = sqrt_(thsr);
-        const R qm1 = fdiv_(sh.dlam[grp][0], (sst + s) * s);
+        const R qm1 = sizeof(R) == 8 ? sst * inv_s - R(1) : fdiv_(sh.dlam[grp][0], (sst + s) * s);
         const R wsx = sh.dlam[grp][1] * inv_s, wsy = sh.dlam[grp][2] * inv_s;
         const R dtr = q.dt, om = q.omega;
         const R irr = frcp_(rr), iP2 = frcp_(R(2) * Pr);
