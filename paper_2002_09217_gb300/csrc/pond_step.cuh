@@ -329,6 +329,32 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
         Ex[a] = ell_inc<R>(jx, a, qm1 * R(a - 1) + wx);
         Ey[a] = ell_inc<R>(jy, a, qm1 * R(a - 1) + wy);
     }
+    if constexpr (sizeof(R) == 8) {
+        // FP64: the transfer applied directly, [G_n f_n]_(jx,jy) - f_x (its rounding is far
+        // below what the FP64 form needs; the increment form is for FP32)
+        R Gx[3], Gy[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            Gx[a] = Ex[a] + (a == jx ? R(1) : R(0));
+            Gy[a] = Ey[a];
+        }
+        R rf[3], rg[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            rf[b] = Gx[0] * v[P_F + 3 * b] + Gx[1] * v[P_F + 3 * b + 1] + Gx[2] * v[P_F + 3 * b + 2];
+            rg[b] = Gx[0] * v[P_G + 3 * b] + Gx[1] * v[P_G + 3 * b + 1] + Gx[2] * v[P_G + 3 * b + 2];
+        }
+        // Gy = Ey + delta(b, jy): the delta picks row jy
+        R sf = sel3(jy, rf[0], rf[1], rf[2]) - fxj, sg = sel3(jy, rg[0], rg[1], rg[2]) - gxj;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            sf += Gy[b] * rf[b];
+            sg += Gy[b] * rg[b];
+        }
+        tf = sf;
+        tg = sg;
+        return;
+    }
     R txf[3], txg[3];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
