@@ -16,9 +16,23 @@ _lock = threading.Lock()
 _lib = None
 
 NPLANES = 25
-# plane layout of a state array of shape (25, ny, nx): f_0..f_8, g_0..g_8, theta, ux, uy,
-# rho, T, uhat_x, uhat_y.  Population index i = 3*jy + jx with c = j - 1.
+# plane layout of a D2Q9 state array of shape (25, ny, nx): f_0..f_8, g_0..g_8, theta, ux,
+# uy, rho, T, uhat_x, uhat_y.  Population index i = 3*jy + jx with c = j - 1.
 PL = dict(f=0, g=9, theta=18, ux=19, uy=20, rho=21, T=22, uhx=23, uhy=24)
+
+LATTICES = {"d2q9": 0, "d2q16": 1}
+
+
+def lattice_q(lattice: str = "d2q9") -> int:
+    """Populations of a lattice: 9 (D2Q9) or 16 (D2Q16)."""
+    return {"d2q9": 9, "d2q16": 16}[lattice]
+
+
+def plane_layout(lattice: str = "d2q9") -> dict:
+    """Plane indices of a state (2Q + 7 planes): f_0.., g_0.., theta, ux, uy, rho, T, uhat."""
+    Q = lattice_q(lattice)
+    return dict(f=0, g=Q, theta=2 * Q, ux=2 * Q + 1, uy=2 * Q + 2, rho=2 * Q + 3, T=2 * Q + 4,
+                uhx=2 * Q + 5, uhy=2 * Q + 6, n=2 * Q + 7)
 
 
 def lib_path() -> str:
@@ -43,7 +57,8 @@ class _CParams(C.Structure):
                 ("p_floor", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int32),
                 ("eos_kind", C.c_int32), ("dt", C.c_double), ("isothermal", C.c_int32),
                 ("pad", C.c_int32), ("T_iso", C.c_double), ("sp_beta", C.c_double),
-                ("sp_rho_l", C.c_double), ("sp_rho_v", C.c_double), ("sp_p0", C.c_double)]
+                ("sp_rho_l", C.c_double), ("sp_rho_v", C.c_double), ("sp_p0", C.c_double),
+                ("lattice", C.c_int32), ("pad2", C.c_int32)]
 
 
 @dataclasses.dataclass
@@ -69,6 +84,15 @@ class Params:
     eos_params: tuple = ()    # (beta, rho_l, rho_v, p0) of the "simplified" double well
     nonlocal_: str = "lagged"  # non-local terms from t - dt ("lagged") or from a first
                                # pass's prediction of t ("current", two passes per step)
+    lattice: str = "d2q9"      # velocity set: "d2q9" (the paper's) or "d2q16"
+
+    @property
+    def Q(self) -> int:
+        return lattice_q(self.lattice)
+
+    @property
+    def nplanes(self) -> int:
+        return 2 * self.Q + 7
 
     def c(self) -> _CParams:
         if self.eos not in ("vdw", "dieterici", "simplified"):
@@ -79,7 +103,7 @@ class Params:
         return _CParams(self.nx, self.ny, self.bc_x, self.bc_y, self.a, self.b, self.R,
                         self.delta, self.kappa, self.tau, self.k_cond, self.p_floor, self.tol,
                         self.max_iter, {"vdw": 0, "dieterici": 1, "simplified": 2}[self.eos], self.dt,
-                        1 if self.isothermal else 0, 0, self.T_iso, *sp)
+                        1 if self.isothermal else 0, 0, self.T_iso, *sp, LATTICES[self.lattice], 0)
 
 
 def _load():
@@ -92,6 +116,9 @@ def _load():
         lib.orc_moment_matrix.argtypes = [dp, dp]
         lib.orc_gauge_matrix.argtypes = [dp, dp, dp]
         lib.orc_gauge_matrix.restype = C.c_int
+        lib.orc_moment_matrix_q.argtypes = [C.c_int32, dp, dp]
+        lib.orc_gauge_matrix_q.argtypes = [C.c_int32, dp, dp, dp]
+        lib.orc_gauge_matrix_q.restype = C.c_int
         lib.orc_lagrange4.argtypes = [C.c_double, dp]
         lib.orc_nonlocal.argtypes = [pp, dp, dp, dp]
         lib.orc_init.argtypes = [pp, dp, dp, dp, dp, dp]
@@ -122,32 +149,46 @@ def _d(x) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
 
 
-def weights() -> np.ndarray:
-    """D2Q9 weights W_i = W_jx W_jy (index i = 3*jy + jx, c = j - 1)."""
-    w1 = np.array([1 / 6, 2 / 3, 1 / 6])
-    return np.array([w1[i % 3] * w1[i // 3] for i in range(9)])
+def lattice_1d(lattice: str = "d2q9") -> tuple[np.ndarray, np.ndarray, float]:
+    """C1, its weights and T_L: D2Q9 {-1, 0, 1}; D2Q16 the four Gauss-Hermite nodes."""
+    if lattice == "d2q16":
+        ci, co = np.sqrt(3 - np.sqrt(6)), np.sqrt(3 + np.sqrt(6))
+        wi, wo = (3 + np.sqrt(6)) / 12, (3 - np.sqrt(6)) / 12
+        return np.array([-co, -ci, ci, co]), np.array([wo, wi, wi, wo]), 1.0
+    return np.array([-1.0, 0.0, 1.0]), np.array([1 / 6, 2 / 3, 1 / 6]), 1.0 / 3.0
 
 
-def velocities(lam) -> tuple[np.ndarray, np.ndarray]:
+def weights(lattice: str = "d2q9") -> np.ndarray:
+    """Weights W_i = W_jx W_jy (index i = q1*jy + jx)."""
+    _, w1, _ = lattice_1d(lattice)
+    q1 = len(w1)
+    return np.array([w1[i % q1] * w1[i // q1] for i in range(q1 * q1)])
+
+
+def velocities(lam, lattice: str = "d2q9") -> tuple[np.ndarray, np.ndarray]:
     """Shifted velocities v_i = sqrt(theta) c_i + u of gauge lam = (theta, ux, uy)."""
     th, ux, uy = lam
-    c = np.array([(i % 3 - 1, i // 3 - 1) for i in range(9)], dtype=np.float64)
+    c1, _, _ = lattice_1d(lattice)
+    q1 = len(c1)
+    c = np.array([(c1[i % q1], c1[i // q1]) for i in range(q1 * q1)], dtype=np.float64)
     s = np.sqrt(th)
     return s * c[:, 0] + ux, s * c[:, 1] + uy
 
 
-def moment_matrix(lam) -> np.ndarray:
-    out = np.zeros(81)
-    _load().orc_moment_matrix(_p(_d(lam)), _p(out))
-    return out.reshape(9, 9)
+def moment_matrix(lam, lattice: str = "d2q9") -> np.ndarray:
+    Q = lattice_q(lattice)
+    out = np.zeros(Q * Q)
+    _load().orc_moment_matrix_q(LATTICES[lattice], _p(_d(lam)), _p(out))
+    return out.reshape(Q, Q)
 
 
-def gauge_matrix(src, dst) -> np.ndarray:
-    out = np.zeros(81)
-    rc = _load().orc_gauge_matrix(_p(_d(src)), _p(_d(dst)), _p(out))
+def gauge_matrix(src, dst, lattice: str = "d2q9") -> np.ndarray:
+    Q = lattice_q(lattice)
+    out = np.zeros(Q * Q)
+    rc = _load().orc_gauge_matrix_q(LATTICES[lattice], _p(_d(src)), _p(_d(dst)), _p(out))
     if rc:
         raise ValueError("singular moment matrix")
-    return out.reshape(9, 9)
+    return out.reshape(Q, Q)
 
 
 def lagrange4(xi: float) -> np.ndarray:
@@ -166,7 +207,7 @@ def nonlocal_fields(P: Params, rho, T) -> np.ndarray:
 
 
 def init_state(P: Params, rho, ux, uy, T) -> np.ndarray:
-    out = np.zeros((NPLANES, P.ny, P.nx))
+    out = np.zeros((P.nplanes, P.ny, P.nx))
     cp = P.c()
     _load().orc_init(C.byref(cp), _p(_d(rho)), _p(_d(ux)), _p(_d(uy)), _p(_d(T)), _p(out))
     return out
@@ -174,7 +215,7 @@ def init_state(P: Params, rho, ux, uy, T) -> np.ndarray:
 
 def stream_node(P: Params, state, X: int, Y: int, lam):
     state = _d(state)
-    ft = np.zeros(9); gt = np.zeros(9)
+    ft = np.zeros(P.Q); gt = np.zeros(P.Q)
     cp = P.c()
     rc = _load().orc_stream_node(C.byref(cp), _p(state), int(X), int(Y), _p(_d(lam)),
                                  _p(ft), _p(gt))
@@ -193,7 +234,7 @@ def macro(P: Params, lam, ft, gt, Fx=0.0, Fy=0.0, rEl=0.0) -> dict:
 
 
 def collide(P: Params, lam, ft, gt, mac, Fx=0.0, Fy=0.0, M0=0.0):
-    fo = np.zeros(9); go = np.zeros(9)
+    fo = np.zeros(P.Q); go = np.zeros(P.Q)
     raw = mac["_raw"] if isinstance(mac, dict) else _d(mac)
     cp = P.c()
     rc = _load().orc_collide(C.byref(cp), _p(_d(lam)), _p(_d(ft)), _p(_d(gt)), _p(_d(raw)),
@@ -204,7 +245,7 @@ def collide(P: Params, lam, ft, gt, mac, Fx=0.0, Fy=0.0, M0=0.0):
 
 
 def step(P: Params, state, n: int = 1, stats=None) -> np.ndarray:
-    """Advance the full grid by n time steps; returns the new state (25, ny, nx)."""
+    """Advance the full grid by n time steps; returns the new state (2Q + 7, ny, nx)."""
     cur = _d(state).copy()
     nxt = np.empty_like(cur)
     st = np.zeros(4)
@@ -232,10 +273,10 @@ def step(P: Params, state, n: int = 1, stats=None) -> np.ndarray:
 
 
 def step_nodes(P: Params, state, nodes, stats=None) -> np.ndarray:
-    """One step evaluated at the given flat node indices only; returns (len, 25)."""
+    """One step evaluated at the given flat node indices only; returns (len, 2Q + 7)."""
     state = _d(state)
     nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.int64))
-    out = np.zeros((len(nodes), NPLANES))
+    out = np.zeros((len(nodes), P.nplanes))
     st = np.zeros(4)
     cp = P.c()
     rc = _load().orc_step_nodes(C.byref(cp), _p(state), nodes.ctypes.data_as(C.POINTER(C.c_int64)),
