@@ -21,8 +21,16 @@
  * use the previous step's density and temperature.
  *
  * Conventions
- *   - Lattice D2Q9 (the only one): c = (cx, cy), cx, cy in {-1, 0, 1}; population
- *     index i = 3*(cy+1) + (cx+1); W = W_cx W_cy with W_0 = 2/3, W_+-1 = 1/6; T_L = 1/3.
+ *   - Lattices (the model holds for any tensor lattice C1 x C1, W_i = W_jx W_jy,
+ *     T_L = sum W c^2; SM "Equilibrium"):
+ *       POND_D2Q9 (the paper's): C1 = {-1, 0, 1}, population index i = 3*(cy+1) + (cx+1),
+ *         W_0 = 2/3, W_+-1 = 1/6, T_L = 1/3;
+ *       POND_D2Q16: C1 = the roots -+sqrt(3 +- sqrt 6) of He_4(c) = c^4 - 6 c^2 + 3 in
+ *         increasing order, index i = 4*jy + jx, Gauss-Hermite weights (3 - sqrt 6)/12
+ *         (outer) and (3 + sqrt 6)/12 (inner), T_L = 1; the transfer map is the product
+ *         of two 4-node Lagrange maps.  Q = 9 or 16 populations per family.
+ *     The non-local terms use the isotropic D2Q9 difference stencils on the grid with
+ *     either lattice.
  *   - Grids are nx * ny nodes, Delta x = 1, row-major with x fastest: node = y*nx + x.
  *   - Host arrays are always caller-owned; they are read or written during the call
  *     only.  Device memory is owned by the context; it is taken from the caller's
@@ -61,7 +69,7 @@ typedef enum {
 } pond_status;
 
 enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
-enum { POND_D2Q9 = 0 };                            /* lattice                         */
+enum { POND_D2Q9 = 0, POND_D2Q16 = 1 };           /* lattice                         */
 enum { POND_VDW = 0, POND_IDEAL = 1, POND_DIETERICI = 2, POND_SIMPLIFIED = 3 };   /* see pond_eos */
 enum { POND_FP64 = 0, POND_MIXED = 1 };            /* arithmetic / storage form       */
 enum { POND_NONLOCAL_LAGGED = 0, POND_NONLOCAL_CURRENT = 1 };   /* see pond_opts.nonlocal */
@@ -69,7 +77,7 @@ enum { POND_NONLOCAL_LAGGED = 0, POND_NONLOCAL_CURRENT = 1 };   /* see pond_opts
 /* Grid: nx, ny >= 1; bc_x, bc_y: POND_PERIODIC, or POND_ZEROGRAD (index clamp). */
 typedef struct { int32_t nx, ny; int32_t bc_x, bc_y; } pond_grid;
 
-typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9               */
+typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9 or POND_D2Q16 */
 
 /* Equation of state.  POND_VDW: van der Waals p = rho R T/(1 - b rho) - a rho^2 with
  * e = (R/delta) T - a rho (main text; SM "Thermodynamics"); 0 < delta <= 2/3.
@@ -102,7 +110,10 @@ typedef struct {
  * lanes_per_node: threads cooperating on one node in the step kernel, 8 or 16 (0 = 8).
  * tile_x: width of the step kernel's tile of 16 nodes, 1, 2, 4, 8 or 16 (tile height
  * 16 / tile_x; 0 = 16 for grids of fewer than 4 rows, else 4).  Both are performance
- * knobs (autotuning); results are the same to rounding.
+ * knobs (autotuning) of the D2Q9 kernel; results are the same to rounding.  The D2Q16
+ * kernel (one thread per node) ignores them.
+ * In the mixed form on D2Q16 the moments, e->T, EoS and frame-search residual are FP64
+ * and no storage-rounding remainders are kept.
  * nonlocal: time level of the Korteweg force, interface energy and heat-flux source,
  * which the paper leaves open.  POND_NONLOCAL_LAGGED (0): from rho, T at t - dt (one
  * launch per step).  POND_NONLOCAL_CURRENT (1): two passes per step, the first a lagged
@@ -140,8 +151,9 @@ typedef struct {
     int64_t max_streams;   /* largest streaming-pass count of any block        */
 } pond_stats_t;
 
-/* Create a context and allocate its device state (two state buffers of 25 planes,
- * a 5-plane FP64 staging buffer and reduction partials).  kappa >= 0: Korteweg coefficient (Eq. korteweg); tau > 1/2: BGK
+/* Create a context and allocate its device state (two state buffers of 2Q + 7 planes,
+ * a 5-plane FP64 staging buffer and reduction partials; on D2Q16 also 9 FP64 planes of
+ * non-local terms).  lattice: POND_D2Q9 or POND_D2Q16 (else POND_EINVAL).  kappa >= 0: Korteweg coefficient (Eq. korteweg); tau > 1/2: BGK
  * relaxation time, omega = 1/tau.  On success *out owns the context. */
 pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, const pond_eos *eos,
                         double kappa, double tau, const pond_opts *opts, pond_ctx **out);
@@ -173,8 +185,9 @@ pond_status pond_moments_device(pond_ctx *ctx, double *d_rho, double *d_ux, doub
  * sum rho uhat_y, sum_nodes sum_i g_i / 2 (total energy)}.  Synchronises. */
 pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 
-/* Full state as 25 host planes of nx*ny doubles: f_0..f_8, g_0..g_8, theta, u_x,
- * u_y (the gauge the populations are stored in), rho, T, uhat_x, uhat_y.
+/* Full state as 2Q + 7 host planes of nx*ny doubles (25 on D2Q9, 39 on D2Q16):
+ * f_0..f_(Q-1), g_0..g_(Q-1), theta, u_x, u_y (the gauge the populations are stored in),
+ * rho, T, uhat_x, uhat_y.
  * pond_get_state synchronises; pond_set_state replaces the current state.  In the mixed
  * form the library keeps, beside each node's FP32 populations, what storage rounding
  * took from mass, energy and momentum: f_4 and g_4 are exchanged with it (as doubles;
@@ -183,7 +196,8 @@ pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 pond_status pond_get_state(pond_ctx *ctx, double *state);
 pond_status pond_set_state(pond_ctx *ctx, const double *state);
 
-/* One time step (one launch of the fused step kernel) bracketed by CUDA events on the
+/* One time step (its launches: the fused step kernel on D2Q9; the two non-local kernels
+ * and the node step on D2Q16) bracketed by CUDA events on the
  * context stream; *ms_out = its duration in milliseconds.  Synchronises (a tracing
  * aid; pond_step is the fast path). */
 pond_status pond_step_timed(pond_ctx *ctx, double *ms_out);
@@ -237,7 +251,8 @@ const char *pond_last_error(const pond_ctx *ctx);
  * wait for the batch's work first.  pond_step on a batched context is POND_EINVAL. */
 pond_status pond_batch_create(void *stream, pond_batch **out);
 
-/* Add an initialised context (same device); waits for the context's queued work. */
+/* Add an initialised D2Q9 context (same device); waits for the context's queued work.
+ * A D2Q16 context is POND_EINVAL. */
 pond_status pond_batch_add(pond_batch *batch, pond_ctx *ctx);
 
 /* Remove a context (waits for the batch's work); the context may be stepped alone again. */

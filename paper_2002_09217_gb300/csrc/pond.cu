@@ -19,6 +19,7 @@
 
 #include "pond_kernels.cuh"
 #include "pond_step.cuh"
+#include "pond_q16.cuh"
 
 using namespace pond;
 
@@ -45,6 +46,8 @@ struct pond_ctx {
     int nonlocal = 0;              // 1: current-time non-local terms (two passes per step)
     void *pred = nullptr;          // first pass's state (nonlocal = 1)
     DevStats *dstats_pred = nullptr;
+    int lattice = POND_D2Q9;       // POND_D2Q16: plane-major state of NP16 planes
+    double *nlbuf = nullptr;       // D2Q16: NL_PLANES FP64 planes of non-local terms
     std::string err;
     size_t bytes = 0;
     DevParams dp{};
@@ -121,9 +124,42 @@ cudaError_t allow_step_smem()
     return e;
 }
 
+// D2Q16: the non-local terms of state `src` into nlbuf, then the node step in -> out.
+template <typename R>
+void launch_q16_pass(pond_ctx *c, const R *in, const R *src, R *out, DevStats *stats)
+{
+    const unsigned nb = blocks_for(c->N, 256);
+    k_q16_nonlocal1<R><<<nb, 256, 0, c->stream>>>(c->dp, src, c->nlbuf);
+    k_q16_nonlocal2<<<nb, 256, 0, c->stream>>>(c->dp, c->nlbuf);
+    // 32 x 4 node patches (128 x 1 strips on grids of fewer than 4 rows)
+    const dim3 blk = c->grid.ny < 4 ? dim3(128, 1) : dim3(32, 4);
+    const dim3 grd(blocks_for((size_t)c->grid.nx, blk.x), blocks_for((size_t)c->grid.ny, blk.y));
+    k_q16_step<R><<<grd, blk, 0, c->stream>>>(c->dp, in, c->nlbuf, out, stats);
+}
+
+template <typename R>
+pond_status launch_step_q16(pond_ctx *c, cudaEvent_t *ev)
+{
+    const R *in = (const R *)c->state[c->cur];
+    R *out = (R *)c->state[1 - c->cur];
+    if (ev) cudaEventRecord(ev[0], c->stream);
+    const R *nl = in;
+    if (c->nonlocal) {
+        // pass 1 predicts rho, T at t (lagged terms); pass 2 redoes the step with the
+        // non-local terms of that prediction
+        launch_q16_pass<R>(c, in, in, (R *)c->pred, c->dstats_pred);
+        nl = (const R *)c->pred;
+    }
+    launch_q16_pass<R>(c, in, nl, out, c->dstats);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    c->cur = 1 - c->cur;
+    return POND_OK;
+}
+
 template <typename R>
 pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
+    if (c->lattice == POND_D2Q16) return launch_step_q16<R>(c, ev);
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
     const int tx = c->dp.tile_x, ty = STEP_NB / tx;
@@ -149,6 +185,11 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 template <typename R>
 void launch_init(pond_ctx *c, const double *rho, const double *ux, const double *uy, const double *T)
 {
+    if (c->lattice == POND_D2Q16) {
+        k_q16_init<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, rho, ux, uy, T,
+                                                                    (R *)c->state[c->cur], c->dstats);
+        return;
+    }
     k_init<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, rho, ux, uy, T,
                                                              (R *)c->state[c->cur], c->dstats);
 }
@@ -156,6 +197,11 @@ void launch_init(pond_ctx *c, const double *rho, const double *ux, const double 
 template <typename R>
 void launch_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T, double *p)
 {
+    if (c->lattice == POND_D2Q16) {
+        k_q16_moments<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur],
+                                                                       rho, ux, uy, T, p);
+        return;
+    }
     k_moments<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur],
                                                                 rho, ux, uy, T, p);
 }
@@ -163,7 +209,10 @@ void launch_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T,
 template <typename R>
 void launch_conserve(pond_ctx *c)
 {
-    k_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
+    if (c->lattice == POND_D2Q16)
+        k_q16_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
+    else
+        k_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
     k_conserve2<<<1, 32, 0, c->stream>>>(c->part, c->red_blocks, c->part + 8 * c->red_blocks);
 }
 
@@ -332,7 +381,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     if ((grid->bc_x != POND_PERIODIC && grid->bc_x != POND_ZEROGRAD) ||
         (grid->bc_y != POND_PERIODIC && grid->bc_y != POND_ZEROGRAD))
         return POND_EINVAL;
-    if (lattice->kind != POND_D2Q9) return POND_EINVAL;
+    if (lattice->kind != POND_D2Q9 && lattice->kind != POND_D2Q16) return POND_EINVAL;
     if (eos->kind != POND_VDW && eos->kind != POND_IDEAL && eos->kind != POND_DIETERICI &&
         eos->kind != POND_SIMPLIFIED)
         return POND_EINVAL;
@@ -365,6 +414,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     c->eos = *eos;
     if (eos->kind == POND_IDEAL) { c->eos.a = 0.0; c->eos.b = 0.0; }
     c->opts = *opts;
+    c->lattice = lattice->kind;
     c->kappa = kappa;
     c->tau = tau;
     c->stream = (cudaStream_t)opts->stream;
@@ -412,19 +462,20 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     split(d.T_iso, d.ff_Tiso);
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
-    size_t sb = (size_t)SL * c->N * c->esize;
+    size_t sb = (size_t)(c->lattice == POND_D2Q16 ? NP16 : SL) * c->N * c->esize;
     c->state[0] = dev_alloc(c, sb);
     c->state[1] = dev_alloc(c, sb);
     c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
     c->part = (double *)dev_alloc(c, (8 * (size_t)c->red_blocks + 8) * sizeof(double));
     c->dstats = (DevStats *)dev_alloc(c, sizeof(DevStats));
+    if (c->lattice == POND_D2Q16) c->nlbuf = (double *)dev_alloc(c, (size_t)NL_PLANES * c->N * sizeof(double));
     c->nonlocal = opts->nonlocal;
     if (c->nonlocal) {
         c->pred = dev_alloc(c, sb);
         c->dstats_pred = (DevStats *)dev_alloc(c, sizeof(DevStats));
     }
     if (!c->state[0] || !c->state[1] || !c->stage || !c->part || !c->dstats ||
-        (c->nonlocal && (!c->pred || !c->dstats_pred))) {
+        (c->nonlocal && (!c->pred || !c->dstats_pred)) || (c->lattice == POND_D2Q16 && !c->nlbuf)) {
         pond_destroy(c);
         return POND_ENOMEM;
     }
@@ -450,6 +501,7 @@ void pond_destroy(pond_ctx *c)
     dev_free(c, c->dstats);
     dev_free(c, c->pred);
     dev_free(c, c->dstats_pred);
+    dev_free(c, c->nlbuf);
     delete c;
 }
 
@@ -563,6 +615,22 @@ pond_status pond_get_state(pond_ctx *c, double *state)
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null output");
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    if (c->lattice == POND_D2Q16) {
+        // plane-major on the device already: a copy (FP64) or a widening (FP32)
+        const size_t tot = (size_t)NP16 * c->N;
+        if (!mixed(c)) {
+            CK(cudaMemcpyAsync(state, c->state[c->cur], tot * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream), "cudaMemcpyAsync D2H");
+            CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+            return POND_OK;
+        }
+        std::vector<float> f(tot);
+        CK(cudaMemcpyAsync(f.data(), c->state[c->cur], tot * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream), "cudaMemcpyAsync D2H");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        for (size_t k = 0; k < tot; ++k) state[k] = (double)f[k];
+        return POND_OK;
+    }
     const size_t N = c->N, rec = (size_t)SL * N;
     std::vector<double> d(mixed(c) ? 0 : rec);
     std::vector<float> f(mixed(c) ? rec : 0);
@@ -590,6 +658,17 @@ pond_status pond_set_state(pond_ctx *c, const double *state)
     pond_status st = check_ctx(c);
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null input");
+    if (c->lattice == POND_D2Q16) {
+        const size_t tot = (size_t)NP16 * c->N;
+        std::vector<float> f(mixed(c) ? tot : 0);
+        for (size_t k = 0; k < f.size(); ++k) f[k] = (float)state[k];
+        const void *src = mixed(c) ? (const void *)f.data() : (const void *)state;
+        CK(cudaMemcpyAsync(c->state[c->cur], src, tot * c->esize, cudaMemcpyHostToDevice, c->stream),
+           "cudaMemcpyAsync H2D");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        c->initialised = true;
+        return POND_OK;
+    }
     const size_t N = c->N, rec = (size_t)SL * N;
     std::vector<double> d(mixed(c) ? 0 : rec, 0.0);
     std::vector<float> f(mixed(c) ? rec : 0, 0.0f);
@@ -797,6 +876,7 @@ pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
     if (c->batch) return bfail(b, POND_EINVAL, "context already belongs to a batch");
     if (!c->initialised) return bfail(b, POND_EINVAL, "context state not initialised");
     if (c->nonlocal) return bfail(b, POND_EINVAL, "two-pass (current-time) contexts are stepped alone");
+    if (c->lattice != POND_D2Q9) return bfail(b, POND_EINVAL, "batches step D2Q9 contexts");
     if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
     // the context's queued work (its initialisation) completes before the batch uses it

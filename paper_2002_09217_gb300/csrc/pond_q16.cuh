@@ -1,0 +1,594 @@
+// pond_q16.cuh -- the PonD van der Waals time step on the D2Q16 lattice for sm_103a.
+//
+// The model holds for any tensor lattice C1 x C1 with weights W_i = W_jx W_jy and lattice
+// temperature T_L = sum W c^2 (SM "Equilibrium").  D2Q16 takes for C1 the four roots
+// -+sqrt(3 +- sqrt 6) of the Hermite polynomial He_4(c) = c^4 - 6 c^2 + 3 with the
+// Gauss-Hermite weights (3 -+ sqrt 6)/12, so that T_L = 1.  The transfer map
+// G = M_lambda'^-1 M_lambda (SM "Transfer matrix") is then the product of two 4-node
+// Lagrange maps, one per axis, and keeps the sixteen moments M_mn, m, n <= 3.
+//
+// Layout: plane-major, plane k of node n at k*N + n, 39 planes (the ABI state's order):
+//   [0..15] f_0..f_15, [16..31] g_0..g_15, [32] theta, [33] u_x, [34] u_y, [35] rho,
+//   [36] T, [37] uhat_x, [38] uhat_y
+// with population i = 4*jy + jx, c_i = (C1[jx], C1[jy]).  A block covers a 2-D patch of
+// nodes with x fastest, so the stencil reads of a warp fall on neighbouring addresses of
+// one plane.
+//
+// One step is three launches: the Korteweg stress K and heat-flux vector q of the state
+// the non-local terms come from, their divergences F = -div K and M_0 = 2 div q, and the
+// node step (frame search with semi-Lagrangian streaming, then BGK collision with the
+// force, heat-flux and force-work sources).  R = float (FP32 storage and streaming /
+// collision arithmetic, FP64 moments, EoS and frame-search residual) or double.
+#pragma once
+
+#include "pond_kernels.cuh"
+
+namespace pond {
+
+constexpr int Q16 = 16;
+constexpr int NP16 = 2 * Q16 + 7;   // planes of a D2Q16 state
+enum : int { Q_F = 0, Q_G = 16, Q_TH = 32, Q_UX = 33, Q_UY = 34, Q_RHO = 35, Q_T = 36, Q_UHX = 37,
+             Q_UHY = 38 };
+// planes of the non-local scratch (FP64): K_xx, K_xy, K_yy, q_x, q_y, rho E_lambda, F_x, F_y, M_0
+enum : int { NL_KXX = 0, NL_KXY, NL_KYY, NL_QX, NL_QY, NL_REL, NL_FX, NL_FY, NL_M0, NL_PLANES };
+
+#define PLN(buf, plane, n, N) (buf)[(size_t)(plane) * (size_t)(N) + (size_t)(n)]
+
+// C1, its weights, and per node k: 1 / prod_{j != k} (c_k - c_j) (the Lagrange
+// denominator), the three other nodes o_m (in increasing order) and 1 / (c_k - o_m).
+template <typename A>
+struct Lat16 {
+    A c[4], w[4], inv_den[4];
+    A o0[4], o1[4], o2[4], r0[4], r1[4], r2[4];
+};
+
+template <typename A>
+__device__ __forceinline__ Lat16<A> make_lat16()
+{
+    const double s6 = sqrt(6.0);
+    const double ci = sqrt(3.0 - s6), co = sqrt(3.0 + s6);
+    const double c[4] = {-co, -ci, ci, co};
+    const double wi = (3.0 + s6) / 12.0, wo = (3.0 - s6) / 12.0;
+    Lat16<A> L;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double d = 1.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j != k) d *= c[k] - c[j];
+        L.c[k] = (A)c[k];
+        L.w[k] = (A)((k == 0 || k == 3) ? wo : wi);
+        L.inv_den[k] = (A)(1.0 / d);
+        const double o0 = k == 0 ? c[1] : c[0], o1 = k <= 1 ? c[2] : c[1], o2 = k <= 2 ? c[3] : c[2];
+        L.o0[k] = (A)o0; L.o1[k] = (A)o1; L.o2[k] = (A)o2;
+        L.r0[k] = (A)(1.0 / (c[k] - o0)); L.r1[k] = (A)(1.0 / (c[k] - o1)); L.r2[k] = (A)(1.0 / (c[k] - o2));
+    }
+    return L;
+}
+
+// element k (runtime, 0..3) of a 4-array held in registers
+template <typename A>
+__device__ __forceinline__ A sel4(const A (&v)[4], int k)
+{
+    return k == 0 ? v[0] : (k == 1 ? v[1] : (k == 2 ? v[2] : v[3]));
+}
+
+// Row k of a per-axis transfer map in increment form.  With the source velocities at
+// xi_j = c_j + eps_j in the target's units, G[k][j] = l_k(c_j + eps_j) and the increment
+// D[k][j] = G[k][j] - delta_kj is
+//   j != k: inv_den_k prod_m ((c_j - o_m) + eps_j)   (one factor is eps_j exactly),
+//   j == k: prod_m (1 + eps_k / (c_k - o_m)) - 1, expanded in the three small terms,
+// so that it carries full relative precision however small the gauge change is (FP32
+// arithmetic would otherwise lose the change under the rounding of G ~ I).
+template <typename A>
+struct IncRow {
+    A id, o0, o1, o2, r0, r1, r2;
+    int k;
+    __device__ __forceinline__ A operator()(int j, A cj, A eps) const
+    {
+        if (j == k) {
+            const A t0 = eps * r0, t1 = eps * r1, t2 = eps * r2;
+            return (t0 + t1 + t2) + (t0 * t1 + t0 * t2 + t1 * t2) + t0 * t1 * t2;
+        }
+        return id * (((cj - o0) + eps) * ((cj - o1) + eps) * ((cj - o2) + eps));
+    }
+};
+
+template <typename A>
+__device__ __forceinline__ IncRow<A> inc_row(const Lat16<A> &L, int k)
+{
+    IncRow<A> b;
+    b.id = sel4(L.inv_den, k);
+    b.o0 = sel4(L.o0, k); b.o1 = sel4(L.o1, k); b.o2 = sel4(L.o2, k);
+    b.r0 = sel4(L.r0, k); b.r1 = sel4(L.r1, k); b.r2 = sel4(L.r2, k);
+    b.k = k;
+    return b;
+}
+
+// Cubic Lagrange weights on the nodes 0, 1, 2, 3 at xi (SM "Reconstruction").
+template <typename A>
+__device__ __forceinline__ void cubic_weights(A xi, A a[4])
+{
+    const A x0 = xi, x1 = xi - A(1), x2 = xi - A(2), x3 = xi - A(3);
+    a[0] = -(x1 * x2 * x3) / A(6);
+    a[1] = (x0 * x2 * x3) / A(2);
+    a[2] = -(x0 * x1 * x3) / A(2);
+    a[3] = (x0 * x1 * x2) / A(6);
+}
+
+// Departure stencil along one axis of a node at integer coordinate X for the velocity v:
+// the departure point X - v dt lies at stencil coordinate xi in [1, 2) of the four nodes
+// x0 .. x0 + 3 (x0 = floor(X - v dt) - 1); computed from the displacement so that FP32
+// keeps full precision on large grids.
+template <typename A>
+__device__ __forceinline__ int departure(int X, A v, A dt, A w[4])
+{
+    const A d = -v * dt;
+    const A fl = floor(d);
+    cubic_weights<A>(d - fl + A(1), w);
+    return X + (int)fl - 1;
+}
+
+// Pressure, energy and enthalpy of the run's EoS in FP64.
+__device__ __forceinline__ double q16_p(const DevParams &p, double r, double t)
+{
+    return eos_pressure<double>(p.eos_kind, p.a, p.b, p.R, r, t, p.sp);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: co-moving equilibrium of host-given (rho, u, T) (Eq. geq with the
+// interface energy kappa |grad rho|^2 / 2 in the total energy), D2Q16 weights, T_L = 1.
+template <typename R>
+__global__ void k_q16_init(DevParams p, const double *__restrict__ rho, const double *__restrict__ ux,
+                           const double *__restrict__ uy, const double *__restrict__ T,
+                           R *__restrict__ st, DevStats *stats)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const Lat16<double> L = make_lat16<double>();
+    const int X = (int)(n % p.nx), Y = (int)(n / p.nx);
+    double gx = 0.0, gy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        const int cx = i % 3 - 1, cy = i / 3 - 1;
+        const long long m = (long long)bc_wrap(Y + cy, p.ny, p.bcy) * p.nx + bc_wrap(X + cx, p.nx, p.bcx);
+        const double w = w1d(cx + 1) * w1d(cy + 1);
+        gx += w * cx * rho[m];
+        gy += w * cy * rho[m];
+    }
+    gx *= 3.0;
+    gy *= 3.0;
+    const double r = rho[n], t = T[n];
+    if (!(r > 0.0) || !(p.b * r < 1.0) || !(t > 0.0)) atomicAdd(&stats->bad_init, 1ull);
+    const double pr = q16_p(p, r, t);
+    const double P = pr > p.p_floor ? pr : p.p_floor;
+    const double th = P / r, s = sqrt(th);
+    const double e = p.cv * t - p.a * r;
+    const double lam_e = p.kappa * (gx * gx + gy * gy);
+    const long long N = p.N;
+    for (int i = 0; i < Q16; ++i) {
+        const int jx = i & 3, jy = i >> 2;
+        const double w = L.w[jx] * L.w[jy];
+        const double vx = s * L.c[jx] + ux[n], vy = s * L.c[jy] + uy[n];
+        PLN(st, Q_F + i, n, N) = (R)(r * w);
+        PLN(st, Q_G + i, n, N) = (R)(r * w * (2.0 * e - 2.0 * P / r + vx * vx + vy * vy) + w * lam_e);
+    }
+    PLN(st, Q_TH, n, N) = (R)th;
+    PLN(st, Q_UX, n, N) = (R)ux[n];
+    PLN(st, Q_UY, n, N) = (R)uy[n];
+    PLN(st, Q_RHO, n, N) = (R)r;
+    PLN(st, Q_T, n, N) = (R)t;
+    PLN(st, Q_UHX, n, N) = (R)ux[n];
+    PLN(st, Q_UHY, n, N) = (R)uy[n];
+}
+
+// ---------------------------------------------------------------------------
+// Non-local terms, stage 1 (from the rho, T planes of `src`): with the isotropic D2Q9
+// grid stencils grad = 3 sum W c phi(x + c), lap = 6 sum W (phi(x + c) - phi(x)),
+//   K = -kappa (rho lap rho + |grad rho|^2 / 2) I + kappa grad rho (x) grad rho  (Eq. korteweg)
+//   q = -mu grad h + k grad T, mu = (tau - 1/2) P dt, h = e + p/rho              (Eq. gtilde)
+//   rho E_lambda = kappa |grad rho|^2 / 2.
+template <typename R>
+__global__ void k_q16_nonlocal1(DevParams p, const R *__restrict__ src, double *__restrict__ nl)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const long long N = p.N;
+    const int X = (int)(n % p.nx), Y = (int)(n / p.nx);
+    double gr[2] = {0.0, 0.0}, gh[2] = {0.0, 0.0}, gT[2] = {0.0, 0.0}, lap = 0.0;
+    const double r0 = (double)PLN(src, Q_RHO, n, N), t0 = (double)PLN(src, Q_T, n, N);
+    for (int i = 0; i < 9; ++i) {
+        const int cx = i % 3 - 1, cy = i / 3 - 1;
+        const long long m = (long long)bc_wrap(Y + cy, p.ny, p.bcy) * p.nx + bc_wrap(X + cx, p.nx, p.bcx);
+        const double w = w1d(cx + 1) * w1d(cy + 1);
+        const double r = (double)PLN(src, Q_RHO, m, N), t = (double)PLN(src, Q_T, m, N);
+        const double h = p.cv * t - p.a * r + q16_p(p, r, t) / r;
+        gr[0] += w * cx * r; gr[1] += w * cy * r;
+        gh[0] += w * cx * h; gh[1] += w * cy * h;
+        gT[0] += w * cx * t; gT[1] += w * cy * t;
+        lap += w * (r - r0);
+    }
+    for (int k = 0; k < 2; ++k) { gr[k] *= 3.0; gh[k] *= 3.0; gT[k] *= 3.0; }
+    lap *= 6.0;
+    const double pr = q16_p(p, r0, t0);
+    const double Pg = pr > p.p_floor ? pr : p.p_floor;
+    const double mu = (p.tau - 0.5) * Pg * p.dt;
+    const double kc = p.k_cond >= 0.0 ? p.k_cond : mu * (p.cv + p.R);
+    const double g2 = gr[0] * gr[0] + gr[1] * gr[1];
+    const double iso = -p.kappa * (r0 * lap + 0.5 * g2);
+    PLN(nl, NL_KXX, n, N) = iso + p.kappa * gr[0] * gr[0];
+    PLN(nl, NL_KXY, n, N) = p.kappa * gr[0] * gr[1];
+    PLN(nl, NL_KYY, n, N) = iso + p.kappa * gr[1] * gr[1];
+    PLN(nl, NL_QX, n, N) = -mu * gh[0] + kc * gT[0];
+    PLN(nl, NL_QY, n, N) = -mu * gh[1] + kc * gT[1];
+    PLN(nl, NL_REL, n, N) = 0.5 * p.kappa * g2;
+}
+
+// Stage 2: F = -div K and M_0 = 2 div q with the same gradient stencil.
+__global__ void k_q16_nonlocal2(DevParams p, double *__restrict__ nl)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const long long N = p.N;
+    const int X = (int)(n % p.nx), Y = (int)(n / p.nx);
+    double dxx = 0.0, dxy_x = 0.0, dxy_y = 0.0, dyy = 0.0, dqx = 0.0, dqy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        const int cx = i % 3 - 1, cy = i / 3 - 1;
+        const long long m = (long long)bc_wrap(Y + cy, p.ny, p.bcy) * p.nx + bc_wrap(X + cx, p.nx, p.bcx);
+        const double w = w1d(cx + 1) * w1d(cy + 1);
+        dxx += w * cx * PLN(nl, NL_KXX, m, N);
+        dxy_x += w * cx * PLN(nl, NL_KXY, m, N);
+        dxy_y += w * cy * PLN(nl, NL_KXY, m, N);
+        dyy += w * cy * PLN(nl, NL_KYY, m, N);
+        dqx += w * cx * PLN(nl, NL_QX, m, N);
+        dqy += w * cy * PLN(nl, NL_QY, m, N);
+    }
+    PLN(nl, NL_FX, n, N) = -3.0 * (dxx + dxy_y);
+    PLN(nl, NL_FY, n, N) = -3.0 * (dxy_x + dyy);
+    PLN(nl, NL_M0, n, N) = 6.0 * (dqx + dqy);
+}
+
+// ---------------------------------------------------------------------------
+// Semi-Lagrangian streaming into node (X, Y) in gauge (th, ux, uy) (Eqs. f/g streaming):
+// for direction i the departure point x - v_i dt is reconstructed from the 4 x 4 nodes
+// around it, each node's populations first carried from its own gauge into (th, u) by
+// the transfer map.  Only component i of G f is needed: with the per-axis maps
+// Gx[ix][jx] = l_ix((s' c_jx + u'_x - u_x)/s) (s' = sqrt(theta') and u' the neighbour's
+// gauge) it is sum_jy Gy[iy][jy] sum_jx Gx[ix][jx] f_(4 jy + jx), evaluated as f_i plus
+// increments (G = I + D per axis).
+template <typename R>
+__device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__restrict__ in, int X,
+                           int Y, R th, R ux, R uy, R *ft, R *gt)
+{
+    const long long N = p.N, nself = (long long)Y * p.nx + X;
+    const R s = sqrt_(th), is = R(1) / s, dt = (R)p.dt;
+#pragma unroll 1
+    for (int iy = 0; iy < 4; ++iy) {
+        const IncRow<R> by = inc_row(L, iy);
+        R ay[4];
+        const int y0 = departure<R>(Y, s * sel4(L.c, iy) + uy, dt, ay);
+        long long rows[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rows[m] = (long long)bc_wrap(y0 + m, p.ny, p.bcy) * p.nx;
+#pragma unroll 1
+        for (int ix = 0; ix < 4; ++ix) {
+            const IncRow<R> bx = inc_row(L, ix);
+            R ax[4];
+            const int x0 = departure<R>(X, s * sel4(L.c, ix) + ux, dt, ax);
+            int cols[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) cols[k] = bc_wrap(x0 + k, p.nx, p.bcx);
+            // interpolated as ref + sum w (v - ref) with ref = the node's own f_i, g_i: the
+            // weights' rounded sum then only scales the small differences
+            const int i = 4 * iy + ix;
+            const R refF = PLN(in, Q_F + i, nself, N), refG = PLN(in, Q_G + i, nself, N);
+            R sf = R(0), sg = R(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const long long nd = rows[m] + cols[k];
+                    const R ths = PLN(in, Q_TH, nd, N);
+                    const R ds = (ths - th) / (sqrt_(ths) + s) * is;   // (s' - s)/s
+                    const R ex = (PLN(in, Q_UX, nd, N) - ux) * is, ey = (PLN(in, Q_UY, nd, N) - uy) * is;
+                    R gx[4], gy[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        gx[j] = bx(j, L.c[j], ds * L.c[j] + ex);
+                        gy[j] = by(j, L.c[j], ds * L.c[j] + ey);
+                    }
+                    // per row jy: base = f_(jy, ix), inc = sum_jx Dx[ix][jx] f_(jy, jx)
+                    R bf[4], bg[4], xf[4], xg[4];
+#pragma unroll
+                    for (int jy = 0; jy < 4; ++jy) {
+                        R fr[4], gr[4];
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) {
+                            fr[jx] = PLN(in, Q_F + 4 * jy + jx, nd, N);
+                            gr[jx] = PLN(in, Q_G + 4 * jy + jx, nd, N);
+                        }
+                        R df = R(0), dg = R(0);
+#pragma unroll
+                        for (int jx = 0; jx < 4; ++jx) { df += gx[jx] * fr[jx]; dg += gx[jx] * gr[jx]; }
+                        bf[jy] = sel4(fr, ix); bg[jy] = sel4(gr, ix);
+                        xf[jy] = df; xg[jy] = dg;
+                    }
+                    R df = R(0), dg = R(0);
+#pragma unroll
+                    for (int jy = 0; jy < 4; ++jy) {
+                        df += gy[jy] * (bf[jy] + xf[jy]);
+                        dg += gy[jy] * (bg[jy] + xg[jy]);
+                    }
+                    // [G f]_i - ref = (f_i - ref) + x-increment of row iy + y-increment
+                    const R wgt = ax[k] * ay[m];
+                    sf += wgt * (((sel4(bf, iy) - refF) + sel4(xf, iy)) + df);
+                    sg += wgt * (((sel4(bg, iy) - refG) + sel4(xg, iy)) + dg);
+                }
+            }
+            sf += refF;
+            sg += refG;
+            ft[4 * iy + ix] = sf;
+            gt[4 * iy + ix] = sg;
+        }
+    }
+}
+
+// Macroscopic fields of streamed populations in gauge (th, ux, uy) (moments Eq.), FP64:
+// out = rho, u_x, u_y, uhat_x, uhat_y, E, e, T, p, P = max(p, p_floor), theta* = P/rho.
+template <typename R>
+__device__ __forceinline__ void q16_macro(const DevParams &p, const Lat16<double> &L, R th, R ux,
+                                          R uy, const R *ft, const R *gt, double Fx, double Fy,
+                                          double rEl, double out[11])
+{
+    const double s = sqrt((double)th);
+    double rho = 0.0, jx = 0.0, jy = 0.0, sg = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q16; ++i) {
+        const double vx = s * L.c[i & 3] + (double)ux, vy = s * L.c[i >> 2] + (double)uy;
+        const double f = (double)ft[i];
+        rho += f;
+        jx += f * vx;
+        jy += f * vy;
+        sg += (double)gt[i];
+    }
+    const double u_x = jx / rho, u_y = jy / rho;
+    const double uhx = u_x + Fx * p.dt / (2.0 * rho), uhy = u_y + Fy * p.dt / (2.0 * rho);
+    const double E = sg / (2.0 * rho);
+    const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEl / rho;
+    const double T = p.isothermal ? p.T_iso : (e + p.a * rho) / p.cv;
+    const double pr = q16_p(p, rho, T);
+    const double P = pr > p.p_floor ? pr : p.p_floor;
+    out[0] = rho; out[1] = u_x; out[2] = u_y; out[3] = uhx; out[4] = uhy;
+    out[5] = E; out[6] = e; out[7] = T; out[8] = pr; out[9] = P; out[10] = P / rho;
+}
+
+// Per-axis transfer map from gauge (s_src, u_src) into (s_dst, u_dst) in increment
+// form: D[i][j] = l_i(c_j + eps_j) - delta_ij with eps_j = ((s_src - s_dst) c_j + du)/s_dst;
+// ds = (s_src - s_dst)/s_dst and du / s_dst are passed in.
+template <typename A>
+__device__ __forceinline__ void axis_inc(const Lat16<A> &L, A ds, A du, A D[4][4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const IncRow<A> b = inc_row(L, i);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) D[i][j] = b(j, L.c[j], ds * L.c[j] + du);
+    }
+}
+
+// Increment of (I + Dy) (x) (I + Dx) applied to h: out_(4 iy + ix) = [G h]_i - h_i.
+template <typename A>
+__device__ __forceinline__ void apply_inc(const A Dx[4][4], const A Dy[4][4], const A h[16], A out[16])
+{
+    A t[16];
+#pragma unroll
+    for (int jy = 0; jy < 4; ++jy)
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix) {
+            A a = A(0);
+#pragma unroll
+            for (int jx = 0; jx < 4; ++jx) a += Dx[ix][jx] * h[4 * jy + jx];
+            t[4 * jy + ix] = a;
+        }
+#pragma unroll
+    for (int iy = 0; iy < 4; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix) {
+            A a = A(0);
+#pragma unroll
+            for (int jy = 0; jy < 4; ++jy) a += Dy[iy][jy] * (h[4 * jy + ix] + t[4 * jy + ix]);
+            out[4 * iy + ix] = t[4 * iy + ix] + a;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// The node step.  in: state at t - dt; nl: non-local terms (F, rho E_lambda, M_0) of the
+// state they are taken from; out: state at t.  Frame search: predictor = the node's
+// stored gauge; corrector = re-stream with (theta*, u) of the streamed moments until the
+// relative change is <= tol or after max_iter streams.  Collision: equilibria built in
+// the co-moving frame lambda* = (theta*, u) and carried into the streaming gauge (Eqs.
+// f collision with S_i, g collision with gtilde and phi, new geq).
+template <typename R>
+__global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restrict__ in,
+                                                  const double *__restrict__ nl, R *__restrict__ out,
+                                                  DevStats *stats)
+{
+    const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y;
+    const bool valid = X < p.nx && Y < p.ny;
+    const long long N = p.N, n = valid ? (long long)Y * p.nx + X : 0;
+    unsigned long long its = 0, nonconv = 0, clamped = 0, nonfinite = 0;
+    if (valid) {
+        const Lat16<R> L = make_lat16<R>();
+        const Lat16<double> Ld = make_lat16<double>();
+        const double Fx = PLN(nl, NL_FX, n, N), Fy = PLN(nl, NL_FY, n, N);
+        const double rEl = PLN(nl, NL_REL, n, N), M0 = PLN(nl, NL_M0, n, N);
+        R th = PLN(in, Q_TH, n, N), ux = PLN(in, Q_UX, n, N), uy = PLN(in, Q_UY, n, N);
+        R ft[Q16], gt[Q16];
+        double mac[11];
+        int it = 0;
+        bool conv = false;
+        for (;;) {
+            ++it;
+            q16_stream<R>(p, L, in, X, Y, th, ux, uy, ft, gt);
+            q16_macro<R>(p, Ld, th, ux, uy, ft, gt, Fx, Fy, rEl, mac);
+            const double t0 = (double)th, st0 = sqrt(t0);
+            const double r0 = fabs(mac[10] - t0) / t0;
+            const double r1 = fabs(mac[1] - (double)ux) / st0, r2 = fabs(mac[2] - (double)uy) / st0;
+            const double r = fmax(fmax(r0, r1), r2);
+            if (r <= p.tol) { conv = true; break; }
+            if (it >= p.max_iter || !(r == r)) break;
+            th = (R)mac[10]; ux = (R)mac[1]; uy = (R)mac[2];
+        }
+        its = (unsigned long long)it;
+        nonconv = conv ? 0ull : 1ull;
+        clamped = mac[8] < p.p_floor ? 1ull : 0ull;
+
+        // ---- collision in type R, equilibria as increments over their co-moving form
+        const TypedParams<R> &q = typed<R>(p);
+        const R rho = (R)mac[0], u_x = (R)mac[1], u_y = (R)mac[2], uhx = (R)mac[3], uhy = (R)mac[4];
+        const R E = (R)mac[5], Pg = (R)mac[9], ths = (R)mac[10];
+        const R fx = (R)Fx, fy = (R)Fy, m0 = (R)M0, dt = q.dt, om = q.omega;
+        const double sd = sqrt((double)th), ssd = sqrt(mac[10]);
+        const R is = (R)(1.0 / sd), sst = (R)ssd;
+        const R ds = (R)((mac[10] - (double)th) / (ssd + sd) / sd);   // (s* - s)/s
+        const R dux = (R)(mac[1] - (double)ux) * is, duy = (R)(mac[2] - (double)uy) * is;
+        const R shx = fx * dt / rho * is, shy = fy * dt / rho * is;   // du of the force
+        R Dx[4][4], Dy[4][4], Ex[4][4], Ey[4][4];
+        axis_inc<R>(L, ds, dux, Dx);                                  // lambda* -> lambda
+        axis_inc<R>(L, ds, duy, Dy);
+        axis_inc<R>(L, ds, dux + shx, Ex);                            // lambda* + du -> lambda
+        axis_inc<R>(L, ds, duy + shy, Ey);
+        R h[Q16], eqi[Q16], shi[Q16];
+#pragma unroll
+        for (int i = 0; i < Q16; ++i) h[i] = rho * (L.w[i & 3] * L.w[i >> 2]);
+        apply_inc<R>(Dx, Dy, h, eqi);
+        apply_inc<R>(Ex, Ey, h, shi);
+        // Collision keeps the mass: sum_i f_out = rho exactly; the stored values are made to
+        // carry it (their FP64 sum is compared with rho and the defect, which the rounded
+        // weights and products would otherwise add every step in the same direction, is
+        // spread by W_i).  Zero in exact arithmetic.
+        R fo[Q16];
+        double sf = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q16; ++i) {
+            fo[i] = ft[i] + om * ((h[i] - ft[i]) + eqi[i]) + (shi[i] - eqi[i]);
+            sf += (double)fo[i];
+        }
+        const R fdef = (R)(mac[0] - sf);
+#pragma unroll
+        for (int i = 0; i < Q16; ++i) PLN(out, Q_F + i, n, N) = fo[i] + fdef * (L.w[i & 3] * L.w[i >> 2]);
+
+        const R H = E + Pg / rho;
+        const R Ixx = R(2) * uhx * fx + dt * fx * fx * E / (R(2) * Pg);
+        const R Ixy = uhx * fy + fx * uhy + dt * fx * fy * E / (R(2) * Pg);
+        const R Iyy = R(2) * uhy * fy + dt * fy * fy * E / (R(2) * Pg);
+        const R Mx = (dt * rho / Pg) * (fx * H - (Ixx * u_x + Ixy * u_y));
+        const R My = (dt * rho / Pg) * (fy * H - (Ixy * u_x + Iyy * u_y));
+        const R Nxx = rho + (dt * rho / (R(2) * Pg)) * Ixx;
+        const R Nxy = (dt * rho / (R(2) * Pg)) * Ixy;
+        const R Nyy = rho + (dt * rho / (R(2) * Pg)) * Iyy;
+        const R phi = R(2) * (uhx * fx + uhy * fy);
+#pragma unroll
+        for (int i = 0; i < Q16; ++i) {
+            const R cx = L.c[i & 3], cy = L.c[i >> 2], W = L.w[i & 3] * L.w[i >> 2];
+            const R vx = sst * cx + u_x, vy = sst * cy + u_y;
+            const R Axx = vx * vx - Pg / rho - u_x * u_x;
+            const R Axy = vx * vy - u_x * u_y;
+            const R Ayy = vy * vy - Pg / rho - u_y * u_y;
+            const R geq = W * (R(2) * rho * E + Mx * (vx - u_x) + My * (vy - u_y) + Nxx * Axx +
+                               R(2) * Nxy * Axy + Nyy * Ayy);
+            const R uc = u_x * cx + u_y * cy;
+            const R gc = m0 * W * (R(1) + rho * uc * uc / (R(2) * Pg) - rho * (vx * vx + vy * vy) / (R(2) * Pg) + R(1));
+            h[i] = om * geq + dt * (gc + W * phi);
+        }
+        R ginc[Q16];
+        apply_inc<R>(Dx, Dy, h, ginc);
+        // energy: sum_i g_out = sum_i g~ + dt (M_0 + 2 uhat . F) exactly (the heat-flux
+        // correction sums to M_0, the force work to 2 uhat . F); the same defect spreading
+        R go[Q16];
+        double sg = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q16; ++i) {
+            go[i] = gt[i] - om * gt[i] + (h[i] + ginc[i]);
+            sg += (double)go[i];
+        }
+        const double g_tot = 2.0 * mac[0] * mac[5] + p.dt * (M0 + 2.0 * (mac[3] * Fx + mac[4] * Fy));
+        const R gdef = (R)(g_tot - sg);
+#pragma unroll
+        for (int i = 0; i < Q16; ++i) PLN(out, Q_G + i, n, N) = go[i] + gdef * (L.w[i & 3] * L.w[i >> 2]);
+        PLN(out, Q_TH, n, N) = th;
+        PLN(out, Q_UX, n, N) = ux;
+        PLN(out, Q_UY, n, N) = uy;
+        PLN(out, Q_RHO, n, N) = rho;
+        PLN(out, Q_T, n, N) = (R)mac[7];
+        PLN(out, Q_UHX, n, N) = uhx;
+        PLN(out, Q_UHY, n, N) = uhy;
+        const double chk = mac[0] + mac[7] + (double)ginc[0] + (double)eqi[0];
+        nonfinite = (chk - chk == 0.0) ? 0ull : 1ull;
+    }
+    warp_add(&stats->streams, its);
+    warp_add(&stats->nonconv, nonconv);
+    warp_add(&stats->clamped, clamped);
+    warp_add(&stats->nonfinite, nonfinite);
+    // largest streaming-pass count of any node
+    unsigned long long mx = its;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    if ((threadIdx.x + threadIdx.y * blockDim.x) % 32 == 0 && mx) atomicMax(&stats->max_streams, mx);
+}
+
+// Output fields: rho, uhat, T, p in FP64.
+template <typename R>
+__global__ void k_q16_moments(DevParams p, const R *__restrict__ st, double *rho, double *ux,
+                              double *uy, double *T, double *pr)
+{
+    const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= p.N) return;
+    const long long N = p.N;
+    const double r = (double)PLN(st, Q_RHO, n, N), t = (double)PLN(st, Q_T, n, N);
+    if (rho) rho[n] = r;
+    if (ux) ux[n] = (double)PLN(st, Q_UHX, n, N);
+    if (uy) uy[n] = (double)PLN(st, Q_UHY, n, N);
+    if (T) T[n] = t;
+    if (pr) pr[n] = q16_p(p, r, t);
+}
+
+// Conservation sums, stage 1: per-block compensated partials of
+// {rho, rho uhat_x, rho uhat_y, sum_i g_i / 2} (stage 2 is k_conserve2).
+template <typename R>
+__global__ void k_q16_conserve1(DevParams p, const R *__restrict__ st, double *part)
+{
+    const long long N = p.N;
+    double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const double r = (double)PLN(st, Q_RHO, n, N);
+        double eg = 0.0;
+        for (int i = 0; i < Q16; ++i) eg += (double)PLN(st, Q_G + i, n, N);
+        const double v[4] = {r, r * (double)PLN(st, Q_UHX, n, N), r * (double)PLN(st, Q_UHY, n, N), 0.5 * eg};
+        for (int k = 0; k < 4; ++k) pair_add(s[k], c[k], v[k], 0.0);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 4; ++k) {
+            const double s2 = __shfl_xor_sync(0xffffffffu, s[k], o);
+            const double c2 = __shfl_xor_sync(0xffffffffu, c[k], o);
+            pair_add(s[k], c[k], s2, c2);
+        }
+    __shared__ double sh[32][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 4; ++k) { sh[warp][2 * k] = s[k]; sh[warp][2 * k + 1] = c[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < 4; ++k) {
+            double ss = sh[0][2 * k], cc = sh[0][2 * k + 1];
+            for (int w = 1; w < nw; ++w) pair_add(ss, cc, sh[w][2 * k], sh[w][2 * k + 1]);
+            part[blockIdx.x * 8 + 2 * k] = ss;
+            part[blockIdx.x * 8 + 2 * k + 1] = cc;
+        }
+    }
+}
+
+}  // namespace pond

@@ -16,7 +16,8 @@ import numpy as np
 from . import build_lib
 
 POND_PERIODIC, POND_ZEROGRAD = 0, 1
-POND_D2Q9 = 0
+POND_D2Q9, POND_D2Q16 = 0, 1
+LATTICES = {"d2q9": POND_D2Q9, "d2q16": POND_D2Q16}
 POND_VDW, POND_IDEAL, POND_DIETERICI, POND_SIMPLIFIED = 0, 1, 2, 3
 POND_FP64, POND_MIXED = 0, 1
 NPLANES = 25
@@ -151,7 +152,7 @@ class Simulation:
                  stream=None, torch_alloc: bool = True, ideal: bool = False,
                  lanes_per_node: int = 0, tile_x: int = 0, eos: str = "vdw",
                  isothermal: bool = False, T_iso: float = 0.0, nonlocal_: str = "lagged",
-                 eos_params: tuple = ()):
+                 eos_params: tuple = (), lattice: str = "d2q9"):
         torch = _torch()
         self._lib = load()
         self.nx, self.ny = int(nx), int(ny)
@@ -184,7 +185,11 @@ class Simulation:
         else:
             self._cb_alloc, self._cb_free = _ALLOC(), _FREE()
         grid = Grid(self.nx, self.ny, bc_x, bc_y)
-        lat = Lattice(POND_D2Q9)
+        if lattice not in LATTICES:
+            raise ValueError("lattice must be 'd2q9' or 'd2q16'")
+        lat = Lattice(LATTICES[lattice])
+        self.lattice = lattice
+        self.nplanes = 2 * (9 if lattice == "d2q9" else 16) + 7
         if eos not in ("vdw", "dieterici", "simplified"):
             raise ValueError("eos must be 'vdw', 'dieterici' or 'simplified'")
         kind = {"dieterici": POND_DIETERICI, "simplified": POND_SIMPLIFIED}.get(
@@ -198,7 +203,7 @@ class Simulation:
                            kappa=kappa, tau=tau, precision=precision, dt=dt, tol=tol,
                            max_iter=max_iter, k_cond=k_cond, p_floor=p_floor,
                            lanes_per_node=lanes_per_node, tile_x=tile_x, eos=eos,
-                           isothermal=isothermal, T_iso=T_iso, nonlocal_=nonlocal_)
+                           isothermal=isothermal, T_iso=T_iso, nonlocal_=nonlocal_, lattice=lattice)
         ctx = C.c_void_p()
         with torch.cuda.device(self._device):
             st = self._lib.pond_create(C.byref(grid), C.byref(lat), C.byref(eos_c), kappa, tau,
@@ -252,12 +257,12 @@ class Simulation:
         return out
 
     def get_state(self) -> np.ndarray:
-        out = np.empty((NPLANES, self.ny, self.nx))
+        out = np.empty((self.nplanes, self.ny, self.nx))
         self._check(self._lib.pond_get_state(self._ctx, _dptr(out)))
         return out
 
     def set_state(self, state):
-        s = np.ascontiguousarray(np.asarray(state, dtype=np.float64).reshape(NPLANES, self.ny, self.nx))
+        s = np.ascontiguousarray(np.asarray(state, dtype=np.float64).reshape(self.nplanes, self.ny, self.nx))
         self._check(self._lib.pond_set_state(self._ctx, _dptr(s)))
 
     def stats(self, reset: bool = False) -> dict:

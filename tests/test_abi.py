@@ -69,6 +69,9 @@ def test_invalid_parameters_are_rejected_on_the_host(lib):
                 pond.Eos(pond.POND_SIMPLIFIED, 0, 0, 1, 1 / 3, 1, 0.1, 1e-3, 5.0, 0.5, 0.0)):  # p0 = 0
         assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(bad), 0.0, 1.0,
                              ctypes.byref(opts), ctypes.byref(out)) == 1
+    lat_bad = pond.Lattice(2)                                             # unknown lattice
+    assert L.pond_create(ctypes.byref(g), ctypes.byref(lat_bad), ctypes.byref(eos), 0.0, 1.0,
+                         ctypes.byref(opts), ctypes.byref(out)) == 1
     assert not out.value
     L.pond_destroy(None)
 
