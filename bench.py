@@ -136,6 +136,23 @@ FLOPS_STREAM_EXTRA = 60
 FLOPS_NONLOCAL = 200
 FLOPS_COLLIDE = 1300
 
+# The same count for the D2Q16 step (k_q16_step), per node update: per stencil pair (16
+# directions x 16 stencil nodes per stream): gauge offsets (9), the eight transfer-map
+# increments of the pair's row per axis (16 for their offsets, 82 for the entries), the
+# x-increments of the four source rows for f and g (64), the y-increment (24), weight and
+# accumulation (11) => 206; per direction: departure points and cubic weights (40); per
+# stream: moments and residual (FP64, 130); per node update: non-local terms (200) and the
+# collision (2300: four per-axis increment maps ~700, three tensor-product applications
+# ~900, forced g equilibrium ~640, mass and energy defect sums ~70).
+FLOPS_Q16_PAIR = 206
+FLOPS_Q16_DIR = 40
+FLOPS_Q16_STREAM_EXTRA = 130
+FLOPS_Q16_COLLIDE = 2300
+
+
+def flops_q16(its: float) -> float:
+    return its * (16 * (FLOPS_Q16_DIR + 16 * FLOPS_Q16_PAIR) + FLOPS_Q16_STREAM_EXTRA) + FLOPS_NONLOCAL + FLOPS_Q16_COLLIDE
+
 
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the bench workload; they hold only for the kernel source they were
@@ -283,7 +300,7 @@ def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
     return summ
 
 
-def other_configs(pond, torch, stream) -> dict:
+def other_configs(pond, torch, stream, sm_mhz: float = 2070.0) -> dict:
     """MLUPS of the other full-size workloads (mixed form, default launch shape, a few
     back-to-back steps after warm-up; the larger ones exceed L2 by themselves)."""
     from paper_2002_09217_gb300 import inputs
@@ -304,6 +321,31 @@ def other_configs(pond, torch, stream) -> dict:
             sim.close()
             out["%s/%s" % (name, prec)] = {"mlups": w.nodes / ms / 1e3, "ms_per_step": ms,
                                            "streams_per_node": st["streams"] / max(1, st["node_updates"])}
+    # the D2Q16 lattice on the 512 x 512 droplet (three launches per step: the two
+    # non-local kernels and the node step); achieved FLOP/s of the step from the formula's
+    # count above against the ALU peak of its precision
+    w = inputs.config("droplet512x512")
+    for prec, steps in (("mixed", 20), ("fp64", 3)):
+        sim = pond.from_workload(w, precision=prec, stream=stream, lattice="d2q16")
+        sim.init_fields(*w.fields())
+        sim.step(3)
+        sim.stats(reset=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(steps)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b) / steps
+        st = sim.stats()
+        sim.close()
+        its = st["streams"] / max(1, st["node_updates"])
+        achieved = w.nodes * flops_q16(its) / (ms * 1e-3) / 1e12
+        peak = alu_peak_tflops(prec, sm_mhz)
+        out["%s/d2q16/%s" % (w.name, prec)] = {
+            "mlups": w.nodes / ms / 1e3, "ms_per_step": ms, "streams_per_node": its,
+            "roofline": {"bound": "alu", "kernel": "k_q16_step (+ two non-local kernels)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "flops_per_update": flops_q16(its)}}
     # the two-pass step (current-time non-local terms) on the slab: two launches per step
     w = inputs.config("slab128x4")
     sim = pond.from_workload(w, precision="mixed", stream=stream, nonlocal_="current")
@@ -473,7 +515,7 @@ def main():
                         "roofline": roofline(w, "fp64", its64, kms64, pk)}
 
     if rank == 0 and not args.no_extras:
-        line["other_configs"] = other_configs(pond, torch, stream)
+        line["other_configs"] = other_configs(pond, torch, stream, pk["sm_max_mhz"])
 
     if not args.no_serving:
         serv = serving_sample(torch, rank, ws)

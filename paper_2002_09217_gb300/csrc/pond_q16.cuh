@@ -82,15 +82,20 @@ __device__ __forceinline__ A sel4(const A (&v)[4], int k)
 // arithmetic would otherwise lose the change under the rounding of G ~ I).
 template <typename A>
 struct IncRow {
-    A id, o0, o1, o2, r0, r1, r2;
+    A id, r0, r1, r2;
+    A d[4][3];   // c_j - o_m (exactly 0 where o_m = c_j)
     int k;
-    __device__ __forceinline__ A operator()(int j, A cj, A eps) const
+    // the whole row at the offsets eps[0..3]
+    __device__ __forceinline__ void row(const A (&eps)[4], A (&out)[4]) const
     {
-        if (j == k) {
-            const A t0 = eps * r0, t1 = eps * r1, t2 = eps * r2;
-            return (t0 + t1 + t2) + (t0 * t1 + t0 * t2 + t1 * t2) + t0 * t1 * t2;
+        const A ek = sel4(eps, k);
+        const A t0 = ek * r0, t1 = ek * r1, t2 = ek * r2;
+        const A diag = (t0 + t1 + t2) + (t0 * t1 + t0 * t2 + t1 * t2) + t0 * t1 * t2;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const A off = id * ((d[j][0] + eps[j]) * (d[j][1] + eps[j]) * (d[j][2] + eps[j]));
+            out[j] = j == k ? diag : off;
         }
-        return id * (((cj - o0) + eps) * ((cj - o1) + eps) * ((cj - o2) + eps));
     }
 };
 
@@ -99,8 +104,14 @@ __device__ __forceinline__ IncRow<A> inc_row(const Lat16<A> &L, int k)
 {
     IncRow<A> b;
     b.id = sel4(L.inv_den, k);
-    b.o0 = sel4(L.o0, k); b.o1 = sel4(L.o1, k); b.o2 = sel4(L.o2, k);
+    const A o0 = sel4(L.o0, k), o1 = sel4(L.o1, k), o2 = sel4(L.o2, k);
     b.r0 = sel4(L.r0, k); b.r1 = sel4(L.r1, k); b.r2 = sel4(L.r2, k);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        b.d[j][0] = L.c[j] - o0;
+        b.d[j][1] = L.c[j] - o1;
+        b.d[j][2] = L.c[j] - o2;
+    }
     b.k = k;
     return b;
 }
@@ -282,47 +293,48 @@ __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__res
             const int i = 4 * iy + ix;
             const R refF = PLN(in, Q_F + i, nself, N), refG = PLN(in, Q_G + i, nself, N);
             R sf = R(0), sg = R(0);
+            // the 16 stencil nodes as a rolled loop (its body stays in the instruction cache)
+#pragma unroll 1
+            for (int mk = 0; mk < 16; ++mk) {
+                const int m = mk >> 2, k = mk & 3;
+                const long long nd = sel4(rows, m) + sel4(cols, k);
+                const R ths = PLN(in, Q_TH, nd, N);
+                const R ds = (ths - th) / (sqrt_(ths) + s) * is;   // (s' - s)/s
+                const R ex = (PLN(in, Q_UX, nd, N) - ux) * is, ey = (PLN(in, Q_UY, nd, N) - uy) * is;
+                R epx[4], epy[4], gx[4], gy[4];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
+                for (int j = 0; j < 4; ++j) {
+                    epx[j] = ds * L.c[j] + ex;
+                    epy[j] = ds * L.c[j] + ey;
+                }
+                bx.row(epx, gx);
+                by.row(epy, gy);
+                // per row jy: base = f_(jy, ix), inc = sum_jx Dx[ix][jx] f_(jy, jx)
+                R bf[4], bg[4], xf[4], xg[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const long long nd = rows[m] + cols[k];
-                    const R ths = PLN(in, Q_TH, nd, N);
-                    const R ds = (ths - th) / (sqrt_(ths) + s) * is;   // (s' - s)/s
-                    const R ex = (PLN(in, Q_UX, nd, N) - ux) * is, ey = (PLN(in, Q_UY, nd, N) - uy) * is;
-                    R gx[4], gy[4];
+                for (int jy = 0; jy < 4; ++jy) {
+                    R fr[4], gr[4];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        gx[j] = bx(j, L.c[j], ds * L.c[j] + ex);
-                        gy[j] = by(j, L.c[j], ds * L.c[j] + ey);
-                    }
-                    // per row jy: base = f_(jy, ix), inc = sum_jx Dx[ix][jx] f_(jy, jx)
-                    R bf[4], bg[4], xf[4], xg[4];
-#pragma unroll
-                    for (int jy = 0; jy < 4; ++jy) {
-                        R fr[4], gr[4];
-#pragma unroll
-                        for (int jx = 0; jx < 4; ++jx) {
-                            fr[jx] = PLN(in, Q_F + 4 * jy + jx, nd, N);
-                            gr[jx] = PLN(in, Q_G + 4 * jy + jx, nd, N);
-                        }
-                        R df = R(0), dg = R(0);
-#pragma unroll
-                        for (int jx = 0; jx < 4; ++jx) { df += gx[jx] * fr[jx]; dg += gx[jx] * gr[jx]; }
-                        bf[jy] = sel4(fr, ix); bg[jy] = sel4(gr, ix);
-                        xf[jy] = df; xg[jy] = dg;
+                    for (int jx = 0; jx < 4; ++jx) {
+                        fr[jx] = PLN(in, Q_F + 4 * jy + jx, nd, N);
+                        gr[jx] = PLN(in, Q_G + 4 * jy + jx, nd, N);
                     }
                     R df = R(0), dg = R(0);
 #pragma unroll
-                    for (int jy = 0; jy < 4; ++jy) {
-                        df += gy[jy] * (bf[jy] + xf[jy]);
-                        dg += gy[jy] * (bg[jy] + xg[jy]);
-                    }
-                    // [G f]_i - ref = (f_i - ref) + x-increment of row iy + y-increment
-                    const R wgt = ax[k] * ay[m];
-                    sf += wgt * (((sel4(bf, iy) - refF) + sel4(xf, iy)) + df);
-                    sg += wgt * (((sel4(bg, iy) - refG) + sel4(xg, iy)) + dg);
+                    for (int jx = 0; jx < 4; ++jx) { df += gx[jx] * fr[jx]; dg += gx[jx] * gr[jx]; }
+                    bf[jy] = sel4(fr, ix); bg[jy] = sel4(gr, ix);
+                    xf[jy] = df; xg[jy] = dg;
                 }
+                R df = R(0), dg = R(0);
+#pragma unroll
+                for (int jy = 0; jy < 4; ++jy) {
+                    df += gy[jy] * (bf[jy] + xf[jy]);
+                    dg += gy[jy] * (bg[jy] + xg[jy]);
+                }
+                // [G f]_i - ref = (f_i - ref) + x-increment of row iy + y-increment
+                const R wgt = sel4(ax, k) * sel4(ay, m);
+                sf += wgt * (((sel4(bf, iy) - refF) + sel4(xf, iy)) + df);
+                sg += wgt * (((sel4(bg, iy) - refG) + sel4(xg, iy)) + dg);
             }
             sf += refF;
             sg += refG;
@@ -367,12 +379,11 @@ __device__ __forceinline__ void q16_macro(const DevParams &p, const Lat16<double
 template <typename A>
 __device__ __forceinline__ void axis_inc(const Lat16<A> &L, A ds, A du, A D[4][4])
 {
+    A eps[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const IncRow<A> b = inc_row(L, i);
+    for (int j = 0; j < 4; ++j) eps[j] = ds * L.c[j] + du;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) D[i][j] = b(j, L.c[j], ds * L.c[j] + du);
-    }
+    for (int i = 0; i < 4; ++i) inc_row(L, i).row(eps, D[i]);
 }
 
 // Increment of (I + Dy) (x) (I + Dx) applied to h: out_(4 iy + ix) = [G h]_i - h_i.
