@@ -115,9 +115,15 @@ def workload(name: str):
     return inputs.config(name)
 
 
-def bytes_per_update(precision: str) -> int:
+def bytes_per_update(precision: str, lattice: str = "d2q9") -> int:
+    e = 4 if precision == "mixed" else 8
+    if lattice == "d2q16":
+        # record read once (f, g, gauge, rho, T: 37 values) + written once (39 values), and
+        # the nine FP64 non-local planes written and read once (rho, T of each node are
+        # read again by the non-local kernels: 2 values)
+        return (37 + 39 + 2) * e + 2 * 9 * 8
     # state read once (f, g, gauge, rho, T: 23 values) + written once (25 values)
-    return 48 * (4 if precision == "mixed" else 8)
+    return 48 * e
 
 
 # Algorithmic FLOPs of the step kernel's formula, per node update (an FMA counts 2):
@@ -180,13 +186,13 @@ def flops_per_stream() -> int:
     return 9 * (FLOPS_DIR + 16 * FLOPS_PAIR) + FLOPS_STREAM_EXTRA
 
 
-def oracle_mlups(w, steps: int) -> dict:
+def oracle_mlups(w, steps: int, lattice: str = "d2q9") -> dict:
     import oracle
     P = oracle.Params(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R,
                       delta=w.delta, kappa=w.kappa, tau=w.tau, dt=w.dt, k_cond=w.k_cond,
                       p_floor=w.p_floor, tol=1e-12, max_iter=20, eos=w.eos, isothermal=w.isothermal,
                       eos_params=tuple(w.eos_params),
-                      T_iso=float(w.T.flat[0]) if w.isothermal else 0.0)
+                      T_iso=float(w.T.flat[0]) if w.isothermal else 0.0, lattice=lattice)
     st = oracle.init_state(P, *w.fields())
     st = oracle.step(P, st, 1)          # warm-up (page-in, thread pool)
     t0 = time.perf_counter()
@@ -194,8 +200,8 @@ def oracle_mlups(w, steps: int) -> dict:
     dt = time.perf_counter() - t0
     return {"value": w.nodes * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": "%d time steps of the full %dx%d grid (FP64 oracle, OpenMP over nodes)"
-                      % (steps, w.nx, w.ny), "state": st, "params": P}
+            "sample": "%d time steps of the full %dx%d grid (FP64 oracle, %s, OpenMP over nodes)"
+                      % (steps, w.nx, w.ny, lattice.upper()), "state": st, "params": P}
 
 
 def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws):
@@ -233,12 +239,17 @@ def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws)
     return ms, st, kms
 
 
-def roofline(w, precision, its, kernel_ms, pk):
-    fl = its * flops_per_stream() + FLOPS_NONLOCAL + FLOPS_COLLIDE
+def roofline(w, precision, its, kernel_ms, pk, lattice="d2q9"):
+    if lattice == "d2q16":
+        fl = flops_q16(its)
+        kernel, traffic = "k_q16_step (+ two non-local kernels, timed together)", None
+    else:
+        fl = its * flops_per_stream() + FLOPS_NONLOCAL + FLOPS_COLLIDE
+        kernel, traffic = "k_pond_step", ncu_traffic(w, precision)
     achieved = w.nodes * fl / (kernel_ms * 1e-3) / 1e12
     peak = alu_peak_tflops(precision, pk["sm_max_mhz"])
-    out = {"bound": "alu", "kernel": "k_pond_step", "achieved": achieved, "peak": peak,
-           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(w, precision),
+    out = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
            "peak_src": "%s: 152 SM x 128 lanes x 2 flop x %.0f MHz%s" % (
                "FP32" if precision == "mixed" else "FP64", pk["sm_max_mhz"],
                "" if precision == "mixed" else " / 64"),
@@ -414,6 +425,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="shocktube2048x4")
+    ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d2q16"],
+                    help="velocity set (D2Q16: the three-launch plane step, no autotuning)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
@@ -435,7 +448,7 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             steps = max(1, min(args.steps, 20))
-            res = oracle_mlups(w, steps)
+            res = oracle_mlups(w, steps, args.lattice)
             line = {"impl": "reference", "metric": "MLUPS", "value": res["value"], "unit": "MLUPS",
                     "n_gpus": ws, "steps": steps, "warmup": 1, "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -464,6 +477,8 @@ def main():
                 pass
 
     def shape_for(prec):
+        if args.lattice != "d2q9":
+            return {"lattice": args.lattice}
         if args.no_autotune:
             return {}
         best = autotune.tune(w, prec, stream=stream)
@@ -491,14 +506,14 @@ def main():
         # pairs of FP32); the FP64 form in FP64
         "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt, "precision": args.precision,
-                   "launch_shape": shape or "default",
+                   "launch_shape": shape or "default", "lattice": args.lattice,
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "frame_search_streams_per_node": its,
-        "gpu_launches": args.steps,
-        "roofline": roofline(w, args.precision, its, kms, pk),
-        "hbm": {"bytes_per_update": bytes_per_update(args.precision),
-                "achieved_gbs": value / ws * 1e6 * bytes_per_update(args.precision) / 1e9,
+        "gpu_launches": args.steps * (3 if args.lattice == "d2q16" else 1),
+        "roofline": roofline(w, args.precision, its, kms, pk, args.lattice),
+        "hbm": {"bytes_per_update": bytes_per_update(args.precision, args.lattice),
+                "achieved_gbs": value / ws * 1e6 * bytes_per_update(args.precision, args.lattice) / 1e9,
                 "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
         "clocks": clocks.summary(),
     }
@@ -512,7 +527,7 @@ def main():
         line["fp64"] = {"value": w.nodes * 30 / (sum(ms64) * 1e-3) / 1e6, "unit": "MLUPS",
                         "ms_per_step": sum(ms64) / 30, "launch_shape": shape64 or "default",
                         "frame_search_streams_per_node": its64,
-                        "roofline": roofline(w, "fp64", its64, kms64, pk)}
+                        "roofline": roofline(w, "fp64", its64, kms64, pk, args.lattice)}
 
     if rank == 0 and not args.no_extras:
         line["other_configs"] = other_configs(pond, torch, stream, pk["sm_max_mhz"])
@@ -524,7 +539,7 @@ def main():
 
     if rank == 0 and not args.no_cpu:
         cpu_steps = args.cpu_steps or max(1, min(40, int(3e5 // w.nodes)))
-        res = oracle_mlups(w, cpu_steps)
+        res = oracle_mlups(w, cpu_steps, args.lattice)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
         # this run's GPU path against the oracle sample (same steps from the same start)
         line["linf_vs_oracle"] = parity_vs_oracle(w, pond, stream, args.precision, shape, res,

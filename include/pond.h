@@ -151,10 +151,12 @@ typedef struct {
     int64_t max_streams;   /* largest streaming-pass count of any block        */
 } pond_stats_t;
 
-/* Create a context and allocate its device state (two state buffers of 2Q + 7 planes,
- * a 5-plane FP64 staging buffer and reduction partials; on D2Q16 also 9 FP64 planes of
- * non-local terms).  lattice: POND_D2Q9 or POND_D2Q16 (else POND_EINVAL).  kappa >= 0: Korteweg coefficient (Eq. korteweg); tau > 1/2: BGK
- * relaxation time, omega = 1/tau.  On success *out owns the context. */
+/* Create a context and allocate its device state (two state buffers holding one record
+ * per node, 32 values on D2Q9 and 40 on D2Q16, in FP32 or FP64; a 5-plane FP64 staging
+ * buffer and reduction partials; on D2Q16 also 9 FP64 planes of non-local terms).
+ * lattice: POND_D2Q9 or POND_D2Q16 (else POND_EINVAL).  kappa >= 0: Korteweg coefficient
+ * (Eq. korteweg); tau > 1/2: BGK relaxation time, omega = 1/tau.  On success *out owns
+ * the context. */
 pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, const pond_eos *eos,
                         double kappa, double tau, const pond_opts *opts, pond_ctx **out);
 

@@ -46,7 +46,7 @@ struct pond_ctx {
     int nonlocal = 0;              // 1: current-time non-local terms (two passes per step)
     void *pred = nullptr;          // first pass's state (nonlocal = 1)
     DevStats *dstats_pred = nullptr;
-    int lattice = POND_D2Q9;       // POND_D2Q16: plane-major state of NP16 planes
+    int lattice = POND_D2Q9;       // POND_D2Q16: node records of SLQ values
     double *nlbuf = nullptr;       // D2Q16: NL_PLANES FP64 planes of non-local terms
     std::string err;
     size_t bytes = 0;
@@ -462,7 +462,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     split(d.T_iso, d.ff_Tiso);
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
-    size_t sb = (size_t)(c->lattice == POND_D2Q16 ? NP16 : SL) * c->N * c->esize;
+    size_t sb = (size_t)(c->lattice == POND_D2Q16 ? SLQ : SL) * c->N * c->esize;
     c->state[0] = dev_alloc(c, sb);
     c->state[1] = dev_alloc(c, sb);
     c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
@@ -616,19 +616,17 @@ pond_status pond_get_state(pond_ctx *c, double *state)
     if (!state) return fail(c, POND_EINVAL, "null output");
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
     if (c->lattice == POND_D2Q16) {
-        // plane-major on the device already: a copy (FP64) or a widening (FP32)
-        const size_t tot = (size_t)NP16 * c->N;
-        if (!mixed(c)) {
-            CK(cudaMemcpyAsync(state, c->state[c->cur], tot * sizeof(double), cudaMemcpyDeviceToHost,
-                               c->stream), "cudaMemcpyAsync D2H");
-            CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-            return POND_OK;
-        }
-        std::vector<float> f(tot);
-        CK(cudaMemcpyAsync(f.data(), c->state[c->cur], tot * sizeof(float), cudaMemcpyDeviceToHost,
-                           c->stream), "cudaMemcpyAsync D2H");
+        // node records on the device, planes on the host
+        const size_t N = c->N, rec = (size_t)SLQ * N;
+        std::vector<double> d(mixed(c) ? 0 : rec);
+        std::vector<float> f(mixed(c) ? rec : 0);
+        void *dst = mixed(c) ? (void *)f.data() : (void *)d.data();
+        CK(cudaMemcpyAsync(dst, c->state[c->cur], rec * c->esize, cudaMemcpyDeviceToHost, c->stream),
+           "cudaMemcpyAsync D2H");
         CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-        for (size_t k = 0; k < tot; ++k) state[k] = (double)f[k];
+        for (int p = 0; p < NP16; ++p)
+            for (size_t n = 0; n < N; ++n)
+                state[(size_t)p * N + n] = mixed(c) ? (double)f[n * SLQ + p] : d[n * SLQ + p];
         return POND_OK;
     }
     const size_t N = c->N, rec = (size_t)SL * N;
@@ -659,11 +657,16 @@ pond_status pond_set_state(pond_ctx *c, const double *state)
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null input");
     if (c->lattice == POND_D2Q16) {
-        const size_t tot = (size_t)NP16 * c->N;
-        std::vector<float> f(mixed(c) ? tot : 0);
-        for (size_t k = 0; k < f.size(); ++k) f[k] = (float)state[k];
-        const void *src = mixed(c) ? (const void *)f.data() : (const void *)state;
-        CK(cudaMemcpyAsync(c->state[c->cur], src, tot * c->esize, cudaMemcpyHostToDevice, c->stream),
+        const size_t N = c->N, rec = (size_t)SLQ * N;
+        std::vector<double> d(mixed(c) ? 0 : rec, 0.0);
+        std::vector<float> f(mixed(c) ? rec : 0, 0.0f);
+        for (int p = 0; p < NP16; ++p)
+            for (size_t n = 0; n < N; ++n) {
+                if (mixed(c)) f[n * SLQ + p] = (float)state[(size_t)p * N + n];
+                else d[n * SLQ + p] = state[(size_t)p * N + n];
+            }
+        const void *src = mixed(c) ? (const void *)f.data() : (const void *)d.data();
+        CK(cudaMemcpyAsync(c->state[c->cur], src, rec * c->esize, cudaMemcpyHostToDevice, c->stream),
            "cudaMemcpyAsync H2D");
         CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
         c->initialised = true;

@@ -7,12 +7,14 @@
 // G = M_lambda'^-1 M_lambda (SM "Transfer matrix") is then the product of two 4-node
 // Lagrange maps, one per axis, and keeps the sixteen moments M_mn, m, n <= 3.
 //
-// Layout: plane-major, plane k of node n at k*N + n, 39 planes (the ABI state's order):
+// Layout: one record of SLQ = 40 values per node (node = y*nx + x), in the ABI state's
+// plane order:
 //   [0..15] f_0..f_15, [16..31] g_0..g_15, [32] theta, [33] u_x, [34] u_y, [35] rho,
-//   [36] T, [37] uhat_x, [38] uhat_y
-// with population i = 4*jy + jx, c_i = (C1[jx], C1[jy]).  A block covers a 2-D patch of
-// nodes with x fastest, so the stencil reads of a warp fall on neighbouring addresses of
-// one plane.
+//   [36] T, [37] uhat_x, [38] uhat_y, [39] unused
+// with population i = 4*jy + jx, c_i = (C1[jx], C1[jy]).  Each row of four populations
+// and the gauge (theta, u_x, u_y, rho) start on 16-byte boundaries (160-byte records in
+// FP32, 320 in FP64), so a stencil node is read with nine 16-byte loads (FP32) at fixed
+// offsets from one address.
 //
 // One step is three launches: the Korteweg stress K and heat-flux vector q of the state
 // the non-local terms come from, their divergences F = -div K and M_0 = 2 div q, and the
@@ -32,7 +34,33 @@ enum : int { Q_F = 0, Q_G = 16, Q_TH = 32, Q_UX = 33, Q_UY = 34, Q_RHO = 35, Q_T
 // planes of the non-local scratch (FP64): K_xx, K_xy, K_yy, q_x, q_y, rho E_lambda, F_x, F_y, M_0
 enum : int { NL_KXX = 0, NL_KXY, NL_KYY, NL_QX, NL_QY, NL_REL, NL_FX, NL_FY, NL_M0, NL_PLANES };
 
-#define PLN(buf, plane, n, N) (buf)[(size_t)(plane) * (size_t)(N) + (size_t)(n)]
+constexpr int SLQ = 40;   // values per node record (39 used, padded to 16-byte rows)
+// value `off` of node n's record, and plane `plane` of the FP64 non-local scratch
+#define REC16(buf, n, off) (buf)[(size_t)(n) * SLQ + (off)]
+#define NLP(buf, plane, n, N) (buf)[(size_t)(plane) * (size_t)(N) + (size_t)(n)]
+
+// Four consecutive record values starting on a 16-byte boundary: one 16-byte load (FP32)
+// or two (FP64), through the read-only path; and the matching stores.
+__device__ __forceinline__ void ld4(const float *p, float (&o)[4])
+{
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&o)[4])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double *p, double a, double b, double c, double d)
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+}
 
 // C1, its weights, and per node k: 1 / prod_{j != k} (c_k - c_j) (the Lagrange
 // denominator), the three other nodes o_m (in increasing order) and 1 / (c_k - o_m).
@@ -180,16 +208,16 @@ __global__ void k_q16_init(DevParams p, const double *__restrict__ rho, const do
         const int jx = i & 3, jy = i >> 2;
         const double w = L.w[jx] * L.w[jy];
         const double vx = s * L.c[jx] + ux[n], vy = s * L.c[jy] + uy[n];
-        PLN(st, Q_F + i, n, N) = (R)(r * w);
-        PLN(st, Q_G + i, n, N) = (R)(r * w * (2.0 * e - 2.0 * P / r + vx * vx + vy * vy) + w * lam_e);
+        REC16(st, n, Q_F + i) = (R)(r * w);
+        REC16(st, n, Q_G + i) = (R)(r * w * (2.0 * e - 2.0 * P / r + vx * vx + vy * vy) + w * lam_e);
     }
-    PLN(st, Q_TH, n, N) = (R)th;
-    PLN(st, Q_UX, n, N) = (R)ux[n];
-    PLN(st, Q_UY, n, N) = (R)uy[n];
-    PLN(st, Q_RHO, n, N) = (R)r;
-    PLN(st, Q_T, n, N) = (R)t;
-    PLN(st, Q_UHX, n, N) = (R)ux[n];
-    PLN(st, Q_UHY, n, N) = (R)uy[n];
+    REC16(st, n, Q_TH) = (R)th;
+    REC16(st, n, Q_UX) = (R)ux[n];
+    REC16(st, n, Q_UY) = (R)uy[n];
+    REC16(st, n, Q_RHO) = (R)r;
+    REC16(st, n, Q_T) = (R)t;
+    REC16(st, n, Q_UHX) = (R)ux[n];
+    REC16(st, n, Q_UHY) = (R)uy[n];
 }
 
 // ---------------------------------------------------------------------------
@@ -206,12 +234,12 @@ __global__ void k_q16_nonlocal1(DevParams p, const R *__restrict__ src, double *
     const long long N = p.N;
     const int X = (int)(n % p.nx), Y = (int)(n / p.nx);
     double gr[2] = {0.0, 0.0}, gh[2] = {0.0, 0.0}, gT[2] = {0.0, 0.0}, lap = 0.0;
-    const double r0 = (double)PLN(src, Q_RHO, n, N), t0 = (double)PLN(src, Q_T, n, N);
+    const double r0 = (double)REC16(src, n, Q_RHO), t0 = (double)REC16(src, n, Q_T);
     for (int i = 0; i < 9; ++i) {
         const int cx = i % 3 - 1, cy = i / 3 - 1;
         const long long m = (long long)bc_wrap(Y + cy, p.ny, p.bcy) * p.nx + bc_wrap(X + cx, p.nx, p.bcx);
         const double w = w1d(cx + 1) * w1d(cy + 1);
-        const double r = (double)PLN(src, Q_RHO, m, N), t = (double)PLN(src, Q_T, m, N);
+        const double r = (double)REC16(src, m, Q_RHO), t = (double)REC16(src, m, Q_T);
         const double h = p.cv * t - p.a * r + q16_p(p, r, t) / r;
         gr[0] += w * cx * r; gr[1] += w * cy * r;
         gh[0] += w * cx * h; gh[1] += w * cy * h;
@@ -226,12 +254,12 @@ __global__ void k_q16_nonlocal1(DevParams p, const R *__restrict__ src, double *
     const double kc = p.k_cond >= 0.0 ? p.k_cond : mu * (p.cv + p.R);
     const double g2 = gr[0] * gr[0] + gr[1] * gr[1];
     const double iso = -p.kappa * (r0 * lap + 0.5 * g2);
-    PLN(nl, NL_KXX, n, N) = iso + p.kappa * gr[0] * gr[0];
-    PLN(nl, NL_KXY, n, N) = p.kappa * gr[0] * gr[1];
-    PLN(nl, NL_KYY, n, N) = iso + p.kappa * gr[1] * gr[1];
-    PLN(nl, NL_QX, n, N) = -mu * gh[0] + kc * gT[0];
-    PLN(nl, NL_QY, n, N) = -mu * gh[1] + kc * gT[1];
-    PLN(nl, NL_REL, n, N) = 0.5 * p.kappa * g2;
+    NLP(nl, NL_KXX, n, N) = iso + p.kappa * gr[0] * gr[0];
+    NLP(nl, NL_KXY, n, N) = p.kappa * gr[0] * gr[1];
+    NLP(nl, NL_KYY, n, N) = iso + p.kappa * gr[1] * gr[1];
+    NLP(nl, NL_QX, n, N) = -mu * gh[0] + kc * gT[0];
+    NLP(nl, NL_QY, n, N) = -mu * gh[1] + kc * gT[1];
+    NLP(nl, NL_REL, n, N) = 0.5 * p.kappa * g2;
 }
 
 // Stage 2: F = -div K and M_0 = 2 div q with the same gradient stencil.
@@ -246,16 +274,16 @@ __global__ void k_q16_nonlocal2(DevParams p, double *__restrict__ nl)
         const int cx = i % 3 - 1, cy = i / 3 - 1;
         const long long m = (long long)bc_wrap(Y + cy, p.ny, p.bcy) * p.nx + bc_wrap(X + cx, p.nx, p.bcx);
         const double w = w1d(cx + 1) * w1d(cy + 1);
-        dxx += w * cx * PLN(nl, NL_KXX, m, N);
-        dxy_x += w * cx * PLN(nl, NL_KXY, m, N);
-        dxy_y += w * cy * PLN(nl, NL_KXY, m, N);
-        dyy += w * cy * PLN(nl, NL_KYY, m, N);
-        dqx += w * cx * PLN(nl, NL_QX, m, N);
-        dqy += w * cy * PLN(nl, NL_QY, m, N);
+        dxx += w * cx * NLP(nl, NL_KXX, m, N);
+        dxy_x += w * cx * NLP(nl, NL_KXY, m, N);
+        dxy_y += w * cy * NLP(nl, NL_KXY, m, N);
+        dyy += w * cy * NLP(nl, NL_KYY, m, N);
+        dqx += w * cx * NLP(nl, NL_QX, m, N);
+        dqy += w * cy * NLP(nl, NL_QY, m, N);
     }
-    PLN(nl, NL_FX, n, N) = -3.0 * (dxx + dxy_y);
-    PLN(nl, NL_FY, n, N) = -3.0 * (dxy_x + dyy);
-    PLN(nl, NL_M0, n, N) = 6.0 * (dqx + dqy);
+    NLP(nl, NL_FX, n, N) = -3.0 * (dxx + dxy_y);
+    NLP(nl, NL_FY, n, N) = -3.0 * (dxy_x + dyy);
+    NLP(nl, NL_M0, n, N) = 6.0 * (dqx + dqy);
 }
 
 // ---------------------------------------------------------------------------
@@ -291,16 +319,18 @@ __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__res
             // interpolated as ref + sum w (v - ref) with ref = the node's own f_i, g_i: the
             // weights' rounded sum then only scales the small differences
             const int i = 4 * iy + ix;
-            const R refF = PLN(in, Q_F + i, nself, N), refG = PLN(in, Q_G + i, nself, N);
+            const R refF = REC16(in, nself, Q_F + i), refG = REC16(in, nself, Q_G + i);
             R sf = R(0), sg = R(0);
             // the 16 stencil nodes as a rolled loop (its body stays in the instruction cache)
 #pragma unroll 1
             for (int mk = 0; mk < 16; ++mk) {
                 const int m = mk >> 2, k = mk & 3;
-                const long long nd = sel4(rows, m) + sel4(cols, k);
-                const R ths = PLN(in, Q_TH, nd, N);
+                const R *rec = in + (size_t)(sel4(rows, m) + sel4(cols, k)) * SLQ;
+                R gv[4];   // theta, u_x, u_y, rho of the stencil node
+                ld4(rec + Q_TH, gv);
+                const R ths = gv[0];
                 const R ds = (ths - th) / (sqrt_(ths) + s) * is;   // (s' - s)/s
-                const R ex = (PLN(in, Q_UX, nd, N) - ux) * is, ey = (PLN(in, Q_UY, nd, N) - uy) * is;
+                const R ex = (gv[1] - ux) * is, ey = (gv[2] - uy) * is;
                 R epx[4], epy[4], gx[4], gy[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
@@ -314,11 +344,8 @@ __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__res
 #pragma unroll
                 for (int jy = 0; jy < 4; ++jy) {
                     R fr[4], gr[4];
-#pragma unroll
-                    for (int jx = 0; jx < 4; ++jx) {
-                        fr[jx] = PLN(in, Q_F + 4 * jy + jx, nd, N);
-                        gr[jx] = PLN(in, Q_G + 4 * jy + jx, nd, N);
-                    }
+                    ld4(rec + Q_F + 4 * jy, fr);
+                    ld4(rec + Q_G + 4 * jy, gr);
                     R df = R(0), dg = R(0);
 #pragma unroll
                     for (int jx = 0; jx < 4; ++jx) { df += gx[jx] * fr[jx]; dg += gx[jx] * gr[jx]; }
@@ -430,9 +457,9 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
     if (valid) {
         const Lat16<R> L = make_lat16<R>();
         const Lat16<double> Ld = make_lat16<double>();
-        const double Fx = PLN(nl, NL_FX, n, N), Fy = PLN(nl, NL_FY, n, N);
-        const double rEl = PLN(nl, NL_REL, n, N), M0 = PLN(nl, NL_M0, n, N);
-        R th = PLN(in, Q_TH, n, N), ux = PLN(in, Q_UX, n, N), uy = PLN(in, Q_UY, n, N);
+        const double Fx = NLP(nl, NL_FX, n, N), Fy = NLP(nl, NL_FY, n, N);
+        const double rEl = NLP(nl, NL_REL, n, N), M0 = NLP(nl, NL_M0, n, N);
+        R th = REC16(in, n, Q_TH), ux = REC16(in, n, Q_UX), uy = REC16(in, n, Q_UY);
         R ft[Q16], gt[Q16];
         double mac[11];
         int it = 0;
@@ -485,8 +512,11 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
             sf += (double)fo[i];
         }
         const R fdef = (R)(mac[0] - sf);
+        R *orec = out + (size_t)n * SLQ;
 #pragma unroll
-        for (int i = 0; i < Q16; ++i) PLN(out, Q_F + i, n, N) = fo[i] + fdef * (L.w[i & 3] * L.w[i >> 2]);
+        for (int i = 0; i < Q16; ++i) fo[i] += fdef * (L.w[i & 3] * L.w[i >> 2]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) st4(orec + Q_F + 4 * r, fo[4 * r], fo[4 * r + 1], fo[4 * r + 2], fo[4 * r + 3]);
 
         const R H = E + Pg / rho;
         const R Ixx = R(2) * uhx * fx + dt * fx * fx * E / (R(2) * Pg);
@@ -525,14 +555,11 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         const double g_tot = 2.0 * mac[0] * mac[5] + p.dt * (M0 + 2.0 * (mac[3] * Fx + mac[4] * Fy));
         const R gdef = (R)(g_tot - sg);
 #pragma unroll
-        for (int i = 0; i < Q16; ++i) PLN(out, Q_G + i, n, N) = go[i] + gdef * (L.w[i & 3] * L.w[i >> 2]);
-        PLN(out, Q_TH, n, N) = th;
-        PLN(out, Q_UX, n, N) = ux;
-        PLN(out, Q_UY, n, N) = uy;
-        PLN(out, Q_RHO, n, N) = rho;
-        PLN(out, Q_T, n, N) = (R)mac[7];
-        PLN(out, Q_UHX, n, N) = uhx;
-        PLN(out, Q_UHY, n, N) = uhy;
+        for (int i = 0; i < Q16; ++i) go[i] += gdef * (L.w[i & 3] * L.w[i >> 2]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) st4(orec + Q_G + 4 * r, go[4 * r], go[4 * r + 1], go[4 * r + 2], go[4 * r + 3]);
+        st4(orec + Q_TH, th, ux, uy, rho);
+        st4(orec + Q_T, (R)mac[7], uhx, uhy, R(0));
         const double chk = mac[0] + mac[7] + (double)ginc[0] + (double)eqi[0];
         nonfinite = (chk - chk == 0.0) ? 0ull : 1ull;
     }
@@ -557,10 +584,10 @@ __global__ void k_q16_moments(DevParams p, const R *__restrict__ st, double *rho
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
     const long long N = p.N;
-    const double r = (double)PLN(st, Q_RHO, n, N), t = (double)PLN(st, Q_T, n, N);
+    const double r = (double)REC16(st, n, Q_RHO), t = (double)REC16(st, n, Q_T);
     if (rho) rho[n] = r;
-    if (ux) ux[n] = (double)PLN(st, Q_UHX, n, N);
-    if (uy) uy[n] = (double)PLN(st, Q_UHY, n, N);
+    if (ux) ux[n] = (double)REC16(st, n, Q_UHX);
+    if (uy) uy[n] = (double)REC16(st, n, Q_UHY);
     if (T) T[n] = t;
     if (pr) pr[n] = q16_p(p, r, t);
 }
@@ -574,10 +601,10 @@ __global__ void k_q16_conserve1(DevParams p, const R *__restrict__ st, double *p
     double s[4] = {0, 0, 0, 0}, c[4] = {0, 0, 0, 0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
-        const double r = (double)PLN(st, Q_RHO, n, N);
+        const double r = (double)REC16(st, n, Q_RHO);
         double eg = 0.0;
-        for (int i = 0; i < Q16; ++i) eg += (double)PLN(st, Q_G + i, n, N);
-        const double v[4] = {r, r * (double)PLN(st, Q_UHX, n, N), r * (double)PLN(st, Q_UHY, n, N), 0.5 * eg};
+        for (int i = 0; i < Q16; ++i) eg += (double)REC16(st, n, Q_G + i);
+        const double v[4] = {r, r * (double)REC16(st, n, Q_UHX), r * (double)REC16(st, n, Q_UHY), 0.5 * eg};
         for (int k = 0; k < 4; ++k) pair_add(s[k], c[k], v[k], 0.0);
     }
     for (int o = 16; o > 0; o >>= 1)
