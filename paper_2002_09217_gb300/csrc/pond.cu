@@ -216,6 +216,15 @@ void launch_conserve(pond_ctx *c)
     k_conserve2<<<1, 32, 0, c->stream>>>(c->part, c->red_blocks, c->part + 8 * c->red_blocks);
 }
 
+// D2Q16 nodes and weights on the host (the same closed forms as the device's)
+void lattice16(double c[4], double w[4])
+{
+    const double s6 = std::sqrt(6.0), ci = std::sqrt(3.0 - s6), co = std::sqrt(3.0 + s6);
+    c[0] = -co; c[1] = -ci; c[2] = ci; c[3] = co;
+    w[0] = w[3] = (3.0 - s6) / 12.0;
+    w[1] = w[2] = (3.0 + s6) / 12.0;
+}
+
 pond_status check_ctx(pond_ctx *c)
 {
     if (!c) return POND_EINVAL;
@@ -627,6 +636,23 @@ pond_status pond_get_state(pond_ctx *c, double *state)
         for (int p = 0; p < NP16; ++p)
             for (size_t n = 0; n < N; ++n)
                 state[(size_t)p * N + n] = mixed(c) ? (double)f[n * SLQ + p] : d[n * SLQ + p];
+        if (mixed(c)) {
+            // the kept remainders go into the exchanged populations: mass and momentum as
+            // W_i (m + (c_ix J_x + c_iy J_y)/s) on f (its sum is m, its momentum m u + J),
+            // energy as W_i G on g
+            double cq[4], wq[4];
+            lattice16(cq, wq);
+            for (size_t n = 0; n < N; ++n) {
+                const float *r = &f[n * SLQ];
+                const double sq = std::sqrt((double)r[Q_TH]);
+                const double m = r[Q_MLO], jx = r[Q_JXLO], jy = r[Q_JYLO], gl = r[Q_GLO];
+                for (int i = 0; i < Q16; ++i) {
+                    const double w = wq[i & 3] * wq[i >> 2];
+                    state[(size_t)(Q_F + i) * N + n] += w * (m + (cq[i & 3] * jx + cq[i >> 2] * jy) / sq);
+                    state[(size_t)(Q_G + i) * N + n] += w * gl;
+                }
+            }
+        }
         return POND_OK;
     }
     const size_t N = c->N, rec = (size_t)SL * N;
@@ -665,6 +691,28 @@ pond_status pond_set_state(pond_ctx *c, const double *state)
                 if (mixed(c)) f[n * SLQ + p] = (float)state[(size_t)p * N + n];
                 else d[n * SLQ + p] = state[(size_t)p * N + n];
             }
+        if (mixed(c)) {
+            // what the FP32 populations leave out becomes the kept remainders again: mass
+            // sum r_i, momentum s sum r_i c_i (beyond the mass part's u m), energy sum r_gi
+            double cq[4], wq[4];
+            lattice16(cq, wq);
+            for (size_t n = 0; n < N; ++n) {
+                float *r = &f[n * SLQ];
+                const double sq = std::sqrt((double)r[Q_TH]);
+                double m = 0.0, sx = 0.0, sy = 0.0, gl = 0.0;
+                for (int i = 0; i < Q16; ++i) {
+                    const double rf = state[(size_t)(Q_F + i) * N + n] - (double)r[Q_F + i];
+                    m += rf;
+                    sx += rf * cq[i & 3];
+                    sy += rf * cq[i >> 2];
+                    gl += state[(size_t)(Q_G + i) * N + n] - (double)r[Q_G + i];
+                }
+                r[Q_MLO] = (float)m;
+                r[Q_JXLO] = (float)(sq * sx);
+                r[Q_JYLO] = (float)(sq * sy);
+                r[Q_GLO] = (float)gl;
+            }
+        }
         const void *src = mixed(c) ? (const void *)f.data() : (const void *)d.data();
         CK(cudaMemcpyAsync(c->state[c->cur], src, rec * c->esize, cudaMemcpyHostToDevice, c->stream),
            "cudaMemcpyAsync H2D");

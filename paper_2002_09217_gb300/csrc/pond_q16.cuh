@@ -10,11 +10,16 @@
 // Layout: one record of SLQ = 40 values per node (node = y*nx + x), in the ABI state's
 // plane order:
 //   [0..15] f_0..f_15, [16..31] g_0..g_15, [32] theta, [33] u_x, [34] u_y, [35] rho,
-//   [36] T, [37] uhat_x, [38] uhat_y, [39] unused
+//   [36] T, [37] uhat_x, [38] uhat_y, [39] mass lo, [40] momentum_x lo,
+//   [41] momentum_y lo, [42] energy lo, [43] unused
 // with population i = 4*jy + jx, c_i = (C1[jx], C1[jy]).  Each row of four populations
-// and the gauge (theta, u_x, u_y, rho) start on 16-byte boundaries (160-byte records in
-// FP32, 320 in FP64), so a stencil node is read with nine 16-byte loads (FP32) at fixed
-// offsets from one address.
+// and the gauge (theta, u_x, u_y, rho) start on 16-byte boundaries (176-byte records in
+// FP32, 352 in FP64), so a stencil node is read with nine 16-byte loads (FP32) at fixed
+// offsets from one address.  The lo values (FP32 form only; zero in FP64) are what the
+// storage rounding of the populations took from the node's exact post-collision mass,
+// momentum (sum f v) and energy (sum g); the next step's moments add them back, so that
+// changes below half an ulp of the populations (the weak edge of an acoustic pulse) are
+// not lost.
 //
 // One step is three launches: the Korteweg stress K and heat-flux vector q of the state
 // the non-local terms come from, their divergences F = -div K and M_0 = 2 div q, and the
@@ -34,7 +39,8 @@ enum : int { Q_F = 0, Q_G = 16, Q_TH = 32, Q_UX = 33, Q_UY = 34, Q_RHO = 35, Q_T
 // planes of the non-local scratch (FP64): K_xx, K_xy, K_yy, q_x, q_y, rho E_lambda, F_x, F_y, M_0
 enum : int { NL_KXX = 0, NL_KXY, NL_KYY, NL_QX, NL_QY, NL_REL, NL_FX, NL_FY, NL_M0, NL_PLANES };
 
-constexpr int SLQ = 40;   // values per node record (39 used, padded to 16-byte rows)
+constexpr int SLQ = 44;   // values per node record (43 used, padded to 16-byte rows)
+enum : int { Q_MLO = 39, Q_JXLO = 40, Q_JYLO = 41, Q_GLO = 42 };
 // value `off` of node n's record, and plane `plane` of the FP64 non-local scratch
 #define REC16(buf, n, off) (buf)[(size_t)(n) * SLQ + (off)]
 #define NLP(buf, plane, n, N) (buf)[(size_t)(plane) * (size_t)(N) + (size_t)(n)]
@@ -203,7 +209,6 @@ __global__ void k_q16_init(DevParams p, const double *__restrict__ rho, const do
     const double th = P / r, s = sqrt(th);
     const double e = p.cv * t - p.a * r;
     const double lam_e = p.kappa * (gx * gx + gy * gy);
-    const long long N = p.N;
     for (int i = 0; i < Q16; ++i) {
         const int jx = i & 3, jy = i >> 2;
         const double w = L.w[jx] * L.w[jy];
@@ -218,6 +223,7 @@ __global__ void k_q16_init(DevParams p, const double *__restrict__ rho, const do
     REC16(st, n, Q_T) = (R)t;
     REC16(st, n, Q_UHX) = (R)ux[n];
     REC16(st, n, Q_UHY) = (R)uy[n];
+    for (int k = Q_MLO; k < SLQ; ++k) REC16(st, n, k) = (R)0;
 }
 
 // ---------------------------------------------------------------------------
@@ -293,12 +299,13 @@ __global__ void k_q16_nonlocal2(DevParams p, double *__restrict__ nl)
 // the transfer map.  Only component i of G f is needed: with the per-axis maps
 // Gx[ix][jx] = l_ix((s' c_jx + u'_x - u_x)/s) (s' = sqrt(theta') and u' the neighbour's
 // gauge) it is sum_jy Gy[iy][jy] sum_jx Gx[ix][jx] f_(4 jy + jx), evaluated as f_i plus
-// increments (G = I + D per axis).
+// increments (G = I + D per axis).  Returns the increments fi, gi of the streamed
+// populations over the node's own stored f_i, g_i (streamed f_i = own f_i + fi[i]).
 template <typename R>
 __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__restrict__ in, int X,
-                           int Y, R th, R ux, R uy, R *ft, R *gt)
+                           int Y, R th, R ux, R uy, R *fi, R *gi)
 {
-    const long long N = p.N, nself = (long long)Y * p.nx + X;
+    const long long nself = (long long)Y * p.nx + X;
     const R s = sqrt_(th), is = R(1) / s, dt = (R)p.dt;
 #pragma unroll 1
     for (int iy = 0; iy < 4; ++iy) {
@@ -321,8 +328,9 @@ __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__res
             const int i = 4 * iy + ix;
             const R refF = REC16(in, nself, Q_F + i), refG = REC16(in, nself, Q_G + i);
             R sf = R(0), sg = R(0);
-            // the 16 stencil nodes as a rolled loop (its body stays in the instruction cache)
-#pragma unroll 1
+            // the 16 stencil nodes as a loop unrolled by two only (fully unrolled, the body
+            // overflows the instruction cache; two iterations give independent chains)
+#pragma unroll 2
             for (int mk = 0; mk < 16; ++mk) {
                 const int m = mk >> 2, k = mk & 3;
                 const R *rec = in + (size_t)(sel4(rows, m) + sel4(cols, k)) * SLQ;
@@ -363,32 +371,67 @@ __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__res
                 sf += wgt * (((sel4(bf, iy) - refF) + sel4(xf, iy)) + df);
                 sg += wgt * (((sel4(bg, iy) - refG) + sel4(xg, iy)) + dg);
             }
-            sf += refF;
-            sg += refG;
-            ft[4 * iy + ix] = sf;
-            gt[4 * iy + ix] = sg;
+            fi[4 * iy + ix] = sf;
+            gi[4 * iy + ix] = sg;
         }
     }
 }
 
-// Macroscopic fields of streamed populations in gauge (th, ux, uy) (moments Eq.), FP64:
-// out = rho, u_x, u_y, uhat_x, uhat_y, E, e, T, p, P = max(p, p_floor), theta* = P/rho.
+// Exact FP64 sums of a node's own stored populations and its kept remainders:
+// own[0] = sum f + mass lo, own[1] = sum f c_x, own[2] = sum f c_y, own[3] = sum g +
+// energy lo, own[4], own[5] = the momentum lo (absolute, sum f v units).
+template <typename R>
+__device__ __forceinline__ void q16_own_sums(const Lat16<double> &L, const R *rec, double own[6])
+{
+    double s0 = 0.0, sx = 0.0, sy = 0.0, sg = 0.0;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        R f[4], g[4];
+        ld4(rec + Q_F + 4 * r, f);
+        ld4(rec + Q_G + 4 * r, g);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            s0 += (double)f[k];
+            sx += (double)f[k] * L.c[k];
+            sy += (double)f[k] * L.c[r];
+            sg += (double)g[k];
+        }
+    }
+    R lo[4];
+    ld4(rec + Q_T, lo);       // T, uhat_x, uhat_y, mass lo
+    R lo2[4];
+    ld4(rec + Q_JXLO, lo2);   // momentum_x lo, momentum_y lo, energy lo, unused
+    own[0] = s0 + (double)lo[3];
+    own[1] = sx;
+    own[2] = sy;
+    own[3] = sg + (double)lo2[2];
+    own[4] = (double)lo2[0];
+    own[5] = (double)lo2[1];
+}
+
+// Macroscopic fields of the streamed populations (own + increments) in gauge (th, ux, uy)
+// (moments Eq.), FP64: out = rho, u_x, u_y, uhat_x, uhat_y, E, e, T, p,
+// P = max(p, p_floor), theta* = P/rho.
 template <typename R>
 __device__ __forceinline__ void q16_macro(const DevParams &p, const Lat16<double> &L, R th, R ux,
-                                          R uy, const R *ft, const R *gt, double Fx, double Fy,
-                                          double rEl, double out[11])
+                                          R uy, const double own[6], const R *fi, const R *gi,
+                                          double Fx, double Fy, double rEl, double out[11])
 {
     const double s = sqrt((double)th);
-    double rho = 0.0, jx = 0.0, jy = 0.0, sg = 0.0;
+    double d0 = 0.0, dx = 0.0, dy = 0.0, dg = 0.0;
 #pragma unroll
     for (int i = 0; i < Q16; ++i) {
-        const double vx = s * L.c[i & 3] + (double)ux, vy = s * L.c[i >> 2] + (double)uy;
-        const double f = (double)ft[i];
-        rho += f;
-        jx += f * vx;
-        jy += f * vy;
-        sg += (double)gt[i];
+        const double f = (double)fi[i];
+        d0 += f;
+        dx += f * L.c[i & 3];
+        dy += f * L.c[i >> 2];
+        dg += (double)gi[i];
     }
+    // sum f v = s sum f c + u sum f, for the stored part and the increments
+    const double rho = own[0] + d0;
+    const double jx = s * (own[1] + dx) + (double)ux * rho + own[4];
+    const double jy = s * (own[2] + dy) + (double)uy * rho + own[5];
+    const double sg = own[3] + dg;
     const double u_x = jx / rho, u_y = jy / rho;
     const double uhx = u_x + Fx * p.dt / (2.0 * rho), uhy = u_y + Fy * p.dt / (2.0 * rho);
     const double E = sg / (2.0 * rho);
@@ -460,14 +503,17 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         const double Fx = NLP(nl, NL_FX, n, N), Fy = NLP(nl, NL_FY, n, N);
         const double rEl = NLP(nl, NL_REL, n, N), M0 = NLP(nl, NL_M0, n, N);
         R th = REC16(in, n, Q_TH), ux = REC16(in, n, Q_UX), uy = REC16(in, n, Q_UY);
-        R ft[Q16], gt[Q16];
+        const R *irec = in + (size_t)n * SLQ;
+        double own[6];
+        q16_own_sums<R>(Ld, irec, own);
+        R ft[Q16], gt[Q16];   // increments during the search, streamed populations after it
         double mac[11];
         int it = 0;
         bool conv = false;
         for (;;) {
             ++it;
             q16_stream<R>(p, L, in, X, Y, th, ux, uy, ft, gt);
-            q16_macro<R>(p, Ld, th, ux, uy, ft, gt, Fx, Fy, rEl, mac);
+            q16_macro<R>(p, Ld, th, ux, uy, own, ft, gt, Fx, Fy, rEl, mac);
             const double t0 = (double)th, st0 = sqrt(t0);
             const double r0 = fabs(mac[10] - t0) / t0;
             const double r1 = fabs(mac[1] - (double)ux) / st0, r2 = fabs(mac[2] - (double)uy) / st0;
@@ -479,6 +525,17 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         its = (unsigned long long)it;
         nonconv = conv ? 0ull : 1ull;
         clamped = mac[8] < p.p_floor ? 1ull : 0ull;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            R f[4], g[4];
+            ld4(irec + Q_F + 4 * r, f);
+            ld4(irec + Q_G + 4 * r, g);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                ft[4 * r + k] += f[k];
+                gt[4 * r + k] += g[k];
+            }
+        }
 
         // ---- collision in type R, equilibria as increments over their co-moving form
         const TypedParams<R> &q = typed<R>(p);
@@ -500,21 +557,51 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         for (int i = 0; i < Q16; ++i) h[i] = rho * (L.w[i & 3] * L.w[i >> 2]);
         apply_inc<R>(Dx, Dy, h, eqi);
         apply_inc<R>(Ex, Ey, h, shi);
-        // Collision keeps the mass: sum_i f_out = rho exactly; the stored values are made to
-        // carry it (their FP64 sum is compared with rho and the defect, which the rounded
-        // weights and products would otherwise add every step in the same direction, is
-        // spread by W_i).  Zero in exact arithmetic.
+        // Collision keeps the mass and adds F dt to the momentum: sum_i f_out = rho and
+        // sum_i f_out v_i = rho u + F dt exactly.  The stored values are made to carry both
+        // (their FP64 sums are compared with the exact ones; the mass defect, which the
+        // rounded weights and products would otherwise add every step in the same
+        // direction, is spread by W_i, the momentum defect by W_i s c_i / theta, which has
+        // no mass).  Zero in exact arithmetic.
         R fo[Q16];
-        double sf = 0.0;
+        double sf = 0.0, sjx = 0.0, sjy = 0.0;
 #pragma unroll
         for (int i = 0; i < Q16; ++i) {
             fo[i] = ft[i] + om * ((h[i] - ft[i]) + eqi[i]) + (shi[i] - eqi[i]);
-            sf += (double)fo[i];
+            const double f = (double)fo[i];
+            sf += f;
+            sjx += f * Ld.c[i & 3];
+            sjy += f * Ld.c[i >> 2];
         }
-        const R fdef = (R)(mac[0] - sf);
+        // momentum of the stored values in the streaming gauge: sum f (s c + u)
+        sjx = sd * sjx + sf * (double)ux;
+        sjy = sd * sjy + sf * (double)uy;
+        const double mdef = mac[0] - sf;
+        const R fdef = (R)mdef;
+        // W_i s c_i J / theta = W_i c_i J / s (sum_i W_i c_i^2 = T_L = 1); the mass part
+        // W_i mdef already carries the momentum mdef u
+        const R jxdef = (R)((mac[0] * mac[1] + Fx * p.dt - sjx - mdef * (double)ux) / sd);
+        const R jydef = (R)((mac[0] * mac[2] + Fy * p.dt - sjy - mdef * (double)uy) / sd);
         R *orec = out + (size_t)n * SLQ;
 #pragma unroll
-        for (int i = 0; i < Q16; ++i) fo[i] += fdef * (L.w[i & 3] * L.w[i >> 2]);
+        for (int i = 0; i < Q16; ++i)
+            fo[i] += (L.w[i & 3] * L.w[i >> 2]) * (fdef + jxdef * L.c[i & 3] + jydef * L.c[i >> 2]);
+        // what the stored values still miss (below their rounding) is kept beside them
+        double mlo = 0.0, jxlo = 0.0, jylo = 0.0;
+        if (sizeof(R) == 4) {
+            double s0 = 0.0, cx = 0.0, cy = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q16; ++i) {
+                const double f = (double)fo[i];
+                s0 += f;
+                cx += f * Ld.c[i & 3];
+                cy += f * Ld.c[i >> 2];
+            }
+            mlo = mac[0] - s0;
+            // the mass lo carries momentum u mlo in the next step's sums
+            jxlo = (mac[0] * mac[1] + Fx * p.dt) - (sd * cx + (double)ux * s0) - mlo * (double)ux;
+            jylo = (mac[0] * mac[2] + Fy * p.dt) - (sd * cy + (double)uy * s0) - mlo * (double)uy;
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r) st4(orec + Q_F + 4 * r, fo[4 * r], fo[4 * r + 1], fo[4 * r + 2], fo[4 * r + 3]);
 
@@ -556,10 +643,18 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         const R gdef = (R)(g_tot - sg);
 #pragma unroll
         for (int i = 0; i < Q16; ++i) go[i] += gdef * (L.w[i & 3] * L.w[i >> 2]);
+        double glo = 0.0;
+        if (sizeof(R) == 4) {
+            double s1 = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q16; ++i) s1 += (double)go[i];
+            glo = g_tot - s1;
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r) st4(orec + Q_G + 4 * r, go[4 * r], go[4 * r + 1], go[4 * r + 2], go[4 * r + 3]);
         st4(orec + Q_TH, th, ux, uy, rho);
-        st4(orec + Q_T, (R)mac[7], uhx, uhy, R(0));
+        st4(orec + Q_T, (R)mac[7], uhx, uhy, (R)mlo);
+        st4(orec + Q_JXLO, (R)jxlo, (R)jylo, (R)glo, R(0));
         const double chk = mac[0] + mac[7] + (double)ginc[0] + (double)eqi[0];
         nonfinite = (chk - chk == 0.0) ? 0ull : 1ull;
     }
@@ -583,7 +678,6 @@ __global__ void k_q16_moments(DevParams p, const R *__restrict__ st, double *rho
 {
     const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= p.N) return;
-    const long long N = p.N;
     const double r = (double)REC16(st, n, Q_RHO), t = (double)REC16(st, n, Q_T);
     if (rho) rho[n] = r;
     if (ux) ux[n] = (double)REC16(st, n, Q_UHX);
@@ -602,7 +696,7 @@ __global__ void k_q16_conserve1(DevParams p, const R *__restrict__ st, double *p
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
          n += (long long)gridDim.x * blockDim.x) {
         const double r = (double)REC16(st, n, Q_RHO);
-        double eg = 0.0;
+        double eg = (double)REC16(st, n, Q_GLO);
         for (int i = 0; i < Q16; ++i) eg += (double)REC16(st, n, Q_G + i);
         const double v[4] = {r, r * (double)REC16(st, n, Q_UHX), r * (double)REC16(st, n, Q_UHY), 0.5 * eg};
         for (int k = 0; k < 4; ++k) pair_add(s[k], c[k], v[k], 0.0);
