@@ -118,10 +118,10 @@ def workload(name: str):
 def bytes_per_update(precision: str, lattice: str = "d2q9") -> int:
     e = 4 if precision == "mixed" else 8
     if lattice == "d2q16":
-        # record read once (f, g, gauge, rho, T: 37 values) + written once (39 values), and
-        # the nine FP64 non-local planes written and read once (rho, T of each node are
-        # read again by the non-local kernels: 2 values)
-        return (37 + 39 + 2) * e + 2 * 9 * 8
+        # the 44-value record read once (populations, gauge, fields, kept remainders) and
+        # written once, rho and T read again by the non-local kernels (2 values), and the
+        # nine FP64 non-local planes written and read once
+        return (44 + 44 + 2) * e + 2 * 9 * 8
     # state read once (f, g, gauge, rho, T: 23 values) + written once (25 values)
     return 48 * e
 

@@ -112,8 +112,9 @@ typedef struct {
  * 16 / tile_x; 0 = 16 for grids of fewer than 4 rows, else 4).  Both are performance
  * knobs (autotuning) of the D2Q9 kernel; results are the same to rounding.  The D2Q16
  * kernel (one thread per node) ignores them.
- * In the mixed form on D2Q16 the moments, e->T, EoS and frame-search residual are FP64
- * and no storage-rounding remainders are kept.
+ * In the mixed form on D2Q16 the moments, e->T, EoS and frame-search residual are FP64;
+ * the storage-rounding remainders of mass, momentum and energy are kept beside each
+ * node as on D2Q9.
  * nonlocal: time level of the Korteweg force, interface energy and heat-flux source,
  * which the paper leaves open.  POND_NONLOCAL_LAGGED (0): from rho, T at t - dt (one
  * launch per step).  POND_NONLOCAL_CURRENT (1): two passes per step, the first a lagged
@@ -152,7 +153,7 @@ typedef struct {
 } pond_stats_t;
 
 /* Create a context and allocate its device state (two state buffers holding one record
- * per node, 32 values on D2Q9 and 40 on D2Q16, in FP32 or FP64; a 5-plane FP64 staging
+ * per node, 32 values on D2Q9 and 44 on D2Q16, in FP32 or FP64; a 5-plane FP64 staging
  * buffer and reduction partials; on D2Q16 also 9 FP64 planes of non-local terms).
  * lattice: POND_D2Q9 or POND_D2Q16 (else POND_EINVAL).  kappa >= 0: Korteweg coefficient
  * (Eq. korteweg); tau > 1/2: BGK relaxation time, omega = 1/tau.  On success *out owns
@@ -194,7 +195,10 @@ pond_status pond_conservation(pond_ctx *ctx, double out[4]);
  * form the library keeps, beside each node's FP32 populations, what storage rounding
  * took from mass, energy and momentum: f_4 and g_4 are exchanged with it (as doubles;
  * set_state splits them again), the momentum part (below one FP32 ulp of the
- * populations) is not exchanged and set_state clears it. */
+ * populations) is not exchanged and set_state clears it.  On D2Q16 (mixed) all four
+ * remainders are exchanged folded into the populations (mass and momentum as
+ * W_i (m + (c_ix J_x + c_iy J_y)/sqrt(theta)) on f, energy as W_i G on g) and set_state
+ * recovers them from what the FP32 populations leave out. */
 pond_status pond_get_state(pond_ctx *ctx, double *state);
 pond_status pond_set_state(pond_ctx *ctx, const double *state);
 
