@@ -658,17 +658,22 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         const double chk = mac[0] + mac[7] + (double)ginc[0] + (double)eqi[0];
         nonfinite = (chk - chk == 0.0) ? 0ull : 1ull;
     }
-    warp_add(&stats->streams, its);
-    warp_add(&stats->nonconv, nonconv);
-    warp_add(&stats->clamped, clamped);
-    warp_add(&stats->nonfinite, nonfinite);
-    // largest streaming-pass count of any node
-    unsigned long long mx = its;
+    // counters: warp sums (every thread of the block reaches here; the warp's lanes are
+    // its linear thread indices, whatever the block's x extent), one atomic per warp
+    unsigned long long v[4] = {its, nonconv, clamped, nonfinite}, mx = its;
     for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = v > mx ? v : mx;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = m2 > mx ? m2 : mx;
     }
-    if ((threadIdx.x + threadIdx.y * blockDim.x) % 32 == 0 && mx) atomicMax(&stats->max_streams, mx);
+    if ((threadIdx.x + threadIdx.y * blockDim.x) % 32 == 0) {
+        if (v[0]) atomicAdd(&stats->streams, v[0]);
+        if (v[1]) atomicAdd(&stats->nonconv, v[1]);
+        if (v[2]) atomicAdd(&stats->clamped, v[2]);
+        if (v[3]) atomicAdd(&stats->nonfinite, v[3]);
+        if (mx) atomicMax(&stats->max_streams, mx);
+    }
 }
 
 // Output fields: rho, uhat, T, p in FP64.
