@@ -244,11 +244,12 @@ void pond_destroy(pond_ctx *ctx);
 const char *pond_last_error(const pond_ctx *ctx);
 
 /* ---- Batches: many simulations advanced together -------------------------------
- * A batch steps all its contexts with one launch of the step kernel per time step and
- * per group of contexts that share precision and lanes_per_node; the launch walks a
+ * A batch steps all its D2Q9 contexts with one launch of the step kernel per time step
+ * and per group of contexts that share precision and lanes_per_node; the launch walks a
  * device work-list of (context, tile) pairs, so contexts of different grid sizes and
- * parameters share it.  Two consecutive steps of every group are captured once in a
- * CUDA graph (when the batch stream is not the legacy default stream) and replayed.
+ * parameters share it.  D2Q16 contexts are stepped by their own three launches on the
+ * batch stream.  Two consecutive steps of the whole batch are captured once in a CUDA
+ * graph (when the batch stream is not the legacy default stream) and replayed.
  * Per-node arithmetic does not depend on the batch: a context gives the same result
  * stepped alone or in any batch.  The paper has no counterpart (serving layer).
  *
@@ -257,8 +258,8 @@ const char *pond_last_error(const pond_ctx *ctx);
  * wait for the batch's work first.  pond_step on a batched context is POND_EINVAL. */
 pond_status pond_batch_create(void *stream, pond_batch **out);
 
-/* Add an initialised D2Q9 context (same device); waits for the context's queued work.
- * A D2Q16 context is POND_EINVAL. */
+/* Add an initialised context (same device); waits for the context's queued work.  A
+ * two-pass (current-time) context is POND_EINVAL. */
 pond_status pond_batch_add(pond_batch *batch, pond_ctx *ctx);
 
 /* Remove a context (waits for the batch's work); the context may be stepped alone again. */

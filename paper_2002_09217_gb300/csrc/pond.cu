@@ -126,15 +126,16 @@ cudaError_t allow_step_smem()
 
 // D2Q16: the non-local terms of state `src` into nlbuf, then the node step in -> out.
 template <typename R>
-void launch_q16_pass(pond_ctx *c, const R *in, const R *src, R *out, DevStats *stats)
+void launch_q16_pass(pond_ctx *c, const R *in, const R *src, R *out, DevStats *stats,
+                     cudaStream_t strm)
 {
     const unsigned nb = blocks_for(c->N, 256);
-    k_q16_nonlocal1<R><<<nb, 256, 0, c->stream>>>(c->dp, src, c->nlbuf);
-    k_q16_nonlocal2<<<nb, 256, 0, c->stream>>>(c->dp, c->nlbuf);
+    k_q16_nonlocal1<R><<<nb, 256, 0, strm>>>(c->dp, src, c->nlbuf);
+    k_q16_nonlocal2<<<nb, 256, 0, strm>>>(c->dp, c->nlbuf);
     // 32 x 4 node patches (128 x 1 strips on grids of fewer than 4 rows)
     const dim3 blk = c->grid.ny < 4 ? dim3(128, 1) : dim3(32, 4);
     const dim3 grd(blocks_for((size_t)c->grid.nx, blk.x), blocks_for((size_t)c->grid.ny, blk.y));
-    k_q16_step<R><<<grd, blk, 0, c->stream>>>(c->dp, in, c->nlbuf, out, stats);
+    k_q16_step<R><<<grd, blk, 0, strm>>>(c->dp, in, c->nlbuf, out, stats);
 }
 
 template <typename R>
@@ -147,10 +148,10 @@ pond_status launch_step_q16(pond_ctx *c, cudaEvent_t *ev)
     if (c->nonlocal) {
         // pass 1 predicts rho, T at t (lagged terms); pass 2 redoes the step with the
         // non-local terms of that prediction
-        launch_q16_pass<R>(c, in, in, (R *)c->pred, c->dstats_pred);
+        launch_q16_pass<R>(c, in, in, (R *)c->pred, c->dstats_pred, c->stream);
         nl = (const R *)c->pred;
     }
-    launch_q16_pass<R>(c, in, nl, out, c->dstats);
+    launch_q16_pass<R>(c, in, nl, out, c->dstats, c->stream);
     if (ev) cudaEventRecord(ev[1], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
@@ -790,6 +791,10 @@ struct pond_batch {
         size_t smem = 0;
     };
     Group g[4];                       // (fp64, mixed) x (8, 16 lanes)
+    // D2Q16 contexts: stepped by their own three launches on the batch stream; cur0 is
+    // the context's current buffer when the lists were built
+    struct Q16 { pond_ctx *c; int cur0; };
+    std::vector<Q16> q16;
     cudaGraphExec_t graph = nullptr;  // two steps (even, odd) of every group
     bool graph_ok = false;
 };
@@ -858,11 +863,24 @@ void launch_group(pond_batch *b, pond_batch::Group &G, int parity)
         k_pond_step_batch<R, 8><<<G.nwork, STEP_NB * 8, G.smem, b->stream>>>(d, G.work);
 }
 
+template <typename R>
+void launch_q16_entry(pond_batch *b, const pond_batch::Q16 &e, int parity)
+{
+    pond_ctx *c = e.c;
+    const int ci = e.cur0 ^ parity;
+    const R *in = (const R *)c->state[ci];
+    launch_q16_pass<R>(c, in, in, (R *)c->state[1 - ci], c->dstats, b->stream);
+}
+
 void launch_all(pond_batch *b, int parity)
 {
     for (int k = 0; k < 4; ++k) {
         if (b->g[k].precision == POND_MIXED) launch_group<float>(b, b->g[k], parity);
         else launch_group<double>(b, b->g[k], parity);
+    }
+    for (const pond_batch::Q16 &e : b->q16) {
+        if (mixed(e.c)) launch_q16_entry<float>(b, e, parity);
+        else launch_q16_entry<double>(b, e, parity);
     }
 }
 
@@ -873,7 +891,12 @@ pond_status batch_build(pond_batch *b)
         b->g[k].lanes = (k & 2) ? 16 : 8;
         b->g[k].sims.clear();
     }
+    b->q16.clear();
     for (pond_ctx *c : b->sims) {
+        if (c->lattice == POND_D2Q16) {
+            b->q16.push_back({c, c->cur});
+            continue;
+        }
         const int k = (c->opts.precision == POND_MIXED ? 1 : 0) | (c->lanes == 16 ? 2 : 0);
         b->g[k].sims.push_back(c);
     }
@@ -927,7 +950,6 @@ pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
     if (c->batch) return bfail(b, POND_EINVAL, "context already belongs to a batch");
     if (!c->initialised) return bfail(b, POND_EINVAL, "context state not initialised");
     if (c->nonlocal) return bfail(b, POND_EINVAL, "two-pass (current-time) contexts are stepped alone");
-    if (c->lattice != POND_D2Q9) return bfail(b, POND_EINVAL, "batches step D2Q9 contexts");
     if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
     // the context's queued work (its initialisation) completes before the batch uses it

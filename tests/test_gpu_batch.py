@@ -128,3 +128,39 @@ def test_batch_mixing_equations_of_state_equals_alone(pond):
     batch.close()
     for s in sims:
         s.close()
+
+
+def test_batch_with_d2q16_members_equals_alone(pond):
+    """D2Q16 simulations (their own three launches on the batch stream, inside the batch's
+    graph) next to a D2Q9 group, with one leaving and rejoining between odd step counts:
+    each equals its alone run bit for bit."""
+    cases = [
+        (inputs.droplet(n=40, ny=28, Tr=0.9, radius=6.0), "mixed", {"lattice": "d2q16"}),
+        (inputs.slab(nx=48, ny=5, Tr=0.9), "fp64", {"lattice": "d2q16"}),
+        (inputs.droplet(n=32, ny=24, Tr=0.9, radius=6.0), "mixed", {}),
+    ]
+    batch = pond.Batch()
+    sims = []
+    for w, prec, kw in cases:
+        s = pond.from_workload(w, precision=prec, **kw)
+        s.init_fields(*w.fields())
+        batch.add(s)
+        sims.append(s)
+    steps = [5, 5, 5]
+    batch.step(5)
+    batch.remove(sims[0])
+    batch.step(4)
+    steps[1] += 4
+    steps[2] += 4
+    batch.add(sims[0])
+    batch.step(3)
+    steps = [n + 3 for n in steps]
+    batch.synchronize()
+    for (w, prec, kw), sim, n in zip(cases, sims, steps):
+        got = sim.moments()
+        ref = _alone(pond, w, prec, kw, n)
+        for key in ref:
+            np.testing.assert_array_equal(got[key], ref[key], err_msg="%s %s %s" % (w.name, kw, key))
+    batch.close()
+    for s in sims:
+        s.close()

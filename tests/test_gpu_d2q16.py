@@ -3,7 +3,7 @@ oracle on the same lattice.
 
 Element by element on small grids (several 32 x 4 node patches plus ragged tails, and
 the 128 x 1 strips of grids of fewer than four rows), the current-time non-local
-variant, conservation sums, checkpoint/resume, batch rejection, and one-step checks at
+variant, conservation sums, checkpoint/resume, and one-step checks at
 sampled nodes of a full-size 1024 x 512 droplet (the oracle steps those nodes from the
 GPU's own previous state).  Bars as on D2Q9: FP64 <= 1e-11, mixed <= 1e-5 relative
 L-infinity per field (rho, uhat_x, uhat_y, T, p).
@@ -117,16 +117,6 @@ def test_checkpoint_resume(pond, precision):
         else:
             err = rel_linf(b.moments(), ref_m)
             assert max(err.values()) <= 1e-6, err
-
-
-def test_batches_refuse_d2q16(pond):
-    w = inputs.droplet(n=16, ny=16, Tr=0.9, radius=4.0, steps=1)
-    with pond.from_workload(w, precision="fp64", lattice=LAT) as sim:
-        sim.init_fields(*w.fields())
-        b = pond.Batch()
-        with pytest.raises(pond.PondError):
-            b.add(sim)
-        b.close()
 
 
 def _fields_q16(P, rows):
