@@ -25,6 +25,9 @@
  *     T_L = sum W c^2; SM "Equilibrium"):
  *       POND_D2Q9 (the paper's): C1 = {-1, 0, 1}, population index i = 3*(cy+1) + (cx+1),
  *         W_0 = 2/3, W_+-1 = 1/6, T_L = 1/3;
+ *       POND_D3Q27 (three dimensions, D = 3 in the energy equilibrium and the heat-flux
+ *         correction): C1^3 with C1 = {-1, 0, 1}, index i = 9*(cz+1) + 3*(cy+1) + (cx+1),
+ *         W = product of 1/6, 2/3, 1/6, T_L = 1/3; the 4x4x4 cubic stencil;
  *       POND_D2Q16: C1 = the roots -+sqrt(3 +- sqrt 6) of He_4(c) = c^4 - 6 c^2 + 3 in
  *         increasing order, index i = 4*jy + jx, Gauss-Hermite weights (3 - sqrt 6)/12
  *         (outer) and (3 + sqrt 6)/12 (inner), T_L = 1; the transfer map is the product
@@ -69,15 +72,17 @@ typedef enum {
 } pond_status;
 
 enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
-enum { POND_D2Q9 = 0, POND_D2Q16 = 1 };           /* lattice                         */
+enum { POND_D2Q9 = 0, POND_D2Q16 = 1, POND_D3Q27 = 2 };   /* lattice                  */
 enum { POND_VDW = 0, POND_IDEAL = 1, POND_DIETERICI = 2, POND_SIMPLIFIED = 3 };   /* see pond_eos */
 enum { POND_FP64 = 0, POND_MIXED = 1 };            /* arithmetic / storage form       */
 enum { POND_NONLOCAL_LAGGED = 0, POND_NONLOCAL_CURRENT = 1 };   /* see pond_opts.nonlocal */
 
-/* Grid: nx, ny >= 1; bc_x, bc_y: POND_PERIODIC, or POND_ZEROGRAD (index clamp). */
-typedef struct { int32_t nx, ny; int32_t bc_x, bc_y; } pond_grid;
+/* Grid: nx, ny >= 1; bc_x, bc_y, bc_z: POND_PERIODIC, or POND_ZEROGRAD (index clamp).
+ * nz: nodes along z, >= 1 on POND_D3Q27 (node = (z*ny + y)*nx + x), 0 or 1 on the
+ * two-dimensional lattices; bc_z is read on D3Q27 only. */
+typedef struct { int32_t nx, ny; int32_t bc_x, bc_y; int32_t nz, bc_z; } pond_grid;
 
-typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9 or POND_D2Q16 */
+typedef struct { int32_t kind; } pond_lattice;     /* kind = POND_D2Q9, D2Q16 or D3Q27 */
 
 /* Equation of state.  POND_VDW: van der Waals p = rho R T/(1 - b rho) - a rho^2 with
  * e = (R/delta) T - a rho (main text; SM "Thermodynamics"); 0 < delta <= 2/3.
@@ -168,6 +173,12 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
 pond_status pond_init_fields(pond_ctx *ctx, const double *rho, const double *ux,
                              const double *uy, const double *T);
 
+/* Same with a z velocity (D3Q27; nx*ny*nz doubles each, host arrays).  On the
+ * two-dimensional lattices uz is ignored; pond_init_fields and the device form take
+ * u_z = 0. */
+pond_status pond_init_fields3(pond_ctx *ctx, const double *rho, const double *ux, const double *uy,
+                              const double *uz, const double *T);
+
 /* Same with device pointers (nx*ny doubles each, read on the context stream). */
 pond_status pond_init_fields_device(pond_ctx *ctx, const double *d_rho, const double *d_ux,
                                     const double *d_uy, const double *d_T);
@@ -180,7 +191,12 @@ pond_status pond_step(pond_ctx *ctx, int64_t n);
 pond_status pond_moments(pond_ctx *ctx, double *rho, double *ux, double *uy, double *T,
                          double *p);
 
-/* Same into device arrays (asynchronous). */
+/* With the z component of uhat (zero on the two-dimensional lattices); host arrays of
+ * nx*ny*nz doubles, NULL skips a field.  Synchronises. */
+pond_status pond_moments3(pond_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *T,
+                          double *p);
+
+/* Same into device arrays (asynchronous; no u_z). */
 pond_status pond_moments_device(pond_ctx *ctx, double *d_rho, double *d_ux, double *d_uy,
                                 double *d_T, double *d_p);
 
@@ -190,7 +206,9 @@ pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 
 /* Full state as 2Q + 7 host planes of nx*ny doubles (25 on D2Q9, 39 on D2Q16):
  * f_0..f_(Q-1), g_0..g_(Q-1), theta, u_x, u_y (the gauge the populations are stored in),
- * rho, T, uhat_x, uhat_y.
+ * rho, T, uhat_x, uhat_y; on D3Q27 63 planes of nx*ny*nz doubles: f, g, theta, u_x, u_y,
+ * u_z, rho, T, uhat_x, uhat_y, uhat_z (its FP32 remainders folded in as on D2Q16, the
+ * momentum part as W_i c_i . J / (sqrt(theta) T_L)).
  * pond_get_state synchronises; pond_set_state replaces the current state.  In the mixed
  * form the library keeps, beside each node's FP32 populations, what storage rounding
  * took from mass, energy and momentum: f_4 and g_4 are exchanged with it (as doubles;
@@ -259,7 +277,7 @@ const char *pond_last_error(const pond_ctx *ctx);
 pond_status pond_batch_create(void *stream, pond_batch **out);
 
 /* Add an initialised context (same device); waits for the context's queued work.  A
- * two-pass (current-time) context is POND_EINVAL. */
+ * two-pass (current-time) context and a D3Q27 context are POND_EINVAL. */
 pond_status pond_batch_add(pond_batch *batch, pond_ctx *ctx);
 
 /* Remove a context (waits for the batch's work); the context may be stepped alone again. */

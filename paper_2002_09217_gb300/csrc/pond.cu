@@ -20,6 +20,7 @@
 #include "pond_kernels.cuh"
 #include "pond_step.cuh"
 #include "pond_q16.cuh"
+#include "pond_q27.cuh"
 
 using namespace pond;
 
@@ -34,7 +35,7 @@ struct pond_ctx {
     size_t N = 0, esize = 0;
     void *state[2] = {nullptr, nullptr};
     int cur = 0;
-    double *stage = nullptr;       // 5 planes of double
+    double *stage = nullptr;       // 6 planes of double
     double *part = nullptr;        // conservation partials (nblk * 8) + out[4]
     int red_blocks = 0;
     DevStats *dstats = nullptr;
@@ -46,7 +47,8 @@ struct pond_ctx {
     int nonlocal = 0;              // 1: current-time non-local terms (two passes per step)
     void *pred = nullptr;          // first pass's state (nonlocal = 1)
     DevStats *dstats_pred = nullptr;
-    int lattice = POND_D2Q9;       // POND_D2Q16: node records of SLQ values
+    int lattice = POND_D2Q9;       // POND_D2Q16: node records of SLQ values; POND_D3Q27: SL27
+    Grid3 g3{1, 0};                // z extent and boundary (D3Q27)
     double *nlbuf = nullptr;       // D2Q16: NL_PLANES FP64 planes of non-local terms
     std::string err;
     size_t bytes = 0;
@@ -157,10 +159,40 @@ pond_status launch_step_q16(pond_ctx *c, cudaEvent_t *ev)
     return POND_OK;
 }
 
+// D3Q27: the non-local terms of state `src`, then the node step in -> out.
+template <typename R>
+void launch_q27_pass(pond_ctx *c, const R *in, const R *src, R *out, DevStats *stats)
+{
+    const unsigned nb = blocks_for(c->N, 256);
+    k_q27_nonlocal1<R><<<nb, 256, 0, c->stream>>>(c->dp, c->g3, src, c->nlbuf);
+    k_q27_nonlocal2<<<nb, 256, 0, c->stream>>>(c->dp, c->g3, c->nlbuf);
+    const dim3 blk = c->grid.ny < 4 ? dim3(128, 1) : dim3(32, 4);
+    const dim3 grd(blocks_for((size_t)c->grid.nx, blk.x), blocks_for((size_t)c->grid.ny, blk.y), (unsigned)c->g3.nz);
+    k_q27_step<R><<<grd, blk, 0, c->stream>>>(c->dp, c->g3, in, c->nlbuf, out, stats);
+}
+
+template <typename R>
+pond_status launch_step_q27(pond_ctx *c, cudaEvent_t *ev)
+{
+    const R *in = (const R *)c->state[c->cur];
+    R *out = (R *)c->state[1 - c->cur];
+    if (ev) cudaEventRecord(ev[0], c->stream);
+    const R *nl = in;
+    if (c->nonlocal) {
+        launch_q27_pass<R>(c, in, in, (R *)c->pred, c->dstats_pred);
+        nl = (const R *)c->pred;
+    }
+    launch_q27_pass<R>(c, in, nl, out, c->dstats);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    c->cur = 1 - c->cur;
+    return POND_OK;
+}
+
 template <typename R>
 pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 {
     if (c->lattice == POND_D2Q16) return launch_step_q16<R>(c, ev);
+    if (c->lattice == POND_D3Q27) return launch_step_q27<R>(c, ev);
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
     const int tx = c->dp.tile_x, ty = STEP_NB / tx;
@@ -184,8 +216,14 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
 }
 
 template <typename R>
-void launch_init(pond_ctx *c, const double *rho, const double *ux, const double *uy, const double *T)
+void launch_init(pond_ctx *c, const double *rho, const double *ux, const double *uy, const double *uz,
+                 const double *T)
 {
+    if (c->lattice == POND_D3Q27) {
+        k_q27_init<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, c->g3, rho, ux, uy, uz, T,
+                                                                    (R *)c->state[c->cur], c->dstats);
+        return;
+    }
     if (c->lattice == POND_D2Q16) {
         k_q16_init<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, rho, ux, uy, T,
                                                                     (R *)c->state[c->cur], c->dstats);
@@ -196,8 +234,13 @@ void launch_init(pond_ctx *c, const double *rho, const double *ux, const double 
 }
 
 template <typename R>
-void launch_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T, double *p)
+void launch_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T, double *p)
 {
+    if (c->lattice == POND_D3Q27) {
+        k_q27_moments<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur],
+                                                                       rho, ux, uy, uz, T, p);
+        return;
+    }
     if (c->lattice == POND_D2Q16) {
         k_q16_moments<R><<<blocks_for(c->N, 256), 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur],
                                                                        rho, ux, uy, T, p);
@@ -210,7 +253,9 @@ void launch_moments(pond_ctx *c, double *rho, double *ux, double *uy, double *T,
 template <typename R>
 void launch_conserve(pond_ctx *c)
 {
-    if (c->lattice == POND_D2Q16)
+    if (c->lattice == POND_D3Q27)
+        k_q27_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
+    else if (c->lattice == POND_D2Q16)
         k_q16_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
     else
         k_conserve1<R><<<c->red_blocks, 256, 0, c->stream>>>(c->dp, (const R *)c->state[c->cur], c->part);
@@ -241,11 +286,11 @@ pond_status check_ctx(pond_ctx *c)
 }
 
 pond_status init_common(pond_ctx *c, const double *d_rho, const double *d_ux, const double *d_uy,
-                        const double *d_T)
+                        const double *d_uz, const double *d_T)
 {
     CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream), "cudaMemsetAsync");
-    if (mixed(c)) launch_init<float>(c, d_rho, d_ux, d_uy, d_T);
-    else launch_init<double>(c, d_rho, d_ux, d_uy, d_T);
+    if (mixed(c)) launch_init<float>(c, d_rho, d_ux, d_uy, d_uz, d_T);
+    else launch_init<double>(c, d_rho, d_ux, d_uy, d_uz, d_T);
     CK(cudaGetLastError(), "k_init launch");
     DevStats hs{};
     CK(cudaMemcpyAsync(&hs, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream), "cudaMemcpyAsync");
@@ -391,7 +436,12 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     if ((grid->bc_x != POND_PERIODIC && grid->bc_x != POND_ZEROGRAD) ||
         (grid->bc_y != POND_PERIODIC && grid->bc_y != POND_ZEROGRAD))
         return POND_EINVAL;
-    if (lattice->kind != POND_D2Q9 && lattice->kind != POND_D2Q16) return POND_EINVAL;
+    if (lattice->kind != POND_D2Q9 && lattice->kind != POND_D2Q16 && lattice->kind != POND_D3Q27)
+        return POND_EINVAL;
+    // z extent: 0 or 1 on the two-dimensional lattices; >= 1 on D3Q27
+    if (grid->nz < 0 || (lattice->kind != POND_D3Q27 && grid->nz > 1)) return POND_EINVAL;
+    if (lattice->kind == POND_D3Q27 && (grid->nz < 1 || (grid->bc_z != POND_PERIODIC && grid->bc_z != POND_ZEROGRAD)))
+        return POND_EINVAL;
     if (eos->kind != POND_VDW && eos->kind != POND_IDEAL && eos->kind != POND_DIETERICI &&
         eos->kind != POND_SIMPLIFIED)
         return POND_EINVAL;
@@ -428,7 +478,8 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     c->kappa = kappa;
     c->tau = tau;
     c->stream = (cudaStream_t)opts->stream;
-    c->N = (size_t)grid->nx * (size_t)grid->ny;
+    c->N = (size_t)grid->nx * (size_t)grid->ny * (size_t)(grid->nz > 1 ? grid->nz : 1);
+    if (c->lattice == POND_D3Q27) c->g3 = Grid3{grid->nz, grid->bc_z};
     c->esize = opts->precision == POND_MIXED ? sizeof(float) : sizeof(double);
     // 8 lanes per node unless the caller picks 16 (measured faster on every grid tried so
     // far; the choice is exposed for the autotuner).
@@ -472,20 +523,21 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
     split(d.T_iso, d.ff_Tiso);
 
     c->red_blocks = (int)std::min<size_t>(1024, std::max<size_t>(1, (c->N + 255) / 256));
-    size_t sb = (size_t)(c->lattice == POND_D2Q16 ? SLQ : SL) * c->N * c->esize;
+    size_t sb = (size_t)(c->lattice == POND_D2Q16 ? SLQ : (c->lattice == POND_D3Q27 ? SL27 : SL)) * c->N * c->esize;
     c->state[0] = dev_alloc(c, sb);
     c->state[1] = dev_alloc(c, sb);
-    c->stage = (double *)dev_alloc(c, 5 * c->N * sizeof(double));
+    c->stage = (double *)dev_alloc(c, 6 * c->N * sizeof(double));
     c->part = (double *)dev_alloc(c, (8 * (size_t)c->red_blocks + 8) * sizeof(double));
     c->dstats = (DevStats *)dev_alloc(c, sizeof(DevStats));
     if (c->lattice == POND_D2Q16) c->nlbuf = (double *)dev_alloc(c, (size_t)NL_PLANES * c->N * sizeof(double));
+    if (c->lattice == POND_D3Q27) c->nlbuf = (double *)dev_alloc(c, (size_t)N3_PLANES * c->N * sizeof(double));
     c->nonlocal = opts->nonlocal;
     if (c->nonlocal) {
         c->pred = dev_alloc(c, sb);
         c->dstats_pred = (DevStats *)dev_alloc(c, sizeof(DevStats));
     }
     if (!c->state[0] || !c->state[1] || !c->stage || !c->part || !c->dstats ||
-        (c->nonlocal && (!c->pred || !c->dstats_pred)) || (c->lattice == POND_D2Q16 && !c->nlbuf)) {
+        (c->nonlocal && (!c->pred || !c->dstats_pred)) || (c->lattice != POND_D2Q9 && !c->nlbuf)) {
         pond_destroy(c);
         return POND_ENOMEM;
     }
@@ -526,7 +578,24 @@ pond_status pond_init_fields(pond_ctx *c, const double *rho, const double *ux, c
     for (int k = 0; k < 4; ++k)
         CK(cudaMemcpyAsync(c->stage + k * c->N, src[k], bytes, cudaMemcpyHostToDevice, c->stream),
            "cudaMemcpyAsync H2D");
-    return init_common(c, c->stage, c->stage + c->N, c->stage + 2 * c->N, c->stage + 3 * c->N);
+    CK(cudaMemsetAsync(c->stage + 4 * c->N, 0, bytes, c->stream), "cudaMemsetAsync");   // u_z = 0
+    return init_common(c, c->stage, c->stage + c->N, c->stage + 2 * c->N, c->stage + 4 * c->N,
+                       c->stage + 3 * c->N);
+}
+
+pond_status pond_init_fields3(pond_ctx *c, const double *rho, const double *ux, const double *uy,
+                              const double *uz, const double *T)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!rho || !ux || !uy || !uz || !T) return fail(c, POND_EINVAL, "null field pointer");
+    size_t bytes = c->N * sizeof(double);
+    const double *src[5] = {rho, ux, uy, T, uz};
+    for (int k = 0; k < 5; ++k)
+        CK(cudaMemcpyAsync(c->stage + k * c->N, src[k], bytes, cudaMemcpyHostToDevice, c->stream),
+           "cudaMemcpyAsync H2D");
+    return init_common(c, c->stage, c->stage + c->N, c->stage + 2 * c->N, c->stage + 4 * c->N,
+                       c->stage + 3 * c->N);
 }
 
 pond_status pond_init_fields_device(pond_ctx *c, const double *d_rho, const double *d_ux,
@@ -535,7 +604,8 @@ pond_status pond_init_fields_device(pond_ctx *c, const double *d_rho, const doub
     pond_status st = check_ctx(c);
     if (st) return st;
     if (!d_rho || !d_ux || !d_uy || !d_T) return fail(c, POND_EINVAL, "null field pointer");
-    return init_common(c, d_rho, d_ux, d_uy, d_T);
+    CK(cudaMemsetAsync(c->stage + 4 * c->N, 0, c->N * sizeof(double), c->stream), "cudaMemsetAsync");
+    return init_common(c, d_rho, d_ux, d_uy, c->stage + 4 * c->N, d_T);
 }
 
 pond_status pond_step(pond_ctx *c, int64_t n)
@@ -580,8 +650,8 @@ pond_status pond_moments_device(pond_ctx *c, double *rho, double *ux, double *uy
     pond_status st = check_ctx(c);
     if (st) return st;
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
-    if (mixed(c)) launch_moments<float>(c, rho, ux, uy, T, p);
-    else launch_moments<double>(c, rho, ux, uy, T, p);
+    if (mixed(c)) launch_moments<float>(c, rho, ux, uy, nullptr, T, p);
+    else launch_moments<double>(c, rho, ux, uy, nullptr, T, p);
     CK(cudaGetLastError(), "k_moments launch");
     return POND_OK;
 }
@@ -597,6 +667,33 @@ pond_status pond_moments(pond_ctx *c, double *rho, double *ux, double *uy, doubl
     st = pond_moments_device(c, dev[0], dev[1], dev[2], dev[3], dev[4]);
     if (st) return st;
     for (int k = 0; k < 5; ++k)
+        if (host[k])
+            CK(cudaMemcpyAsync(host[k], dev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+               "cudaMemcpyAsync D2H");
+    CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    return POND_OK;
+}
+
+pond_status pond_moments3(pond_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T,
+                          double *p)
+{
+    pond_status st = check_ctx(c);
+    if (st) return st;
+    if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    double *host[6] = {rho, ux, uy, uz, T, p};
+    double *dev[6];
+    for (int k = 0; k < 6; ++k) dev[k] = host[k] ? c->stage + k * c->N : nullptr;
+    if (c->lattice == POND_D3Q27) {
+        if (mixed(c)) launch_moments<float>(c, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5]);
+        else launch_moments<double>(c, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5]);
+    } else {
+        // two-dimensional lattices: u_z = 0
+        if (mixed(c)) launch_moments<float>(c, dev[0], dev[1], dev[2], nullptr, dev[4], dev[5]);
+        else launch_moments<double>(c, dev[0], dev[1], dev[2], nullptr, dev[4], dev[5]);
+        if (dev[3]) CK(cudaMemsetAsync(dev[3], 0, c->N * sizeof(double), c->stream), "cudaMemsetAsync");
+    }
+    CK(cudaGetLastError(), "k_moments launch");
+    for (int k = 0; k < 6; ++k)
         if (host[k])
             CK(cudaMemcpyAsync(host[k], dev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                "cudaMemcpyAsync D2H");
@@ -625,6 +722,38 @@ pond_status pond_get_state(pond_ctx *c, double *state)
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null output");
     if (!c->initialised) return fail(c, POND_EINVAL, "state not initialised");
+    if (c->lattice == POND_D3Q27) {
+        const size_t N = c->N, rec = (size_t)SL27 * N;
+        std::vector<double> d(mixed(c) ? 0 : rec);
+        std::vector<float> f(mixed(c) ? rec : 0);
+        void *dst = mixed(c) ? (void *)f.data() : (void *)d.data();
+        CK(cudaMemcpyAsync(dst, c->state[c->cur], rec * c->esize, cudaMemcpyDeviceToHost, c->stream),
+           "cudaMemcpyAsync D2H");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        for (int p = 0; p < NP27; ++p) {
+            const int o = rec27_off(p);
+            for (size_t n = 0; n < N; ++n)
+                state[(size_t)p * N + n] = mixed(c) ? (double)f[n * SL27 + o] : d[n * SL27 + o];
+        }
+        if (mixed(c)) {
+            // kept remainders folded into the exchanged populations: W_i (m + c_i.J/(s T_L))
+            // on f, W_i G on g
+            const double w1[3] = {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0};
+            for (size_t n = 0; n < N; ++n) {
+                const float *r = &f[n * SL27];
+                const double sq = std::sqrt((double)r[R_TH]);
+                const double m = r[R_MLO], gl = r[R_GLO];
+                const double J[3] = {r[R_JLO], r[R_JLO + 1], r[R_JLO + 2]};
+                for (int i = 0; i < Q27; ++i) {
+                    const int cx = i % 3 - 1, cy = (i / 3) % 3 - 1, cz = i / 9 - 1;
+                    const double w = w1[cx + 1] * w1[cy + 1] * w1[cz + 1];
+                    state[(size_t)i * N + n] += w * (m + (cx * J[0] + cy * J[1] + cz * J[2]) / (sq * (1.0 / 3.0)));
+                    state[(size_t)(Q27 + i) * N + n] += w * gl;
+                }
+            }
+        }
+        return POND_OK;
+    }
     if (c->lattice == POND_D2Q16) {
         // node records on the device, planes on the host
         const size_t N = c->N, rec = (size_t)SLQ * N;
@@ -683,6 +812,40 @@ pond_status pond_set_state(pond_ctx *c, const double *state)
     pond_status st = check_ctx(c);
     if (st) return st;
     if (!state) return fail(c, POND_EINVAL, "null input");
+    if (c->lattice == POND_D3Q27) {
+        const size_t N = c->N, rec = (size_t)SL27 * N;
+        std::vector<double> d(mixed(c) ? 0 : rec, 0.0);
+        std::vector<float> f(mixed(c) ? rec : 0, 0.0f);
+        for (int p = 0; p < NP27; ++p) {
+            const int o = rec27_off(p);
+            for (size_t n = 0; n < N; ++n) {
+                if (mixed(c)) f[n * SL27 + o] = (float)state[(size_t)p * N + n];
+                else d[n * SL27 + o] = state[(size_t)p * N + n];
+            }
+        }
+        if (mixed(c))
+            for (size_t n = 0; n < N; ++n) {
+                // what the FP32 populations leave out becomes the kept remainders again
+                float *r = &f[n * SL27];
+                const double sq = std::sqrt((double)r[R_TH]);
+                double m = 0.0, S[3] = {0, 0, 0}, gl = 0.0;
+                for (int i = 0; i < Q27; ++i) {
+                    const double rf = state[(size_t)i * N + n] - (double)r[R_F + i];
+                    m += rf;
+                    S[0] += rf * (i % 3 - 1); S[1] += rf * ((i / 3) % 3 - 1); S[2] += rf * (i / 9 - 1);
+                    gl += state[(size_t)(Q27 + i) * N + n] - (double)r[R_G + i];
+                }
+                r[R_MLO] = (float)m;
+                for (int a = 0; a < 3; ++a) r[R_JLO + a] = (float)(sq * S[a]);
+                r[R_GLO] = (float)gl;
+            }
+        const void *src = mixed(c) ? (const void *)f.data() : (const void *)d.data();
+        CK(cudaMemcpyAsync(c->state[c->cur], src, rec * c->esize, cudaMemcpyHostToDevice, c->stream),
+           "cudaMemcpyAsync H2D");
+        CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+        c->initialised = true;
+        return POND_OK;
+    }
     if (c->lattice == POND_D2Q16) {
         const size_t N = c->N, rec = (size_t)SLQ * N;
         std::vector<double> d(mixed(c) ? 0 : rec, 0.0);
@@ -950,6 +1113,7 @@ pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
     if (c->batch) return bfail(b, POND_EINVAL, "context already belongs to a batch");
     if (!c->initialised) return bfail(b, POND_EINVAL, "context state not initialised");
     if (c->nonlocal) return bfail(b, POND_EINVAL, "two-pass (current-time) contexts are stepped alone");
+    if (c->lattice == POND_D3Q27) return bfail(b, POND_EINVAL, "D3Q27 contexts are stepped alone");
     if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
     // the context's queued work (its initialisation) completes before the batch uses it

@@ -127,6 +127,64 @@ def droplet(n=512, Tr=0.85, radius=64.0, width=4.0, amp=1e-4, steps=20000, seed=
                     z.copy(), np.full((ny, n), Tr * t_cr()))
 
 
+@dataclasses.dataclass
+class Workload3:
+    """A three-dimensional (D3Q27) workload: fields of shape (nz, ny, nx)."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    bc_x: int
+    bc_y: int
+    bc_z: int
+    T_r: float
+    kappa: float
+    tau: float
+    dt: float
+    steps: int
+    rho: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    uz: np.ndarray
+    T: np.ndarray
+    a: float = A_VDW
+    b: float = B_VDW
+    R: float = R_GAS
+    delta: float = 1.0 / 3.0
+    k_cond: float = -1.0
+    p_floor: float = 0.05 / 6.0
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def fields(self):
+        return self.rho, self.ux, self.uy, self.uz, self.T
+
+
+def droplet3d(n=96, Tr=0.85, radius=20.0, width=4.0, amp=1e-4, steps=2000, seed=SEED, kappa=0.02,
+              tau=1.0, ny=None, nz=None, bc_z=0):
+    """Liquid sphere at the box centre in its vapour (D3Q27), periodic in x and y."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    rv, rl, dt = coexistence(Tr)
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(n) + 0.5, indexing="ij")
+    r = np.sqrt((x - n / 2) ** 2 + (y - ny / 2) ** 2 + (z - nz / 2) ** 2)
+    rho = (rv + (rl - rv) * 0.5 * (1.0 - np.tanh((r - radius) / width))) * (1.0 + noise(seed, (nz, ny, n), amp))
+    zero = np.zeros((nz, ny, n))
+    return Workload3("droplet3d%dx%dx%d" % (n, ny, nz), n, ny, nz, 0, 0, bc_z, Tr, kappa, tau, dt, steps,
+                     rho, zero, zero.copy(), zero.copy(), np.full((nz, ny, n), Tr * t_cr()))
+
+
+def from_workload3(w, precision="mixed", **kw):
+    """Keyword arguments of a D3Q27 ``pond.Simulation`` for a ``Workload3``."""
+    d = dict(bc_x=w.bc_x, bc_y=w.bc_y, bc_z=w.bc_z, nz=w.nz, a=w.a, b=w.b, R=w.R, delta=w.delta,
+             kappa=w.kappa, tau=w.tau, precision=precision, dt=w.dt, k_cond=w.k_cond, p_floor=w.p_floor,
+             lattice="d3q27")
+    d.update(kw)
+    return d
+
+
 def coexistence_slab(Tr=0.9, delta=1.0 / 3.0, advected=False, nx=256, ny=1, width=4.0, steps=8000,
                      kappa=0.02, tau=1.0):
     """A liquid slab over the middle half of a periodic box in its vapour at the Maxwell

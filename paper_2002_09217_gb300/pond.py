@@ -16,8 +16,8 @@ import numpy as np
 from . import build_lib
 
 POND_PERIODIC, POND_ZEROGRAD = 0, 1
-POND_D2Q9, POND_D2Q16 = 0, 1
-LATTICES = {"d2q9": POND_D2Q9, "d2q16": POND_D2Q16}
+POND_D2Q9, POND_D2Q16, POND_D3Q27 = 0, 1, 2
+LATTICES = {"d2q9": POND_D2Q9, "d2q16": POND_D2Q16, "d3q27": POND_D3Q27}
 POND_VDW, POND_IDEAL, POND_DIETERICI, POND_SIMPLIFIED = 0, 1, 2, 3
 POND_FP64, POND_MIXED = 0, 1
 NPLANES = 25
@@ -29,7 +29,8 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
 class Grid(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32)]
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
+                ("nz", C.c_int32), ("bc_z", C.c_int32)]
 
 
 class Lattice(C.Structure):
@@ -84,6 +85,8 @@ def load() -> C.CDLL:
         lib.pond_create.argtypes = [C.POINTER(Grid), C.POINTER(Lattice), C.POINTER(Eos), C.c_double,
                                     C.c_double, C.POINTER(Opts), C.POINTER(P)]
         for name, args in [("pond_init_fields", [P, dp, dp, dp, dp]),
+                           ("pond_init_fields3", [P, dp, dp, dp, dp, dp]),
+                           ("pond_moments3", [P, dp, dp, dp, dp, dp, dp]),
                            ("pond_init_fields_device", [P, P, P, P, P]),
                            ("pond_step", [P, C.c_int64]),
                            ("pond_moments", [P, dp, dp, dp, dp, dp]),
@@ -152,11 +155,12 @@ class Simulation:
                  stream=None, torch_alloc: bool = True, ideal: bool = False,
                  lanes_per_node: int = 0, tile_x: int = 0, eos: str = "vdw",
                  isothermal: bool = False, T_iso: float = 0.0, nonlocal_: str = "lagged",
-                 eos_params: tuple = (), lattice: str = "d2q9"):
+                 eos_params: tuple = (), lattice: str = "d2q9", nz: int = 1,
+                 bc_z: int = POND_PERIODIC):
         torch = _torch()
         self._lib = load()
-        self.nx, self.ny = int(nx), int(ny)
-        self.N = self.nx * self.ny
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
         self.precision = precision
         if precision not in ("mixed", "fp64"):
             raise ValueError("precision must be 'mixed' or 'fp64'")
@@ -184,12 +188,14 @@ class Simulation:
             self._cb_alloc, self._cb_free = _ALLOC(_alloc), _FREE(_free)
         else:
             self._cb_alloc, self._cb_free = _ALLOC(), _FREE()
-        grid = Grid(self.nx, self.ny, bc_x, bc_y)
+        grid = Grid(self.nx, self.ny, bc_x, bc_y, self.nz, bc_z)
         if lattice not in LATTICES:
-            raise ValueError("lattice must be 'd2q9' or 'd2q16'")
+            raise ValueError("lattice must be 'd2q9', 'd2q16' or 'd3q27'")
         lat = Lattice(LATTICES[lattice])
         self.lattice = lattice
-        self.nplanes = 2 * (9 if lattice == "d2q9" else 16) + 7
+        self.nplanes = {"d2q9": 25, "d2q16": 39, "d3q27": 63}[lattice]
+        # host arrays: (ny, nx) on the two-dimensional lattices, (nz, ny, nx) on D3Q27
+        self.shape = (self.nz, self.ny, self.nx) if lattice == "d3q27" else (self.ny, self.nx)
         if eos not in ("vdw", "dieterici", "simplified"):
             raise ValueError("eos must be 'vdw', 'dieterici' or 'simplified'")
         kind = {"dieterici": POND_DIETERICI, "simplified": POND_SIMPLIFIED}.get(
@@ -218,12 +224,17 @@ class Simulation:
             raise PondError(st, self._lib.pond_last_error(self._ctx).decode())
 
     def _host(self, x) -> np.ndarray:
-        a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), (self.ny, self.nx)))
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), self.shape))
         return a
 
     # -- API ---------------------------------------------------------------
-    def init_fields(self, rho, ux, uy, T):
-        """Host numpy arrays (ny, nx) or CUDA float64 tensors."""
+    def init_fields(self, rho, ux, uy, T, uz=None):
+        """Host numpy arrays (ny, nx) ((nz, ny, nx) on D3Q27) or CUDA float64 tensors;
+        uz (host, D3Q27) defaults to zero."""
+        if uz is not None:
+            arrs = [self._host(v) for v in (rho, ux, uy, uz, T)]
+            self._check(self._lib.pond_init_fields3(self._ctx, *[_dptr(a) for a in arrs]))
+            return
         if hasattr(rho, "is_cuda") and rho.is_cuda:
             ts = [t.contiguous() for t in (rho, ux, uy, T)]
             self._check(self._lib.pond_init_fields_device(self._ctx, *[C.c_void_p(t.data_ptr()) for t in ts]))
@@ -241,6 +252,10 @@ class Simulation:
         return float(out[0])
 
     def moments(self) -> dict:
+        if self.lattice == "d3q27":
+            outs = [np.empty(self.shape) for _ in range(6)]
+            self._check(self._lib.pond_moments3(self._ctx, *[_dptr(o) for o in outs]))
+            return dict(zip(("rho", "ux", "uy", "uz", "T", "p"), outs))
         outs = [np.empty((self.ny, self.nx)) for _ in range(5)]
         self._check(self._lib.pond_moments(self._ctx, *[_dptr(o) for o in outs]))
         return dict(zip(("rho", "ux", "uy", "T", "p"), outs))
@@ -257,12 +272,12 @@ class Simulation:
         return out
 
     def get_state(self) -> np.ndarray:
-        out = np.empty((self.nplanes, self.ny, self.nx))
+        out = np.empty((self.nplanes,) + self.shape)
         self._check(self._lib.pond_get_state(self._ctx, _dptr(out)))
         return out
 
     def set_state(self, state):
-        s = np.ascontiguousarray(np.asarray(state, dtype=np.float64).reshape(self.nplanes, self.ny, self.nx))
+        s = np.ascontiguousarray(np.asarray(state, dtype=np.float64).reshape((self.nplanes,) + self.shape))
         self._check(self._lib.pond_set_state(self._ctx, _dptr(s)))
 
     def stats(self, reset: bool = False) -> dict:
