@@ -61,27 +61,20 @@ __device__ __forceinline__ A sel3(const A (&v)[3], int k)
 template <typename A>
 __device__ __forceinline__ void inc_row3(int k, const A (&eps)[3], A (&out)[3])
 {
-    // l_k(xi) = prod_{m != k} (xi - c_m) / (c_k - c_m), c = -1, 0, 1
-    const A ck = A(k - 1);
-    A diag;
-    {
-        const A ek = sel3(eps, k);
-        // the two other nodes o0 < o1
-        const A o0 = k == 0 ? A(0) : A(-1), o1 = k == 2 ? A(0) : A(1);
-        const A t0 = ek / (ck - o0), t1 = ek / (ck - o1);
-        diag = (t0 + t1) + t0 * t1;
-    }
+    // l_k(xi) = prod_{m != k} (xi - c_m) / (c_k - c_m), c = -1, 0, 1: the inverse
+    // denominators (1/2, -1, 1/2) and 1/(c_k - o_m) are exact binary constants
+    const A id = k == 1 ? A(-1) : A(0.5);
+    const A r0 = k == 0 ? A(-1) : (k == 1 ? A(1) : A(0.5));     // 1/(c_k - o0), o0 < o1
+    const A r1 = k == 0 ? A(-0.5) : (k == 1 ? A(-1) : A(1));    // 1/(c_k - o1)
+    const A ek = sel3(eps, k);
+    const A t0 = ek * r0, t1 = ek * r1;
+    const A diag = (t0 + t1) + t0 * t1;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const A cj = A(j - 1);
-        A num = A(1), den = A(1);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            if (m == k) continue;
-            num *= (cj - A(m - 1)) + eps[j];
-            den *= ck - A(m - 1);
-        }
-        out[j] = j == k ? diag : num / den;
+        // the factors (c_j - c_m) + eps_j for m = 0, 1, 2 (the one with m = j is eps_j)
+        const A f0 = A(j) + eps[j], f1 = A(j - 1) + eps[j], f2 = A(j - 2) + eps[j];
+        const A prod = k == 0 ? f1 * f2 : (k == 1 ? f0 * f2 : f0 * f1);
+        out[j] = j == k ? diag : id * prod;
     }
 }
 
@@ -90,8 +83,8 @@ __device__ __forceinline__ void cubic_w(A xi, A a[4])
 {
     const A x0 = xi, x1 = xi - A(1), x2 = xi - A(2), x3 = xi - A(3);
     a[0] = -(x1 * x2 * x3) / A(6);
-    a[1] = (x0 * x2 * x3) / A(2);
-    a[2] = -(x0 * x1 * x3) / A(2);
+    a[1] = (x0 * x2 * x3) * A(0.5);
+    a[2] = -(x0 * x1 * x3) * A(0.5);
     a[3] = (x0 * x1 * x2) / A(6);
 }
 
