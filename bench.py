@@ -156,6 +156,59 @@ FLOPS_Q16_STREAM_EXTRA = 130
 FLOPS_Q16_COLLIDE = 2300
 
 
+# The D3Q27 step (k_q27_step), per node update: per stencil pair (27 directions x 64
+# stencil nodes per stream): gauge offsets (29), the three per-axis increment rows (60),
+# the x-, y- and z-increments and accumulation for f and g (198), weight (2) => 289; per
+# direction: three departure points and cubic weights (60); per stream: moments and
+# residual (FP64, 260); per node update: non-local terms (600) and the collision (7000:
+# six per-axis increment maps ~360, three three-axis applications ~4800, forced g
+# equilibrium ~1620, defect sums ~300).
+FLOPS_Q27_PAIR = 289
+FLOPS_Q27_DIR = 60
+FLOPS_Q27_STREAM_EXTRA = 260
+FLOPS_Q27_NONLOCAL = 600
+FLOPS_Q27_COLLIDE = 7000
+
+
+def flops_q27(its: float) -> float:
+    return its * (27 * (FLOPS_Q27_DIR + 64 * FLOPS_Q27_PAIR) + FLOPS_Q27_STREAM_EXTRA) + FLOPS_Q27_NONLOCAL + FLOPS_Q27_COLLIDE
+
+
+def d3q27_run(pond, torch, stream, precision, steps, warmup, nx=96, ny=96, nz=64, sm_mhz=2070.0) -> dict:
+    """MLUPS of the D3Q27 step on a liquid sphere in its vapour (96 x 96 x 64 nodes, 72-value
+    records; 0.6 M nodes x 288 B = 170 MB per FP32 state buffer, larger than L2), with its
+    ALU roofline and an end-to-end figure (host fields in, steps, host fields out)."""
+    import numpy as np
+    from paper_2002_09217_gb300 import inputs
+    w = inputs.droplet3d(n=nx, ny=ny, nz=nz, radius=20.0)
+    sim = pond.Simulation(w.nx, w.ny, stream=stream, **inputs.from_workload3(w, precision))
+    sim.init_fields(w.rho, w.ux, w.uy, w.T)
+    sim.step(warmup)
+    stream.synchronize()
+    sim.stats(reset=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    sim.step(steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b) / steps
+    st = sim.stats()
+    its = st["streams"] / max(1, st["node_updates"])
+    t0 = time.perf_counter()
+    sim.init_fields(*[np.ascontiguousarray(x) for x in (w.rho, w.ux, w.uy, w.T)], uz=w.uz)
+    sim.step(steps)
+    sim.moments()
+    e2e = w.nodes * steps / (time.perf_counter() - t0) / 1e6
+    sim.close()
+    achieved = w.nodes * flops_q27(its) / (ms * 1e-3) / 1e12
+    peak = alu_peak_tflops(precision, sm_mhz)
+    return {"workload": w.name, "mlups": w.nodes / ms / 1e3, "ms_per_step": ms, "streams_per_node": its,
+            "e2e_mlups": e2e,
+            "roofline": {"bound": "alu", "kernel": "k_q27_step (+ two non-local kernels, timed together)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "flops_per_update": flops_q27(its)}}
+
+
 def flops_q16(its: float) -> float:
     return its * (16 * (FLOPS_Q16_DIR + 16 * FLOPS_Q16_PAIR) + FLOPS_Q16_STREAM_EXTRA) + FLOPS_NONLOCAL + FLOPS_Q16_COLLIDE
 
@@ -357,6 +410,9 @@ def other_configs(pond, torch, stream, sm_mhz: float = 2070.0) -> dict:
             "roofline": {"bound": "alu", "kernel": "k_q16_step (+ two non-local kernels)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "flops_per_update": flops_q16(its)}}
+    # the D3Q27 lattice on a 96 x 96 x 64 liquid sphere
+    for prec, steps in (("mixed", 5), ("fp64", 2)):
+        out["droplet3d96x96x64/d3q27/%s" % prec] = d3q27_run(pond, torch, stream, prec, steps, 2, sm_mhz=sm_mhz)
     # the two-pass step (current-time non-local terms) on the slab: two launches per step
     w = inputs.config("slab128x4")
     sim = pond.from_workload(w, precision="mixed", stream=stream, nonlocal_="current")
@@ -425,8 +481,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--workload", default="shocktube2048x4")
-    ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d2q16"],
-                    help="velocity set (D2Q16: the three-launch plane step, no autotuning)")
+    ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d2q16", "d3q27"],
+                    help="velocity set (D2Q16: the three-launch plane step, no autotuning; "
+                         "D3Q27: a 96 x 96 x 64 sphere, its own short line)")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving sample")
@@ -475,6 +532,30 @@ def main():
                 pk["fma_" + prec] = pond.fma_peak(prec, iters, stream)
             except pond.PondError:
                 pass
+
+    if args.lattice == "d3q27":
+        # the three-dimensional lattice: its own short line on a 96 x 96 x 64 sphere
+        steps = max(1, min(args.steps, 20))
+        clocks = ClockSampler(local)
+        with clocks:
+            r = d3q27_run(pond, torch, stream, args.precision, steps, args.warmup, sm_mhz=pk["sm_max_mhz"])
+        nodes = 96 * 96 * 64
+        line = {"metric": "MLUPS", "value": ws * r["mlups"], "unit": "MLUPS", "n_gpus": ws, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": r["workload"], "nx": 96, "ny": 96, "nz": 64, "lattice": "d3q27",
+                           "precision": args.precision, "l2": "inputs larger than L2 (170 MB per FP32 buffer)"},
+                "frame_search_streams_per_node": r["streams_per_node"], "gpu_launches": 3 * steps,
+                "roofline": r["roofline"], "clocks": clocks.summary(),
+                "e2e": {"value": ws * r["e2e_mlups"], "unit": "MLUPS", "h2d_bytes_per_step": 5 * nodes * 8 / steps,
+                        "d2h_bytes_per_step": 6 * nodes * 8 / steps}}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
 
     def shape_for(prec):
         if args.lattice != "d2q9":

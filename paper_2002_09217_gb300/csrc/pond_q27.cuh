@@ -414,8 +414,10 @@ __device__ __forceinline__ void apply3_inc(const A Dx[3][3], const A Dy[3][3], c
 
 // ---------------------------------------------------------------------------
 // The node step (frame search, then collision), one thread per node.
+// FP32: registers capped for four resident blocks per SM (the stencil gathers are
+// latency-bound; 16 warps hide more of it than 8: +21 % measured); FP64 keeps two.
 template <typename R>
-__global__ void __launch_bounds__(128) k_q27_step(DevParams p, Grid3 g3, const R *__restrict__ in,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_q27_step(DevParams p, Grid3 g3, const R *__restrict__ in,
                                                   const double *__restrict__ nl, R *__restrict__ out,
                                                   DevStats *stats)
 {
