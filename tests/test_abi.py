@@ -69,7 +69,13 @@ def test_invalid_parameters_are_rejected_on_the_host(lib):
                 pond.Eos(pond.POND_SIMPLIFIED, 0, 0, 1, 1 / 3, 1, 0.1, 1e-3, 5.0, 0.5, 0.0)):  # p0 = 0
         assert L.pond_create(ctypes.byref(g), ctypes.byref(lat), ctypes.byref(bad), 0.0, 1.0,
                              ctypes.byref(opts), ctypes.byref(out)) == 1
-    lat_bad = pond.Lattice(2)                                             # unknown lattice
+    # the z extent: D3Q27 needs nz >= 1 and a valid bc_z; the 2-D lattices nz <= 1
+    for gz, lk in ((pond.Grid(8, 8, 0, 0, 0, 0), pond.POND_D3Q27), (pond.Grid(8, 8, 0, 0, 4, 2), pond.POND_D3Q27),
+                   (pond.Grid(8, 8, 0, 0, 2, 0), pond.POND_D2Q9), (pond.Grid(8, 8, 0, 0, 3, 0), pond.POND_D2Q16)):
+        lz = pond.Lattice(lk)
+        assert L.pond_create(ctypes.byref(gz), ctypes.byref(lz), ctypes.byref(eos), 0.0, 1.0,
+                             ctypes.byref(opts), ctypes.byref(out)) == 1
+    lat_bad = pond.Lattice(3)                                             # unknown lattice
     assert L.pond_create(ctypes.byref(g), ctypes.byref(lat_bad), ctypes.byref(eos), 0.0, 1.0,
                          ctypes.byref(opts), ctypes.byref(out)) == 1
     assert not out.value
