@@ -502,6 +502,37 @@ def main():
 
     w = workload(args.workload)
 
+    if args.impl == "reference" and args.lattice == "d3q27":
+        # the 3-D oracle on a bounded sample of the 96 x 96 x 64 sphere: one step of 2,000
+        # nodes (the whole grid's moments and non-local terms included)
+        if rank == 0:
+            import numpy as np
+            from oracle import core3d
+            from paper_2002_09217_gb300 import inputs
+            w3 = inputs.droplet3d(n=96, ny=96, nz=64, radius=20.0)
+            P3 = core3d.Params3(nx=w3.nx, ny=w3.ny, nz=w3.nz, a=w3.a, b=w3.b, R=w3.R, delta=w3.delta,
+                                kappa=w3.kappa, tau=w3.tau, k_cond=w3.k_cond, p_floor=w3.p_floor,
+                                tol=1e-12, dt=w3.dt)
+            st = core3d.init_state(P3, *w3.fields())
+            nodes = np.random.default_rng(3).choice(w3.nodes, 2000, replace=False)
+            t0 = time.perf_counter()
+            core3d.step_nodes(P3, st, nodes)
+            el = time.perf_counter() - t0
+            v = len(nodes) / el / 1e6
+            import oracle
+            line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": ws,
+                    "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                    "dtype": "f64", "data": "synthetic",
+                    "config": {"workload": w3.name, "nx": w3.nx, "ny": w3.ny, "nz": w3.nz, "lattice": "d3q27"},
+                    "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                                     "sample": "one step of 2,000 sampled nodes of the 96x96x64 sphere (3-D FP64 oracle)"},
+                    "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
     if args.impl == "reference":
         if rank == 0:
             steps = max(1, min(args.steps, 20))
