@@ -296,7 +296,6 @@ __device__ void q27_stream(const DevParams &p, const Grid3 &g3, const R *__restr
                     tz[jz] = sel3(bb, iy) + sel3(xx, iy) + a;
                 }
                 const R zinc = Dz[0] * tz[0] + Dz[1] * tz[1] + Dz[2] * tz[2];
-                const R bz[3] = {b[0][0], b[1][0], b[2][0]};
                 // [G f]_i - ref = (f_i - ref) + x-inc + y-inc + z-inc of row (iz, iy)
                 R bi, xi_, yi;
                 {
@@ -310,7 +309,6 @@ __device__ void q27_stream(const DevParams &p, const Grid3 &g3, const R *__restr
                     xi_ = sel3(xsel, iz);
                     yi = sel3(yz, iz);
                 }
-                (void)bz;
                 const R ref = pg == 0 ? refF : refG;
                 const R dv = ((bi - ref) + xi_) + yi + zinc;
                 if (pg == 0) sf += wgt * dv;
