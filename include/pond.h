@@ -201,7 +201,8 @@ pond_status pond_moments_device(pond_ctx *ctx, double *d_rho, double *d_ux, doub
                                 double *d_T, double *d_p);
 
 /* Global sums in FP64 with compensated summation: out = {sum rho, sum rho uhat_x,
- * sum rho uhat_y, sum_nodes sum_i g_i / 2 (total energy)}.  Synchronises. */
+ * sum rho uhat_y, sum_nodes sum_i g_i / 2 (total energy)}, the kept FP32 energy
+ * remainders included; on D3Q27 the z momentum is not among them.  Synchronises. */
 pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 
 /* Full state as 2Q + 7 host planes of nx*ny doubles (25 on D2Q9, 39 on D2Q16):
