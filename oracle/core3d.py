@@ -84,6 +84,9 @@ def _load():
         lib.orc3_step.restype = C.c_int
         lib.orc3_step_nodes.argtypes = [pp, dp, C.POINTER(C.c_int64), C.c_int64, dp]
         lib.orc3_step_nodes.restype = C.c_int
+        lib.orc3_macro.argtypes = [pp, dp, dp, dp, dp, C.c_double, dp]
+        lib.orc3_collide.argtypes = [pp, dp, dp, dp, dp, dp, C.c_double, dp, dp]
+        lib.orc3_collide.restype = C.c_int
         _lib = lib
     return _lib
 
@@ -155,6 +158,27 @@ def step_nodes(P: Params3, state, nodes) -> np.ndarray:
                                len(nodes), _p(out)):
         raise FloatingPointError("oracle step failed (singular moment matrix)")
     return out
+
+
+def macro(P: Params3, lam, ft, gt, F=(0.0, 0.0, 0.0), rEl=0.0) -> dict:
+    """Macroscopic fields of streamed populations in gauge lam = (theta, ux, uy, uz)."""
+    out = np.zeros(13)
+    cp = P.c()
+    _load().orc3_macro(C.byref(cp), _p(_d(lam)), _p(_d(ft)), _p(_d(gt)), _p(_d(F)), float(rEl), _p(out))
+    keys = ["rho", "ux", "uy", "uz", "uhx", "uhy", "uhz", "E", "e", "T", "p", "P", "theta"]
+    return dict(zip(keys, out.tolist())) | {"_raw": out}
+
+
+def collide(P: Params3, lam, ft, gt, mac, F=(0.0, 0.0, 0.0), M0=0.0):
+    """Post-collision f, g (27 each) in the streaming gauge lam."""
+    fo = np.zeros(Q)
+    go = np.zeros(Q)
+    raw = mac["_raw"] if isinstance(mac, dict) else _d(mac)
+    cp = P.c()
+    if _load().orc3_collide(C.byref(cp), _p(_d(lam)), _p(_d(ft)), _p(_d(gt)), _p(_d(raw)), _p(_d(F)),
+                            float(M0), _p(fo), _p(go)):
+        raise ValueError("singular moment matrix")
+    return fo, go
 
 
 def moments(P: Params3, state) -> dict:

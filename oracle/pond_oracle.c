@@ -24,7 +24,7 @@
  * The transfer matrix is deliberately computed from its definition with an LU
  * solve of the 9x9 moment system, not from any closed form.
  *
- * Readings of points the paper leaves open (listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - frame search: predictor = previous-step gauge; corrector = re-stream with the
  *     gauge (max(p,p_floor)/(rho T_L), u) from the streamed moments; stop when the
  *     relative change is <= tol or after max_iter streams.  The node keeps the last

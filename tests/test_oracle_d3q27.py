@@ -190,3 +190,39 @@ def test_galilean_boost_along_z_is_a_shift():
     for k, bar in (("rho", 1e-11), ("ux", 1e-12), ("uy", 1e-12), ("uz", 1e-11), ("T", 1e-8)):
         gap = np.abs(np.roll(a[k], 1, axis=0) - (b[k] - (U if k == "uz" else 0.0))).max()
         assert gap < bar, (k, gap)
+
+
+@pytest.mark.parametrize("force", [(0.07, -0.04, 0.05), (0.0, 0.11, -0.03)])
+def test_forced_g_equilibrium_second_moment_is_the_paper_R_in_3d(force):
+    """The forced g equilibrium's second moment in three dimensions (SM, Chapman-Enskog
+    with force, the modified equilibrium moments; reading R18 for the 3-D tensors):
+    sum g^eq v_a v_b = 2 rho uhat_a uhat_b (H + P/rho) + 2 P H delta_ab for all nine
+    (a, b), with omega = 1, M_0 = 0 and the force-work source phi (2 W_i uhat.F in the
+    co-moving frame) removed.  Also the zeroth and first moments 2 rho E, 2 rho uhat H."""
+    rng = np.random.default_rng(2718)
+    w = o3.weights()
+    P = o3.Params3(nx=4, ny=4, nz=4, tau=1.0, dt=0.6)
+    lam = np.array([0.19, 0.11, -0.06, 0.04])
+    rho = 2.9
+    f = rho * w * (1.0 + 0.05 * rng.uniform(-1, 1, 27))
+    g = f * 0.4 * (1.0 + 0.05 * rng.uniform(-1, 1, 27))
+    mac = o3.macro(P, lam, f, g, force, 0.002)
+    assert mac["p"] > P.p_floor
+    _, go = o3.collide(P, lam, f, g, mac, force, 0.0)
+    s = math.sqrt(lam[0])
+    c = np.array([[i % 3 - 1, (i // 3) % 3 - 1, i // 9 - 1] for i in range(27)], dtype=float)
+    v = s * c + lam[1:][None, :]
+    rho_, E, Pg = mac["rho"], mac["E"], mac["P"]
+    uh = np.array([mac["uhx"], mac["uhy"], mac["uhz"]])
+    u = np.array([mac["ux"], mac["uy"], mac["uz"]])
+    H = E + Pg / rho_
+    work = 2.0 * float(uh @ np.asarray(force))
+    assert go.sum() - P.dt * work == pytest.approx(2 * rho_ * E, rel=1e-12)
+    for a in range(3):
+        q_a = (go * v[:, a]).sum() - P.dt * work * u[a]
+        assert q_a == pytest.approx(2 * rho_ * uh[a] * H, rel=1e-10, abs=1e-14)
+        for b in range(3):
+            phi_ab = work * ((Pg / rho_) * (a == b) + u[a] * u[b])
+            R_ab = (go * v[:, a] * v[:, b]).sum() - P.dt * phi_ab
+            want = 2 * rho_ * uh[a] * uh[b] * (H + Pg / rho_) + 2 * Pg * H * (a == b)
+            assert R_ab == pytest.approx(want, rel=1e-11, abs=1e-14), (a, b)

@@ -301,6 +301,44 @@ def test_forced_g_equilibrium_carries_uhat_H_flux():
     assert geq_vx == pytest.approx(2 * rho * mac["uhx"] * H, rel=1e-10)
 
 
+@pytest.mark.parametrize("lattice", ["d2q9", "d2q16"])
+@pytest.mark.parametrize("force", [(0.09, -0.05), (-0.02, 0.13), (0.0, 0.0)])
+def test_forced_g_equilibrium_second_moment_is_the_paper_R(lattice, force):
+    """Second moment of the forced g equilibrium (SM, Chapman-Enskog with force, the
+    modified equilibrium moments): R_ab = sum g^eq v_a v_b
+    = 2 rho uhat_a uhat_b (H + P/rho) + 2 P H delta_ab, with H = E + P/rho and E the
+    total energy per mass (reading R8).  The force tensor I = uhat F + F uhat +
+    dt F F E/(2P) inside M and N cancels from the zeroth and first moments but not from
+    this one: a wrong factor, a dropped F F term or a missing off-diagonal entry of I
+    changes R.  The force is strong enough for the dt^2 F F part to count (about 0.5 %
+    of R_xx).  Checked with omega = 1, M_0 = 0 and the phi source (2 W_i uhat.F in the
+    co-moving frame, second moment work (P/rho delta + u u)) removed."""
+    rng = np.random.default_rng(5150)
+    W_l = oracle.weights(lattice)
+    Q = len(W_l)
+    P = oracle.Params(nx=4, ny=4, tau=1.0, dt=0.7, lattice=lattice)
+    lam = np.array([0.21 if lattice == "d2q9" else 0.07, 0.13, -0.07])
+    rho = 3.1
+    f = rho * W_l * (1.0 + 0.05 * rng.uniform(-1, 1, Q))
+    g = f * 0.4 * (1.0 + 0.05 * rng.uniform(-1, 1, Q))
+    mac = oracle.macro(P, lam, f, g, force[0], force[1], 0.002)
+    assert mac["p"] > P.p_floor   # the case uses the van der Waals pressure itself
+    _, go = oracle.collide(P, lam, f, g, mac, force[0], force[1], 0.0)
+    vx, vy = oracle.velocities(lam, lattice)
+    rho_, E, Pg = mac["rho"], mac["E"], mac["P"]
+    uh = np.array([mac["uhx"], mac["uhy"]])
+    u = np.array([mac["ux"], mac["uy"]])
+    H = E + Pg / rho_
+    work = 2.0 * (uh[0] * force[0] + uh[1] * force[1])
+    v = (vx, vy)
+    for a in range(2):
+        for b in range(2):
+            phi_ab = work * ((Pg / rho_) * (a == b) + u[a] * u[b])
+            R_ab = (go * v[a] * v[b]).sum() - P.dt * phi_ab
+            want = 2 * rho_ * uh[a] * uh[b] * (H + Pg / rho_) + 2 * Pg * H * (a == b)
+            assert R_ab == pytest.approx(want, rel=1e-11, abs=1e-14), (a, b)
+
+
 # ------------------------------------------------------------- whole step
 @pytest.mark.parametrize("u", [(0.0, 0.0), (0.37, -0.21), (-1.3, 0.8)])
 def test_uniform_state_is_stationary_for_any_velocity(u):
