@@ -1,21 +1,26 @@
 """Benchmark of the PonD van der Waals time step on GB300.
 
-Workload (default): the supercritical real-gas shock tube, 2048 x 4 nodes,
-T = 1.1 T_cr, density ratio 4 with a tanh step of width 4, zero-gradient ends in x.
-One bench "step" = one time step of the whole hot path (non-local terms, frame search
-with streaming, collision: one launch of the fused step kernel) over the grid.
-Metric: MLUPS (million node updates per second) in the mixed FP32/FP64 form; the plain
-FP64 form, a bounded continuous-batching serving sample and the FP64 CPU oracle are
+Workload (default): the droplet-shock interaction, 2048 x 1024 nodes, T = 0.8 T_cr, a
+liquid droplet of radius 80 at x = 600 hit by a Mach 1.5 shock (Rankine-Hugoniot state of
+the van der Waals fluid) from x = 300, zero-gradient boundaries: the largest single-GPU
+workload.  One bench "step" = one time step of the whole hot path (non-local terms,
+frame search with streaming, collision: one launch of the fused step kernel) over the
+grid.  Metric: MLUPS (million node updates per second) in the mixed FP32/FP64 form; the
+plain FP64 form of the same workload (its own roofline), the shock tube and the other
+workloads, a bounded continuous-batching serving sample and the FP64 CPU oracle are
 reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
-                  [--impl reference] [--no-cpu] [--no-serving] [--no-autotune]
+                  [--workload NAME] [--impl reference] [--no-cpu] [--no-serving]
+                  [--no-autotune] [--no-extras]
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events on the
-simulation's stream, with the L2 flushed (a 512 MiB buffer written) between timed steps
-because the state (about 1 MB) is far smaller than L2.  The launch shape (lanes per node,
-tile shape) comes from the autotuner.  Under torchrun (N > 1) each rank runs an
-independent replica (the workload does not shard) and the slowest rank's time counts.
+simulation's stream.  The 2048 x 1024 state (268 MB per FP32 buffer) is larger than L2;
+for workloads whose state fits in L2 a 512 MiB buffer is written between timed steps.
+A step is one kernel launch, so the roofline's kernel time is the same per-step event
+time.  The launch shape (lanes per node, tile shape) comes from the autotuner.  Under
+torchrun (N > 1) each rank runs an independent replica (the workload does not shard) and
+the slowest rank's time counts.
 """
 from __future__ import annotations
 
@@ -257,8 +262,18 @@ def oracle_mlups(w, steps: int, lattice: str = "d2q9") -> dict:
                       % (steps, w.nx, w.ny, lattice.upper()), "state": st, "params": P}
 
 
+L2_BYTES = 129e6
+
+
+def state_bytes(w, precision: str) -> float:
+    """Bytes of one state buffer (32-value records) of a D2Q9 workload."""
+    return w.nodes * 32 * (4 if precision == "mixed" else 8)
+
+
 def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws):
-    """Timed steps of one precision form: per-step CUDA events, L2 flushed between."""
+    """Timed steps of one precision form: per-step CUDA events; the L2 is flushed between
+    timed steps when the state fits in it.  Returns the per-step times, the counters and
+    the mean kernel time (the step is one launch: the same events)."""
     sim = pond.from_workload(w, precision=precision, stream=stream, **shape)
     dev_fields = [torch.tensor(a, device=stream.device, dtype=torch.float64) for a in w.fields()]
     with torch.cuda.stream(stream):
@@ -272,24 +287,19 @@ def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws)
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
+    do_flush = state_bytes(w, precision) < 2 * L2_BYTES
     with torch.cuda.stream(stream):
         for k in range(steps):
-            flush.fill_(float(k))
+            if do_flush:
+                flush.fill_(float(k))
             evs[k][0].record(stream)
             sim.step(1)
             evs[k][1].record(stream)
     torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in evs]
     st = sim.stats()
-    # the kernel alone, timed by the library with events around its launch
-    kms = 0.0
-    reps = min(steps, 50)
-    for k in range(reps):
-        with torch.cuda.stream(stream):
-            flush.fill_(float(k))
-        kms += sim.step_timed() / reps
     sim.close()
-    return ms, st, kms
+    return ms, st, sum(ms) / len(ms)
 
 
 def roofline(w, precision, its, kernel_ms, pk, lattice="d2q9"):
@@ -364,23 +374,27 @@ def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
     return summ
 
 
-def other_configs(pond, torch, stream, sm_mhz: float = 2070.0) -> dict:
-    """MLUPS of the other full-size workloads (mixed form, default launch shape, a few
-    back-to-back steps after warm-up; the larger ones exceed L2 by themselves)."""
+def other_configs(pond, torch, stream, sm_mhz: float = 2070.0, skip: str = "") -> dict:
+    """MLUPS of the other full-size workloads (default launch shape, a few back-to-back
+    steps after warm-up; the larger ones exceed L2 by themselves), both forms."""
     from paper_2002_09217_gb300 import inputs
     out = {}
-    for name, steps in (("slab128x4", 200), ("droplet512x512", 20), ("dropletshock2048x1024", 10)):
+    for name, steps in (("slab128x4", 200), ("shocktube2048x4", 200), ("droplet512x512", 20),
+                        ("dropletshock2048x1024", 10)):
+        if name == skip:
+            continue
         w = inputs.config(name)
-        for prec in ("mixed", "fp64") if name == "slab128x4" else ("mixed",):
+        for prec in ("mixed", "fp64"):
+            n = steps if prec == "mixed" or w.nodes < 10000 else max(3, steps // 5)
             sim = pond.from_workload(w, precision=prec, stream=stream)
             sim.init_fields(*w.fields())
             sim.step(3)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            sim.step(steps)
+            sim.step(n)
             b.record(stream)
             b.synchronize()
-            ms = a.elapsed_time(b) / steps
+            ms = a.elapsed_time(b) / n
             st = sim.stats()
             sim.close()
             out["%s/%s" % (name, prec)] = {"mlups": w.nodes / ms / 1e3, "ms_per_step": ms,
@@ -480,7 +494,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--workload", default="shocktube2048x4")
+    ap.add_argument("--workload", default="dropletshock2048x1024")
     ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d2q16", "d3q27"],
                     help="velocity set (D2Q16: the three-launch plane step, no autotuning; "
                          "D3Q27: a 96 x 96 x 64 sphere, its own short line)")
@@ -535,12 +549,15 @@ def main():
 
     if args.impl == "reference":
         if rank == 0:
-            steps = max(1, min(args.steps, 20))
+            # full-grid oracle steps, bounded: a 2048 x 1024 step takes ~10 s on 16 cores
+            steps = max(1, min(args.steps, 20 if w.nodes < 100000 else 3))
             res = oracle_mlups(w, steps, args.lattice)
             line = {"impl": "reference", "metric": "MLUPS", "value": res["value"], "unit": "MLUPS",
                     "n_gpus": ws, "steps": steps, "warmup": 1, "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                    "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt},
+                    "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt, "precision": "fp64",
+                               "launch_shape": "n/a (CPU oracle)", "lattice": args.lattice,
+                               "l2": "n/a (CPU)", "parallelism": "replicas" if ws > 1 else "single"},
                     "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")},
                     "e2e": {"value": res["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                             "d2h_bytes_per_step": 0}}
@@ -597,6 +614,7 @@ def main():
         return {"lanes_per_node": best["lanes_per_node"], "tile_x": best["tile_x"]}
 
     shape = shape_for(args.precision)
+    big = state_bytes(w, args.precision) >= 2 * L2_BYTES
     clocks = ClockSampler(local)
     with clocks:
         ms, st, kms = run_form(w, pond, torch, stream, flush, args.precision, args.steps,
@@ -619,7 +637,8 @@ def main():
         "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt, "precision": args.precision,
                    "launch_shape": shape or "default", "lattice": args.lattice,
-                   "l2": "flushed between timed steps (512 MiB write)",
+                   "l2": ("inputs larger than L2 (%.0f MB per state buffer)" % (state_bytes(w, args.precision) / 1e6)
+                          if big else "flushed between timed steps (512 MiB write)"),
                    "parallelism": "replicas" if ws > 1 else "single"},
         "frame_search_streams_per_node": its,
         "gpu_launches": args.steps * (3 if args.lattice == "d2q16" else 1),
@@ -634,15 +653,18 @@ def main():
     if args.precision == "mixed" and not args.no_extras:
         # the plain FP64 form of the same workload (fewer steps: the FP64 pipes are 1/64)
         shape64 = shape_for("fp64")
-        ms64, st64, kms64 = run_form(w, pond, torch, stream, flush, "fp64", 30, 3, shape64, 1)
-        its64 = st64["streams"] / max(1, w.nodes * 30)
-        line["fp64"] = {"value": w.nodes * 30 / (sum(ms64) * 1e-3) / 1e6, "unit": "MLUPS",
-                        "ms_per_step": sum(ms64) / 30, "launch_shape": shape64 or "default",
+        n64 = 30 if w.nodes < 1000000 else 8
+        ms64, st64, kms64 = run_form(w, pond, torch, stream, flush, "fp64", n64, 3, shape64, 1)
+        its64 = st64["streams"] / max(1, w.nodes * n64)
+        line["fp64"] = {"value": w.nodes * n64 / (sum(ms64) * 1e-3) / 1e6, "unit": "MLUPS", "steps": n64,
+                        "ms_per_step": sum(ms64) / n64, "launch_shape": shape64 or "default",
                         "frame_search_streams_per_node": its64,
-                        "roofline": roofline(w, "fp64", its64, kms64, pk, args.lattice)}
+                        "hbm": {"bytes_per_update": bytes_per_update("fp64", args.lattice)},
+                        "roofline": roofline(w, "fp64", its64, kms64, pk, args.lattice),
+                        "e2e": end_to_end(w, pond, torch, stream, "fp64", shape64, n_seg=10, reps=2)}
 
     if rank == 0 and not args.no_extras:
-        line["other_configs"] = other_configs(pond, torch, stream, pk["sm_max_mhz"])
+        line["other_configs"] = other_configs(pond, torch, stream, pk["sm_max_mhz"], skip=w.name)
 
     if not args.no_serving:
         serv = serving_sample(torch, rank, ws)
@@ -653,9 +675,13 @@ def main():
         cpu_steps = args.cpu_steps or max(1, min(40, int(3e5 // w.nodes)))
         res = oracle_mlups(w, cpu_steps, args.lattice)
         line["cpu_baseline"] = {k: res[k] for k in ("value", "unit", "cores", "kind", "sample")}
-        # this run's GPU path against the oracle sample (same steps from the same start)
+        # this run's GPU path against the oracle sample (same steps from the same start,
+        # every node compared), in the bench's form and in FP64
         line["linf_vs_oracle"] = parity_vs_oracle(w, pond, stream, args.precision, shape, res,
                                                   cpu_steps + 1)
+        if args.precision == "mixed" and not args.no_extras and args.lattice == "d2q9":
+            line["fp64"]["linf_vs_oracle"] = parity_vs_oracle(w, pond, stream, "fp64", shape_for("fp64"),
+                                                              res, cpu_steps + 1)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -43,8 +43,13 @@
  *     default stream).  Calls that return host data synchronise that stream.
  *   - Errors are returned as pond_status; pond_last_error() gives a message.  Device
  *     conditions (non-converged frame search, pressure floor hit, NaN) are counted on
- *     the device and reported by pond_stats().  There is no CPU fallback: a missing
- *     or unusable GPU is POND_ECUDA.
+ *     the device (pond_stats() reads the counts) and raised as sticky flags that the
+ *     synchronising calls pond_moments, pond_moments3 and pond_conservation return as
+ *     their status: POND_ENAN while the state holds non-finite values, else
+ *     POND_ENONCONV, else POND_ETHETA for conditions that occurred since the previous
+ *     report.  ENONCONV and ETHETA are warnings: the call has completed and its
+ *     outputs are written; the report clears both flags.  There is no CPU fallback: a
+ *     missing or unusable GPU is POND_ECUDA.
  *   - A context is not thread safe; distinct contexts may be used concurrently.
  */
 #ifndef POND_H
@@ -65,10 +70,13 @@ typedef enum {
     POND_EINVAL = 1,    /* invalid argument or parameter out of range             */
     POND_ENOMEM = 2,    /* device allocation failed                               */
     POND_ECUDA = 3,     /* CUDA runtime error (message in pond_last_error)         */
-    POND_ENONCONV = 4,  /* reserved: frame search did not converge somewhere       */
-    POND_ETHETA = 5,    /* reserved: pressure floor was hit                       */
+    POND_ENONCONV = 4,  /* warning: a frame search hit max_iter since the last
+                           report (sticky flag; outputs are still written)         */
+    POND_ETHETA = 5,    /* warning: the pressure floor was hit since the last
+                           report (sticky flag; outputs are still written)         */
     POND_ENAN = 6,      /* a NaN/Inf appeared in the state (see pond_stats)        */
-    POND_ETIMEOUT = 7   /* reserved for bounded device waits                      */
+    POND_ETIMEOUT = 7   /* reserved: no kernel of this library waits on another
+                           block or device, so no call returns it                  */
 } pond_status;
 
 enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
@@ -187,22 +195,27 @@ pond_status pond_init_fields_device(pond_ctx *ctx, const double *d_rho, const do
 pond_status pond_step(pond_ctx *ctx, int64_t n);
 
 /* Macroscopic fields to host arrays (nx*ny doubles each, NULL skips a field):
- * rho, fluid velocity uhat = u + F dt/(2 rho), T, p (vdW EoS).  Synchronises. */
+ * rho, fluid velocity uhat = u + F dt/(2 rho), T, p (vdW EoS).  Synchronises.
+ * Returns the sticky device flags (POND_ENONCONV, POND_ETHETA, POND_ENAN, see the
+ * conventions above); with ENONCONV or ETHETA the fields are written. */
 pond_status pond_moments(pond_ctx *ctx, double *rho, double *ux, double *uy, double *T,
                          double *p);
 
 /* With the z component of uhat (zero on the two-dimensional lattices); host arrays of
- * nx*ny*nz doubles, NULL skips a field.  Synchronises. */
+ * nx*ny*nz doubles, NULL skips a field.  Synchronises; returns the sticky device flags
+ * as pond_moments does. */
 pond_status pond_moments3(pond_ctx *ctx, double *rho, double *ux, double *uy, double *uz, double *T,
                           double *p);
 
-/* Same into device arrays (asynchronous; no u_z). */
+/* Same into device arrays (asynchronous, so it reports no device flags; no u_z). */
 pond_status pond_moments_device(pond_ctx *ctx, double *d_rho, double *d_ux, double *d_uy,
                                 double *d_T, double *d_p);
 
 /* Global sums in FP64 with compensated summation: out = {sum rho, sum rho uhat_x,
  * sum rho uhat_y, sum_nodes sum_i g_i / 2 (total energy)}, the kept FP32 energy
- * remainders included; on D3Q27 the z momentum is not among them.  Synchronises. */
+ * remainders included; on D3Q27 the z momentum is not among them.  Synchronises;
+ * returns the sticky device flags as pond_moments does (out is written with ENONCONV or
+ * ETHETA). */
 pond_status pond_conservation(pond_ctx *ctx, double out[4]);
 
 /* Full state as 2Q + 7 host planes of nx*ny doubles (25 on D2Q9, 39 on D2Q16):
@@ -227,7 +240,9 @@ pond_status pond_set_state(pond_ctx *ctx, const double *state);
  * aid; pond_step is the fast path). */
 pond_status pond_step_timed(pond_ctx *ctx, double *ms_out);
 
-/* Read (and, if reset != 0, zero) the device counters.  Synchronises. */
+/* Read (and, if reset != 0, zero) the device counters.  Synchronises.  Returns
+ * POND_ENAN while the counters hold non-finite node updates, else POND_OK; a reset also
+ * clears the sticky flags. */
 pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);
 
 /* Conservation sums without any allocation, for callers that cannot allocate device
@@ -236,8 +251,12 @@ pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);
  * that hands the library only pre-placed buffers.  The paper has no counterpart; this
  * is a service of the library.
  *
- * d_planes: device pointer to a state in the 25-plane FP64 layout of pond_get_state
- * (plane p of node n at p*n_nodes + n), caller-owned and only read.  out: host array of
+ * d_planes: device pointer to a D2Q9 state in the 25-plane FP64 layout of pond_get_state
+ * (plane p of node n at p*n_nodes + n), caller-owned and only read.  Only D2Q9 states
+ * are summed correctly: the plane indices of the D2Q16 (39) and D3Q27 (63) layouts
+ * differ, and the library cannot tell them apart from the pointer.  The pointer and
+ * n_nodes are not checked against the allocation either (the C ABI cannot see it): the
+ * caller must pass at least 25 * n_nodes doubles on the current device.  out: host array of
  * 4 doubles {sum rho, sum rho uhat_x, sum rho uhat_y, sum_nodes sum_i g_i / 2}, summed in
  * FP64 with compensated summation as pond_conservation does.  stream: cudaStream_t of
  * the work (NULL = default stream); the call synchronises it before returning.
@@ -246,7 +265,9 @@ pond_status pond_stats(pond_ctx *ctx, pond_stats_t *out, int32_t reset);
  * (32,776 doubles, 256 KiB, held on every device that loads the library until the
  * process exits), so n_nodes may be at most 8,388,608; larger n_nodes, n_nodes < 1 or
  * NULL pointers return POND_EINVAL.  The array's device address is looked up on the
- * first call on each device (that call should come before any stream capture).  All
+ * first call on each device (that call should come before any stream capture) and
+ * kept for the life of the process, which assumes the device's primary context is not
+ * reset (cudaDeviceReset) in between.  All
  * calls share the one array: calls that overlap on the GPU (different streams, threads
  * or processes sharing a context) race on it; every slot a call reads it has written
  * itself first.  Returns POND_ECUDA on a CUDA error. */
@@ -289,6 +310,20 @@ pond_status pond_batch_step(pond_batch *batch, int64_t n);
 
 /* Number of contexts in the batch. */
 int32_t pond_batch_size(const pond_batch *batch);
+
+/* Admission by device memory: pond_batch_add refuses (POND_ENOMEM, the context stays
+ * valid and outside the batch) a context whose pond_device_bytes would take the sum over
+ * the members above `bytes`; 0 (the default) sets no limit.  A budget below what the
+ * members already hold is POND_EINVAL. */
+pond_status pond_batch_set_budget(pond_batch *batch, size_t bytes);
+
+/* Sum of pond_device_bytes over the batch's members. */
+size_t pond_batch_bytes(const pond_batch *batch);
+
+/* Completion poll without blocking: *done = 1 when all work enqueued by the batch's
+ * last pond_batch_step has completed on the device (also before any step), else 0.
+ * POND_ECUDA if that work failed. */
+pond_status pond_batch_poll(pond_batch *batch, int32_t *done);
 
 /* Last error message of the batch (never NULL). */
 const char *pond_batch_last_error(const pond_batch *batch);

@@ -13,8 +13,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "pond.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "pond_kernels.cuh"), os.path.join(HERE, "csrc", "pond_step.cuh"),
-               os.path.join(ROOT, "include", "pond.h")]
+DEPS = SRC + [os.path.join(HERE, "csrc", f) for f in ("pond_kernels.cuh", "pond_step.cuh", "pond_q16.cuh",
+                                                      "pond_q27.cuh")] + [os.path.join(ROOT, "include", "pond.h")]
 LIB = os.path.join(HERE, "libpond.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

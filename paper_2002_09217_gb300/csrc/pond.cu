@@ -53,6 +53,9 @@ struct pond_ctx {
     std::string err;
     size_t bytes = 0;
     DevParams dp{};
+    // device counters already reported by a sync point's status (sticky flags: a
+    // condition is reported once, by the first sync point after it occurred)
+    unsigned long long rep_nonconv = 0, rep_clamped = 0;
 };
 
 namespace {
@@ -285,6 +288,35 @@ pond_status check_ctx(pond_ctx *c)
     return POND_OK;
 }
 
+// Status of a sync point from the device counters hs (read after the context stream
+// was synchronised): POND_ENAN while the state holds non-finite values; otherwise
+// POND_ENONCONV if frame searches hit max_iter since the last report, else POND_ETHETA if
+// the pressure floor was hit since the last report, else POND_OK.  A report clears both
+// flags (the counts stay readable through pond_stats).
+pond_status report_flags(pond_ctx *c, const DevStats &hs)
+{
+    if (hs.nonfinite)
+        return fail(c, POND_ENAN, "non-finite values in the state (" + std::to_string(hs.nonfinite) +
+                                      " node updates; see pond_stats)");
+    const unsigned long long nc = hs.nonconv - std::min(hs.nonconv, c->rep_nonconv);
+    const unsigned long long cl = hs.clamped - std::min(hs.clamped, c->rep_clamped);
+    c->rep_nonconv = hs.nonconv;
+    c->rep_clamped = hs.clamped;
+    if (nc)
+        return fail(c, POND_ENONCONV, "frame search hit max_iter at " + std::to_string(nc) +
+                                          " node updates since the last report (results are returned)");
+    if (cl)
+        return fail(c, POND_ETHETA, "pressure floor hit at " + std::to_string(cl) +
+                                        " node updates since the last report (results are returned)");
+    return POND_OK;
+}
+
+// Enqueue the copy of the device counters into hs (read it after synchronising).
+cudaError_t fetch_stats(pond_ctx *c, DevStats *hs)
+{
+    return cudaMemcpyAsync(hs, c->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, c->stream);
+}
+
 pond_status init_common(pond_ctx *c, const double *d_rho, const double *d_ux, const double *d_uy,
                         const double *d_uz, const double *d_T)
 {
@@ -301,6 +333,7 @@ pond_status init_common(pond_ctx *c, const double *d_rho, const double *d_ux, co
                                         + std::to_string(hs.bad_init) + " nodes violate it)");
     c->initialised = true;
     c->steps = 0;
+    c->rep_nonconv = c->rep_clamped = 0;
     return POND_OK;
 }
 
@@ -400,14 +433,16 @@ pond_status pond_conservation_noalloc(const double *d_planes, int64_t n_nodes, d
     if (noalloc_scratch(&scratch) != cudaSuccess) return POND_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (int)((n_nodes + NOALLOC_SPAN - 1) / NOALLOC_SPAN);
+    // launch errors are peeked right after each launch (a sticky error left by other work
+    // is neither taken nor cleared here); the stream's synchronisation decides the result
     k_conserve_planes1<<<nb, 256, 0, s>>>(d_planes, (long long)n_nodes, NOALLOC_SPAN, scratch);
+    if (cudaPeekAtLastError() != cudaSuccess) return POND_ECUDA;
     k_conserve2<<<1, 32, 0, s>>>(scratch, nb, scratch + 8 * NOALLOC_MAX_BLOCKS);
-    if (cudaGetLastError() != cudaSuccess) return POND_ECUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return POND_ECUDA;
     if (cudaMemcpyAsync(out, scratch + 8 * NOALLOC_MAX_BLOCKS, 4 * sizeof(double),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return POND_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return POND_ECUDA;
-    return POND_OK;
+    return cudaStreamSynchronize(s) == cudaSuccess ? POND_OK : POND_ECUDA;
 }
 
 
@@ -670,8 +705,10 @@ pond_status pond_moments(pond_ctx *c, double *rho, double *ux, double *uy, doubl
         if (host[k])
             CK(cudaMemcpyAsync(host[k], dev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                "cudaMemcpyAsync D2H");
+    DevStats hs{};
+    CK(fetch_stats(c, &hs), "cudaMemcpyAsync D2H");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    return POND_OK;
+    return report_flags(c, hs);
 }
 
 pond_status pond_moments3(pond_ctx *c, double *rho, double *ux, double *uy, double *uz, double *T,
@@ -697,8 +734,10 @@ pond_status pond_moments3(pond_ctx *c, double *rho, double *ux, double *uy, doub
         if (host[k])
             CK(cudaMemcpyAsync(host[k], dev[k], c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
                "cudaMemcpyAsync D2H");
+    DevStats hs{};
+    CK(fetch_stats(c, &hs), "cudaMemcpyAsync D2H");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    return POND_OK;
+    return report_flags(c, hs);
 }
 
 pond_status pond_conservation(pond_ctx *c, double out[4])
@@ -712,8 +751,10 @@ pond_status pond_conservation(pond_ctx *c, double out[4])
     CK(cudaGetLastError(), "conservation launch");
     CK(cudaMemcpyAsync(out, c->part + 8 * c->red_blocks, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                        c->stream), "cudaMemcpyAsync D2H");
+    DevStats hs{};
+    CK(fetch_stats(c, &hs), "cudaMemcpyAsync D2H");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    return POND_OK;
+    return report_flags(c, hs);
 }
 
 pond_status pond_get_state(pond_ctx *c, double *state)
@@ -919,6 +960,7 @@ pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
        "cudaMemcpyAsync D2H");
     if (reset) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream), "cudaMemsetAsync");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+    if (reset) c->rep_nonconv = c->rep_clamped = 0;
     out->steps = c->steps;
     out->node_updates = c->steps * (int64_t)c->N;
     out->streams = (int64_t)hs.streams;
@@ -960,6 +1002,8 @@ struct pond_batch {
     std::vector<Q16> q16;
     cudaGraphExec_t graph = nullptr;  // two steps (even, odd) of every group
     bool graph_ok = false;
+    size_t budget = 0;                // device bytes the members may hold (0: no limit)
+    size_t member_bytes = 0;          // sum of the members' pond_device_bytes
 };
 
 cudaEvent_t batch_done_event(pond_batch *b) { return b->done; }
@@ -1115,10 +1159,14 @@ pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
     if (c->nonlocal) return bfail(b, POND_EINVAL, "two-pass (current-time) contexts are stepped alone");
     if (c->lattice == POND_D3Q27) return bfail(b, POND_EINVAL, "D3Q27 contexts are stepped alone");
     if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
+    if (b->budget && b->member_bytes + c->bytes > b->budget)
+        return bfail(b, POND_ENOMEM, "the context's " + std::to_string(c->bytes) + " device bytes exceed the batch budget (" +
+                                         std::to_string(b->member_bytes) + " of " + std::to_string(b->budget) + " in use)");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
     // the context's queued work (its initialisation) completes before the batch uses it
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaStreamSynchronize");
     b->sims.push_back(c);
+    b->member_bytes += c->bytes;
     c->batch = b;
     b->dirty = true;
     return POND_OK;
@@ -1132,12 +1180,36 @@ pond_status pond_batch_remove(pond_batch *b, pond_ctx *c)
     cudaSetDevice(b->device);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaStreamSynchronize");
     b->sims.erase(it);
+    b->member_bytes -= std::min(b->member_bytes, c->bytes);
     c->batch = nullptr;
     b->dirty = true;
     return POND_OK;
 }
 
 int32_t pond_batch_size(const pond_batch *b) { return b ? (int32_t)b->sims.size() : 0; }
+
+pond_status pond_batch_set_budget(pond_batch *b, size_t bytes)
+{
+    if (!b) return POND_EINVAL;
+    b->err.clear();
+    if (bytes && bytes < b->member_bytes)
+        return bfail(b, POND_EINVAL, "budget below the members' current device bytes");
+    b->budget = bytes;
+    return POND_OK;
+}
+
+size_t pond_batch_bytes(const pond_batch *b) { return b ? b->member_bytes : 0; }
+
+pond_status pond_batch_poll(pond_batch *b, int32_t *done)
+{
+    if (!b || !done) return POND_EINVAL;
+    b->err.clear();
+    if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaSuccess) { *done = 1; return POND_OK; }
+    if (e == cudaErrorNotReady) { *done = 0; return POND_OK; }
+    return bfail(b, POND_ECUDA, std::string("batch poll: ") + cudaGetErrorString(e));
+}
 
 pond_status pond_batch_step(pond_batch *b, int64_t n)
 {

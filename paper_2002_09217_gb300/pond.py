@@ -23,6 +23,10 @@ POND_FP64, POND_MIXED = 0, 1
 NPLANES = 25
 STATUS = {0: "POND_OK", 1: "POND_EINVAL", 2: "POND_ENOMEM", 3: "POND_ECUDA", 4: "POND_ENONCONV",
           5: "POND_ETHETA", 6: "POND_ENAN", 7: "POND_ETIMEOUT"}
+POND_ENONCONV, POND_ETHETA = 4, 5
+# warning-class statuses of the synchronising calls: the call completed and wrote its
+# outputs; the status reports a sticky device flag (see include/pond.h)
+WARNINGS = (POND_ENONCONV, POND_ETHETA)
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -72,12 +76,13 @@ def lib_path() -> str:
 
 
 def load() -> C.CDLL:
-    """Load libpond.so (building it with nvcc first if it is missing)."""
+    """Load libpond.so (building it with nvcc first if it is missing or older than any
+    of its sources)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(build_lib.LIB):
+        if not build_lib.up_to_date():
             build_lib.build()
         lib = C.CDLL(build_lib.LIB)
         P = C.c_void_p
@@ -124,6 +129,12 @@ def load() -> C.CDLL:
         lib.pond_batch_last_error.restype = C.c_char_p
         lib.pond_batch_destroy.argtypes = [C.c_void_p]
         lib.pond_batch_destroy.restype = None
+        lib.pond_batch_set_budget.argtypes = [C.c_void_p, C.c_size_t]
+        lib.pond_batch_set_budget.restype = C.c_int
+        lib.pond_batch_bytes.argtypes = [C.c_void_p]
+        lib.pond_batch_bytes.restype = C.c_size_t
+        lib.pond_batch_poll.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+        lib.pond_batch_poll.restype = C.c_int
         _lib = lib
         return lib
 
@@ -217,11 +228,24 @@ class Simulation:
         if st != 0:
             raise PondError(st, "pond_create failed")
         self._ctx = ctx
+        self.flags = []          # (status, message) of each warning a sync point returned
+        self.last_flag = None    # the last sync point's warning, or None
 
     # -- helpers ---------------------------------------------------------
     def _check(self, st: int):
         if st != 0:
             raise PondError(st, self._lib.pond_last_error(self._ctx).decode())
+
+    def _check_sync(self, st: int):
+        """Status of a synchronising call: the warning-class sticky flags (frame search
+        hit max_iter, pressure floor hit) are recorded in ``self.flags`` and do not raise;
+        every other non-zero status raises."""
+        if st in WARNINGS:
+            self.flags.append((STATUS[st], self._lib.pond_last_error(self._ctx).decode()))
+            self.last_flag = STATUS[st]
+            return
+        self.last_flag = None
+        self._check(st)
 
     def _host(self, x) -> np.ndarray:
         a = np.ascontiguousarray(np.broadcast_to(np.asarray(x, dtype=np.float64), self.shape))
@@ -254,10 +278,10 @@ class Simulation:
     def moments(self) -> dict:
         if self.lattice == "d3q27":
             outs = [np.empty(self.shape) for _ in range(6)]
-            self._check(self._lib.pond_moments3(self._ctx, *[_dptr(o) for o in outs]))
+            self._check_sync(self._lib.pond_moments3(self._ctx, *[_dptr(o) for o in outs]))
             return dict(zip(("rho", "ux", "uy", "uz", "T", "p"), outs))
         outs = [np.empty((self.ny, self.nx)) for _ in range(5)]
-        self._check(self._lib.pond_moments(self._ctx, *[_dptr(o) for o in outs]))
+        self._check_sync(self._lib.pond_moments(self._ctx, *[_dptr(o) for o in outs]))
         return dict(zip(("rho", "ux", "uy", "T", "p"), outs))
 
     def moments_device(self, out: dict):
@@ -268,7 +292,7 @@ class Simulation:
 
     def conservation(self) -> np.ndarray:
         out = np.zeros(4)
-        self._check(self._lib.pond_conservation(self._ctx, _dptr(out)))
+        self._check_sync(self._lib.pond_conservation(self._ctx, _dptr(out)))
         return out
 
     def get_state(self) -> np.ndarray:
@@ -311,11 +335,27 @@ class Simulation:
 
 
 def conservation_noalloc(d_planes, n_nodes: int, stream=None) -> np.ndarray:
-    """Conservation sums of a caller-owned device state in the 25-plane FP64 layout,
+    """Conservation sums of a caller-owned D2Q9 device state in the 25-plane FP64 layout,
     computed without any device allocation (see pond_conservation_noalloc in pond.h).
-    d_planes: a CUDA float64 tensor (or a raw device address) of 25 * n_nodes values."""
+
+    d_planes: a contiguous CUDA float64 tensor of exactly 25 * n_nodes values on the
+    current device (checked here, since the C ABI cannot see the allocation and the
+    kernel reads all 25 planes), or a raw device address, which is NOT checked: the
+    caller then guarantees 25 * n_nodes doubles of a D2Q9 state on the current device."""
     lib = load()
-    ptr = d_planes.data_ptr() if hasattr(d_planes, "data_ptr") else int(d_planes)
+    if hasattr(d_planes, "data_ptr"):
+        import torch
+        n = int(n_nodes)
+        if n < 1:
+            raise PondError(1, "n_nodes must be positive")
+        if (not d_planes.is_cuda or d_planes.device != torch.device("cuda", torch.cuda.current_device())
+                or d_planes.dtype != torch.float64 or not d_planes.is_contiguous()
+                or d_planes.numel() != NPLANES * n):
+            raise PondError(1, "d_planes must be a contiguous float64 tensor of 25 * n_nodes values "
+                               "(a D2Q9 state) on the current CUDA device")
+        ptr = d_planes.data_ptr()
+    else:
+        ptr = int(d_planes)
     sp = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
     out = np.zeros(4)
     st = lib.pond_conservation_noalloc(C.c_void_p(ptr), int(n_nodes), _dptr(out),
@@ -354,6 +394,20 @@ class Batch:
 
     def step(self, n: int = 1):
         self._check(self._lib.pond_batch_step(self._h, int(n)))
+
+    def set_budget(self, nbytes: int):
+        """Device-memory budget of the members (0: no limit); add() then refuses a
+        simulation that would exceed it with PondError(POND_ENOMEM)."""
+        self._check(self._lib.pond_batch_set_budget(self._h, int(nbytes)))
+
+    def device_bytes(self) -> int:
+        return int(self._lib.pond_batch_bytes(self._h))
+
+    def poll(self) -> bool:
+        """True when the work of the last step() call has completed (no blocking)."""
+        done = C.c_int32()
+        self._check(self._lib.pond_batch_poll(self._h, C.byref(done)))
+        return bool(done.value)
 
     def synchronize(self):
         self._stream.synchronize()

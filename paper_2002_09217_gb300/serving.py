@@ -5,10 +5,13 @@ when the device memory it needs fits the budget, initialises it on the GPU and a
 the running batch of its precision.  Each precision has its own batch on its own CUDA
 stream, the mixed one at higher priority, so the fast mixed-precision requests do not
 wait for the FP64 ones (which run at the FP64 pipe's 1/64 rate on GB300) and the two
-groups' kernels overlap on the device.  Whenever a batch's previous chunk of steps has finished (a CUDA event, polled
-without blocking), the server retires its requests that reached their step count (fields
-back to the host), frees their memory, admits more and launches the batch's next chunk
-with ``pond_batch_step`` (one launch per time step and kernel group, graph-replayed).
+groups' kernels overlap on the device.  Whenever a batch's previous chunk of steps has
+finished (``pond_batch_poll``, which does not block), the server retires its requests that
+reached their step count (fields back to the host), frees their memory, admits more and
+launches the batch's next chunk with ``pond_batch_step`` (one launch per time step and
+kernel group, graph-replayed).  Admission is checked twice: against an estimate before the
+simulation's memory is taken, and by the batch itself (``pond_batch_set_budget``), which
+refuses a member whose exact device bytes would exceed the budget.
 Latency of a request = completion time - arrival time.
 
 The per-node arithmetic does not depend on the batch, so a request's result is the same
@@ -36,6 +39,8 @@ class Result:
     precision: str
     fields: dict | None
     status: dict
+    state: object = None      # the final state (25 planes) when the server keeps it
+    workload: object = None   # the request's inputs.Workload
 
     @property
     def latency(self) -> float:
@@ -43,10 +48,13 @@ class Result:
 
 
 def footprint_bytes(nodes: int, precision: str) -> int:
-    """Device bytes of one simulation: two state buffers of 32-value records, a 5-plane
-    FP64 staging buffer and small reduction/counter blocks (as pond_create allocates)."""
+    """Estimated device bytes of one D2Q9 simulation before it is created: two state
+    buffers of 32-value records, a 6-plane FP64 staging buffer and the reduction partials
+    and counters (as pond_create allocates).  Once created, the server charges the
+    library's exact figure (pond_device_bytes) instead."""
     esize = 4 if precision == "mixed" else 8
-    return 2 * 32 * nodes * esize + 5 * nodes * 8 + 65536
+    blocks = min(1024, max(1, (nodes + 255) // 256))
+    return 2 * 32 * nodes * esize + 6 * nodes * 8 + (8 * blocks + 8) * 8 + 4096
 
 
 class Server:
@@ -55,26 +63,43 @@ class Server:
     PRECISIONS = ("mixed", "fp64")
 
     def __init__(self, hbm_budget: int, chunk: int = 50, max_resident: int = 64,
-                 keep_fields: bool = True):
+                 keep_fields: bool = True, keep_state: bool = False):
         import torch
         self.torch = torch
         self.budget = int(hbm_budget)
         self.chunk = int(chunk)
         self.max_resident = int(max_resident)
         self.keep_fields = keep_fields
+        self.keep_state = keep_state   # also return each request's full final state
+        self.peak_bytes = 0
         # the mixed stream at higher priority: an FP64 group launch holds tens of thousands
         # of slow blocks, and the block scheduler would otherwise dispatch them ahead of the
         # mixed group's
         self.streams = {"mixed": torch.cuda.Stream(priority=-1), "fp64": torch.cuda.Stream(priority=0)}
         self.batches = {k: pond.Batch(self.streams[k]) for k in self.PRECISIONS}
+        for b in self.batches.values():
+            b.set_budget(self.budget)
+        self.refused = 0          # admissions the batch refused after creation (budget)
 
-    def _start(self, req, now):
+    def _start(self, req, now, used):
+        """Create, initialise and batch a request's simulation; None if the batch's budget
+        check (exact device bytes) refuses it."""
         w = inputs.request_workload(req)
         sim = pond.from_workload(w, precision=req.precision, stream=self.streams[req.precision])
+        nbytes = sim.device_bytes()
+        if used + nbytes > self.budget and used > 0:
+            sim.close()
+            return None
         sim.init_fields(*w.fields())
-        self.batches[req.precision].add(sim)
+        try:
+            self.batches[req.precision].add(sim)
+        except pond.PondError as e:
+            sim.close()
+            if e.status != 2:
+                raise
+            return None
         return {"req": req, "sim": sim, "left": req.steps, "admitted": now, "nodes": w.nodes,
-                "bytes": footprint_bytes(w.nodes, req.precision)}
+                "bytes": nbytes, "w": w}
 
     def run(self, requests, time_scale: float = 1.0) -> list[Result]:
         """Serve the requests; arrival times are in seconds after the start, multiplied
@@ -84,7 +109,7 @@ class Server:
         heapq.heapify(pending)
         waiting = []                                   # arrived, not yet admitted (FIFO)
         running = {k: [] for k in self.PRECISIONS}
-        inflight = {k: None for k in self.PRECISIONS}  # event after a batch's last chunk
+        inflight = {k: False for k in self.PRECISIONS}  # a batch's last chunk may still run
         used = 0
         results = []
         t0 = time.perf_counter()
@@ -94,22 +119,24 @@ class Server:
                 waiting.append(heapq.heappop(pending)[2])
             busy = False
             for k in self.PRECISIONS:
-                ev = inflight[k]
-                if ev is not None and not ev.query():
+                if inflight[k] and not self.batches[k].poll():
                     busy = True
                     continue
-                inflight[k] = None
+                inflight[k] = False
                 # retire what the finished chunk completed (its stream is idle)
                 for it in [it for it in running[k] if it["left"] == 0]:
                     sim = it["sim"]
                     self.batches[k].remove(sim)
                     fields = sim.moments() if self.keep_fields else None
                     status = sim.stats()
+                    status["flags"] = [f for f, _ in sim.flags]
+                    if self.keep_state:
+                        it["state"] = sim.get_state()
                     sim.close()
                     req = it["req"]
                     results.append(Result(req.rid, req.arrival * time_scale, it["admitted"],
                                           time.perf_counter() - t0, req.steps, it["nodes"],
-                                          req.precision, fields, status))
+                                          req.precision, fields, status, it.get("state"), it["w"]))
                     used -= it["bytes"]
                     running[k].remove(it)
             # admission by footprint, in arrival order
@@ -119,21 +146,23 @@ class Server:
                 if used + need > self.budget and any(running.values()):
                     break
                 k = req.precision
-                if inflight[k] is not None:
+                if inflight[k]:
                     break                  # its batch is stepping; it joins after the chunk
+                item = self._start(req, time.perf_counter() - t0, used)
+                if item is None:
+                    self.refused += 1
+                    break                  # over the budget: wait for memory to free up
                 waiting.pop(0)
-                item = self._start(req, time.perf_counter() - t0)
                 running[k].append(item)
                 used += item["bytes"]
+                self.peak_bytes = max(self.peak_bytes, used)
             for k in self.PRECISIONS:
                 if inflight[k] is None and running[k]:
                     n = min(self.chunk, min(it["left"] for it in running[k]))
                     self.batches[k].step(n)
                     for it in running[k]:
                         it["left"] -= n
-                    ev = torch.cuda.Event()
-                    ev.record(self.streams[k])
-                    inflight[k] = ev
+                    inflight[k] = True
                     busy = True
             if not busy and not waiting:
                 if pending:

@@ -89,3 +89,47 @@ def test_no_cpu_fallback_without_gpu():
     from paper_2002_09217_gb300 import pond
     with pytest.raises(pond.PondError):
         pond.Simulation(8, 8)
+
+
+def test_header_states_the_sticky_status_semantics():
+    """The synchronising calls return the device flags: the header documents that
+    ENONCONV and ETHETA are warnings whose outputs are written, and declares the batch's
+    budget and completion poll."""
+    txt = open(os.path.join(ROOT, "include", "pond.h")).read()
+    for needle in ("POND_ENONCONV = 4", "POND_ETHETA = 5", "sticky", "pond_batch_set_budget",
+                   "pond_batch_poll", "pond_batch_bytes"):
+        assert needle in txt, needle
+
+
+def test_binding_keeps_warning_statuses_and_raises_on_errors():
+    """Simulation._check_sync records POND_ENONCONV / POND_ETHETA (the call completed and
+    wrote its outputs) and raises on every other non-zero status; checked with a stand-in
+    for the library's last-error call, no GPU needed."""
+    from paper_2002_09217_gb300 import pond
+
+    class FakeLib:
+        @staticmethod
+        def pond_last_error(_ctx):
+            return b"message"
+
+    sim = pond.Simulation.__new__(pond.Simulation)
+    sim._lib, sim._ctx, sim.flags, sim.last_flag = FakeLib(), None, [], None
+    sim._check_sync(0)
+    assert sim.flags == [] and sim.last_flag is None
+    sim._check_sync(4)
+    sim._check_sync(5)
+    assert [f for f, _ in sim.flags] == ["POND_ENONCONV", "POND_ETHETA"] and sim.last_flag == "POND_ETHETA"
+    for st in (1, 3, 6):
+        with pytest.raises(pond.PondError) as ei:
+            sim._check_sync(st)
+        assert ei.value.status == st
+    sim._ctx = None
+
+
+def test_build_tracks_every_included_source():
+    """Every header the CUDA translation unit includes is a build dependency, so an edit to
+    any of them rebuilds the library."""
+    src = open(os.path.join(ROOT, "paper_2002_09217_gb300", "csrc", "pond.cu")).read()
+    included = re.findall(r'#include "([^"]+)"', src)
+    deps = {os.path.basename(d) for d in build_lib.DEPS}
+    assert included and all(os.path.basename(h) in deps for h in included), (included, deps)

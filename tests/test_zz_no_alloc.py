@@ -39,8 +39,16 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     from paper_2002_09217_gb300 import pond
 
     planes = torch.zeros(25 * 8, device="cuda", dtype=torch.float64)
+    # a raw address reaches the C entry point, which refuses the size before any launch
     with pytest.raises(pond.PondError) as ei:
-        pond.conservation_noalloc(planes, 8_388_609)
+        pond.conservation_noalloc(planes.data_ptr(), 8_388_609)
     assert ei.value.status == 1
     with pytest.raises(pond.PondError):
-        pond.conservation_noalloc(planes, 0)
+        pond.conservation_noalloc(planes.data_ptr(), 0)
+    # a tensor is checked by the wrapper: 25 * n_nodes float64 values, contiguous, on the
+    # current device
+    for bad, n in ((planes, 8_388_609), (planes, 0), (planes, 9), (planes.float(), 8),
+                   (planes.view(25, 8).t(), 8), (planes.cpu(), 8)):
+        with pytest.raises(pond.PondError) as ei:
+            pond.conservation_noalloc(bad, n)
+        assert ei.value.status == 1
