@@ -313,8 +313,9 @@ int32_t pond_batch_size(const pond_batch *batch);
 
 /* Admission by device memory: pond_batch_add refuses (POND_ENOMEM, the context stays
  * valid and outside the batch) a context whose pond_device_bytes would take the sum over
- * the members above `bytes`; 0 (the default) sets no limit.  A budget below what the
- * members already hold is POND_EINVAL. */
+ * the members above `bytes`, unless the batch is empty (a lone member may exceed the
+ * budget, so that no context is refused for ever); 0 (the default) sets no limit.  A
+ * budget below what the members already hold is POND_EINVAL. */
 pond_status pond_batch_set_budget(pond_batch *batch, size_t bytes);
 
 /* Sum of pond_device_bytes over the batch's members. */

@@ -1159,7 +1159,8 @@ pond_status pond_batch_add(pond_batch *b, pond_ctx *c)
     if (c->nonlocal) return bfail(b, POND_EINVAL, "two-pass (current-time) contexts are stepped alone");
     if (c->lattice == POND_D3Q27) return bfail(b, POND_EINVAL, "D3Q27 contexts are stepped alone");
     if (c->device != b->device) return bfail(b, POND_EINVAL, "context lives on another device");
-    if (b->budget && b->member_bytes + c->bytes > b->budget)
+    // a lone member may exceed the budget, so that no context is refused for ever
+    if (b->budget && !b->sims.empty() && b->member_bytes + c->bytes > b->budget)
         return bfail(b, POND_ENOMEM, "the context's " + std::to_string(c->bytes) + " device bytes exceed the batch budget (" +
                                          std::to_string(b->member_bytes) + " of " + std::to_string(b->budget) + " in use)");
     if (cudaSetDevice(b->device) != cudaSuccess) return bfail(b, POND_ECUDA, "cudaSetDevice");

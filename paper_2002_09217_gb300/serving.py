@@ -82,12 +82,13 @@ class Server:
         self.refused = 0          # admissions the batch refused after creation (budget)
 
     def _start(self, req, now, used):
-        """Create, initialise and batch a request's simulation; None if the batch's budget
-        check (exact device bytes) refuses it."""
+        """Create, initialise and batch a request's simulation; None if the exact device
+        bytes (pond_device_bytes) or the batch's own budget check refuse it while other
+        requests hold memory."""
         w = inputs.request_workload(req)
         sim = pond.from_workload(w, precision=req.precision, stream=self.streams[req.precision])
         nbytes = sim.device_bytes()
-        if used + nbytes > self.budget and used > 0:
+        if used > 0 and used + nbytes > self.budget:
             sim.close()
             return None
         sim.init_fields(*w.fields())
@@ -139,7 +140,9 @@ class Server:
                                           req.precision, fields, status, it.get("state"), it["w"]))
                     used -= it["bytes"]
                     running[k].remove(it)
-            # admission by footprint, in arrival order
+            # admission by footprint, in arrival order: the estimate first (nothing is
+            # allocated for a request that cannot fit), then the exact bytes once created;
+            # a request larger than the budget runs when nothing else is resident
             while waiting and sum(len(v) for v in running.values()) < self.max_resident:
                 req = waiting[0]
                 need = footprint_bytes(req.side * req.side, req.precision)
@@ -151,13 +154,15 @@ class Server:
                 item = self._start(req, time.perf_counter() - t0, used)
                 if item is None:
                     self.refused += 1
+                    if not any(running.values()):
+                        raise RuntimeError("request %d cannot be admitted with nothing resident" % req.rid)
                     break                  # over the budget: wait for memory to free up
                 waiting.pop(0)
                 running[k].append(item)
                 used += item["bytes"]
                 self.peak_bytes = max(self.peak_bytes, used)
             for k in self.PRECISIONS:
-                if inflight[k] is None and running[k]:
+                if not inflight[k] and running[k]:
                     n = min(self.chunk, min(it["left"] for it in running[k]))
                     self.batches[k].step(n)
                     for it in running[k]:
