@@ -43,6 +43,10 @@ constexpr int STEP_NB = 16;   // nodes per block (lanes per node LPN = 8 or 16 i
                               // evenly over the 152 SMs
 constexpr unsigned STEP_NB_MASK = STEP_NB == 32 ? 0xffffffffu : ((1u << STEP_NB) - 1u);
 constexpr int HALO = 3;       // staged halo width (stencil reach for |v| dt < 1)
+// Largest side of a node's stencil region (the union of its 9 directions' 4x4 stencils)
+// that the region stream handles: 4 + the spread of the departure points' floors, 5 for
+// |v| dt < 1; wider regions take the per-pair stream.
+constexpr int REGION_MAX = 8;
 // resident blocks per SM the register budget is sized for: in FP32 five blocks of 128
 // threads (8 lanes per node, about 96 registers) or two of 256 (16 lanes); in FP64 one,
 // so that its wider values stay in registers
@@ -104,6 +108,10 @@ struct StepShared {
     R mom[STEP_NB][4];         // sum f~ c_x, sum f~ c_y (gauge units) as (hi, lo) pairs
     R bhi[STEP_NB][4];         // sums of the node's stored f, f cx, f cy, g, error-free as
     R blo[STEP_NB][4];         //   unevaluated (hi, lo) pairs of R
+    // Lagrange weights of the current stream per axis and region column (row) c, one per
+    // direction of that axis: wt[j][axis][c][k] = a_(c - o_k)(xi_k), zero outside the
+    // 4-node stencil of direction k (o_k its offset in the node's region)
+    R wt[STEP_NB][2][REGION_MAX][4];
     int active[STEP_NB];
     int any_active;
 };
@@ -158,6 +166,27 @@ __device__ __forceinline__ R lag1(int j, R xi)
     if (j == 1) return t0 * t2 * t3 * R(0.5);
     if (j == 2) return -(t0 * t1 * t3) * R(0.5);
     return t0 * t1 * t2 * R(1.0 / 6.0);
+}
+
+// A departure offset (in nodes) limited to +-2^20, NaN mapped to the lower bound: keeps
+// stencil indices derived from it in int range whatever the gauge (fmax returns the
+// non-NaN operand).
+template <typename R>
+__device__ __forceinline__ R clamp_offset(R d)
+{
+    return fmin(fmax(d, R(-1048576)), R(1048576));
+}
+
+// a_j(xi) for a run-time j: the three factors (xi - m), m != j, picked by selects.
+template <typename R>
+__device__ __forceinline__ R lag1_rt(int j, R xi)
+{
+    const R t0 = xi, t1 = xi - R(1), t2 = xi - R(2), t3 = xi - R(3);
+    const R a = j == 0 ? t1 : t0;
+    const R b = j <= 1 ? t2 : t1;
+    const R c = j <= 2 ? t3 : t2;
+    const R inv = j == 0 ? R(-1.0 / 6.0) : (j == 1 ? R(0.5) : (j == 2 ? R(-0.5) : R(1.0 / 6.0)));
+    return a * b * c * inv;
 }
 
 // a[i] for a run-time i without local-memory indexing (unrolled selects).
@@ -370,6 +399,40 @@ __device__ __forceinline__ void pair_inc(const R v[24], int jx, int jy, R th, R 
     }
     tf = sf;
     tg = sg;
+}
+
+// One stencil node of a node's region carried into the arrival gauge for all nine
+// directions of one population family, weighted and accumulated:
+//   acc[(k, l)] += wx[k] wy[l] ([G_n f_n](k, l) - f_x(k, l))
+// with G_n = (I + Ex) (x) (I + Ey) the separable transfer map from the stencil node's
+// gauge into the arrival gauge (SM "Transfer matrix"), Ex[k][a] = l_k increments at the
+// source velocities.  In FP32 the increment form (see pair_inc) keeps the rounding
+// relative to the differences: (f_n - f_x)(k, l) + t(k, l) + sum_b Ey[l][b] (f_n(k, b) +
+// t(k, b)), t(k, b) = sum_a Ex[k][a] f_n(a, b); in FP64 the map is applied directly.
+// All indices are compile-time: each stencil node is transformed once for every
+// direction whose stencil contains it.
+template <typename R>
+__device__ __forceinline__ void region_family(const R *v, const R *own, const R (&Ex)[3][3],
+                                              const R (&Ey)[3][3], const R (&wx)[3], const R (&wy)[3],
+                                              R (&acc)[9])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R t[3], u[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            t[b] = Ex[k][0] * v[3 * b] + Ex[k][1] * v[3 * b + 1] + Ex[k][2] * v[3 * b + 2];
+            if constexpr (sizeof(R) == 8) t[b] += v[3 * b + k];
+            u[b] = sizeof(R) == 8 ? t[b] : v[3 * b + k] + t[b];
+        }
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const int i = 3 * l + k;
+            R o = sizeof(R) == 8 ? t[l] - own[i] : (v[i] - own[i]) + t[l];
+            o += Ey[l][0] * u[0] + Ey[l][1] * u[1] + Ey[l][2] * u[2];
+            acc[i] += (wx[k] * wy[l]) * o;
+        }
+    }
 }
 
 // The double-well constants in the arithmetic type of a kernel.
@@ -660,8 +723,110 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             const R th = sh.lam[grp][0], ux = sh.lam[grp][1], uy = sh.lam[grp][2];
             const R s = sqrt_(th), inv_s = R(1) / s;
             R a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-            // rows of directions (jy) in a rolled loop, the three directions of a row
-            // unrolled so that their transfer coefficients are compile-time selections
+            // Departure points x - v_i dt of the directions of each axis (the x part depends
+            // on jx only, the y part on jy only): stencil start floor(.) - 1 and the
+            // Lagrange coordinate xi in [1, 2).  The node's region is the union of its
+            // directions' 4x4 stencils: (4 + spread of the floors) per axis.
+            // Offsets are clamped to +-2^20 nodes first (a NaN offset goes to the bound):
+            // with a non-finite or runaway gauge the floors and their spread stay in int
+            // range, so the region is always 4..8 wide when taken and its indices stay
+            // inside the weight tables.
+            int fl[2][3];
+            R xi[2][3];
+#pragma unroll
+            for (int ax = 0; ax < 2; ++ax)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    const R d = clamp_offset(-(s * R(j - 1) + (ax == 0 ? ux : uy)) * q.dt);
+                    const R f = floor(d);
+                    fl[ax][j] = (int)f;
+                    xi[ax][j] = d - f + R(1);
+                }
+            const int lo_x = min(fl[0][0], min(fl[0][1], fl[0][2]));
+            const int lo_y = min(fl[1][0], min(fl[1][1], fl[1][2]));
+            const int ncols = 4 + max(fl[0][0], max(fl[0][1], fl[0][2])) - lo_x;
+            const int nrows = 4 + max(fl[1][0], max(fl[1][1], fl[1][2])) - lo_y;
+            if (ncols <= REGION_MAX && nrows <= REGION_MAX) {
+                // weight tables: lane c < 8 fills region column c and region row c
+                if (lane < REGION_MAX) {
+#pragma unroll
+                    for (int ax = 0; ax < 2; ++ax) {
+                        const int n_ax = ax == 0 ? ncols : nrows, lo = ax == 0 ? lo_x : lo_y;
+                        if (lane < n_ax) {
+                            R w4[4];
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) {
+                                const int kk2 = lane - (fl[ax][j] - lo);
+                                w4[j] = (kk2 >= 0 && kk2 < 4) ? lag1_rt<R>(kk2, xi[ax][j]) : R(0);
+                            }
+                            w4[3] = R(0);
+                            R *dst = sh.wt[grp][ax][lane];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) dst[j] = w4[j];
+                        }
+                    }
+                }
+                __syncwarp(gmask);
+                R accf[9], accg[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) accf[i] = accg[i] = R(0);
+                const int x_lo = X + lo_x - 1, y_lo = Y + lo_y - 1;
+                const int nreg = ncols * nrows;
+                const float inc = 1.0f / (float)ncols;
+                // region nodes round-robin over the group's lanes
+#pragma unroll 1
+                for (int r = lane; r < nreg; r += LPN) {
+                    const int cy = (int)(((float)r + 0.5f) * inc), cx = r - cy * ncols;
+                    const int sl = slot_of(x_lo + cx, y_lo + cy);
+                    R v[24];
+                    if (sl >= 0) {
+                        load_slot24(tile + sl * TS, v);
+                    } else {
+                        const size_t nd = (size_t)bc_wrap(y_lo + cy, p.ny, p.bcy) * p.nx +
+                                          bc_wrap(x_lo + cx, p.nx, p.bcx);
+                        load_rec24(in + nd * SL, v);
+                        v[P_SQ] = sqrt_(v[P_TH]);
+                    }
+                    const R thn = v[P_TH], sn = v[P_SQ];
+                    const R qm1 = sizeof(R) == 8 ? sn * inv_s - R(1) : fdiv_(thn - th, (sn + s) * s);
+                    const R wxg = (v[P_UX] - ux) * inv_s, wyg = (v[P_UY] - uy) * inv_s;
+                    R Ex[3][3], Ey[3][3];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        const R ex = qm1 * R(a - 1) + wxg, ey = qm1 * R(a - 1) + wyg;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            Ex[k][a] = ell_inc<R>(k, a, ex);
+                            Ey[k][a] = ell_inc<R>(k, a, ey);
+                        }
+                    }
+                    R wx[3], wy[3];
+                    {
+                        const R *px = sh.wt[grp][0][cx], *py = sh.wt[grp][1][cy];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            wx[j] = px[j];
+                            wy[j] = py[j];
+                        }
+                    }
+                    // the node's own populations are read from its staged slot
+                    region_family<R>(v + P_F, own + P_F, Ex, Ey, wx, wy, accf);
+                    region_family<R>(v + P_G, own + P_G, Ex, Ey, wx, wy, accg);
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    part[i * LPN] = accf[i];
+                    part[(9 + i) * LPN] = accg[i];
+                    a0 += accf[i];
+                    if (i % 3 == 0) a1 -= accf[i];
+                    if (i % 3 == 2) a1 += accf[i];
+                    a2 += accf[i] * R(i / 3 - 1);
+                    a3 += accg[i];
+                }
+            } else {
+            // per-pair stream for wide regions (|v| dt of 2 nodes or more): rows of
+            // directions (jy) in a rolled loop, the three directions of a row unrolled so
+            // that their transfer coefficients are compile-time selections
 #pragma unroll 1
             for (int jy = 0; jy < 3; ++jy) {
                 R fxr[3], gxr[3];   // own populations of this row of directions
@@ -670,14 +835,14 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     fxr[a] = own[P_F + 3 * jy + a];
                     gxr[a] = own[P_G + 3 * jy + a];
                 }
-                const R dy = -(s * R(jy - 1) + uy) * q.dt;
+                const R dy = clamp_offset(-(s * R(jy - 1) + uy) * q.dt);
                 const R fly = floor(dy);
                 const int y0 = Y + (int)fly - 1;
                 const R eta = dy - fly + R(1);
 #pragma unroll
                 for (int jx = 0; jx < 3; ++jx) {
                     const int i = 3 * jy + jx;
-                    const R dx = -(s * R(jx - 1) + ux) * q.dt;
+                    const R dx = clamp_offset(-(s * R(jx - 1) + ux) * q.dt);
                     const R flx = floor(dx);
                     const int x0 = X + (int)flx - 1;
                     const R ax = lag1<R>(kk, dx - flx + R(1));
@@ -713,6 +878,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     a2 += vf * R(jy - 1);
                     a3 += vg;
                 }
+            }
             }
 #pragma unroll
             for (int o = LPN / 2; o > 0; o >>= 1) {
