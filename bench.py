@@ -131,21 +131,38 @@ def bytes_per_update(precision: str, lattice: str = "d2q9") -> int:
     return 48 * e
 
 
-# Algorithmic FLOPs of the step kernel's formula, per node update (an FMA counts 2):
-#  per stencil pair (9 directions x 16 stencil nodes per stream): gauge offsets (8), the
-#  six transfer increments (4 for the offsets, ~20 for the increments), the x-increments
-#  of the three source rows for f and g (30), the f and g increment components (22),
-#  Lagrange weight and accumulation (7) => 91; per direction: departure point, basis and
-#  moment sums (20); per stream: moments and residual (60); per node update: the
-#  Korteweg tensor, heat flux and their divergences counted once per node (200; the kernel
-#  recomputes them at each neighbour) and the collision (1300: transfer rows of both axes
-#  ~230, forced g equilibrium ~410, BGK updates ~150, carrying X* into the streaming
-#  gauge ~390, exact rest-population remainders ~100).
+# Algorithmic FLOPs of the D2Q9 step kernel's formula (an FMA counts 2).  A stream of a
+# node transforms each node of its stencil region (the union of its nine directions'
+# 4x4 stencils, counted by the kernel: pond_stats region_nodes) once for all directions:
+#  per region node: gauge offsets (9), the per-axis transfer increments from h = e/2 and
+#  p = h (2c + e) (42), the nine weight products (9), and per population family the
+#  x-transform of the three source rows (45), the sums for the y-transform (9), the
+#  increment-form outputs (72) and the weighted accumulation (18) => 348;
+#  per stream: departure points, Lagrange weight tables and moment sums of the nine
+#  directions (9 x 20) and the moments, EoS and residual (60) => 240;
+#  streams of regions wider than 8 nodes take the per-direction path: per stencil pair
+#  (9 directions x 16 stencil nodes) gauge offsets (8), six transfer increments (24), the
+#  x-increments of three source rows for f and g (30), the f and g components (22),
+#  weight and accumulation (7) => 91, plus the same 240 per stream;
+#  per node update: the Korteweg tensor, heat flux and their divergences counted once per
+#  node (200; the kernel recomputes them at each neighbour) and the collision (1300:
+#  transfer rows of both axes ~230, forced g equilibrium ~410, BGK updates ~150, carrying
+#  X* into the streaming gauge ~390, exact rest-population remainders ~100).
+FLOPS_REGION_NODE = 348
 FLOPS_PAIR = 91
 FLOPS_DIR = 20
 FLOPS_STREAM_EXTRA = 60
 FLOPS_NONLOCAL = 200
 FLOPS_COLLIDE = 1300
+
+
+def flops_d2q9(st: dict, updates: int) -> float:
+    """FLOPs per node update of the D2Q9 step from its counters (pond_stats)."""
+    per_stream = 9 * FLOPS_DIR + FLOPS_STREAM_EXTRA
+    pair_streams = st.get("pair_streams", 0)
+    total = (st["region_nodes"] * FLOPS_REGION_NODE + st["streams"] * per_stream
+             + pair_streams * 9 * 16 * FLOPS_PAIR + updates * (FLOPS_NONLOCAL + FLOPS_COLLIDE))
+    return total / max(1, updates)
 
 # The same count for the D2Q16 step (k_q16_step), per node update: per stencil pair (16
 # directions x 16 stencil nodes per stream): gauge offsets (9), the eight transfer-map
@@ -302,12 +319,12 @@ def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws)
     return ms, st, sum(ms) / len(ms)
 
 
-def roofline(w, precision, its, kernel_ms, pk, lattice="d2q9"):
+def roofline(w, precision, its, kernel_ms, pk, lattice="d2q9", st=None, updates=0):
     if lattice == "d2q16":
         fl = flops_q16(its)
         kernel, traffic = "k_q16_step (+ two non-local kernels, timed together)", None
     else:
-        fl = its * flops_per_stream() + FLOPS_NONLOCAL + FLOPS_COLLIDE
+        fl = flops_d2q9(st, updates)
         kernel, traffic = "k_pond_step", ncu_traffic(w, precision)
     achieved = w.nodes * fl / (kernel_ms * 1e-3) / 1e12
     peak = alu_peak_tflops(precision, pk["sm_max_mhz"])
@@ -642,7 +659,8 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single"},
         "frame_search_streams_per_node": its,
         "gpu_launches": args.steps * (3 if args.lattice == "d2q16" else 1),
-        "roofline": roofline(w, args.precision, its, kms, pk, args.lattice),
+        "roofline": roofline(w, args.precision, its, kms, pk, args.lattice, st, w.nodes * args.steps),
+        "region_nodes_per_stream": st["region_nodes"] / max(1, st["streams"] - st["pair_streams"]),
         "hbm": {"bytes_per_update": bytes_per_update(args.precision, args.lattice),
                 "achieved_gbs": value / ws * 1e6 * bytes_per_update(args.precision, args.lattice) / 1e9,
                 "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
@@ -660,7 +678,7 @@ def main():
                         "ms_per_step": sum(ms64) / n64, "launch_shape": shape64 or "default",
                         "frame_search_streams_per_node": its64,
                         "hbm": {"bytes_per_update": bytes_per_update("fp64", args.lattice)},
-                        "roofline": roofline(w, "fp64", its64, kms64, pk, args.lattice),
+                        "roofline": roofline(w, "fp64", its64, kms64, pk, args.lattice, st64, w.nodes * n64),
                         "e2e": end_to_end(w, pond, torch, stream, "fp64", shape64, n_seg=10, reps=2)}
 
     if rank == 0 and not args.no_extras:

@@ -45,9 +45,9 @@
  *     conditions (non-converged frame search, pressure floor hit, NaN) are counted on
  *     the device (pond_stats() reads the counts) and raised as sticky flags that the
  *     synchronising calls pond_moments, pond_moments3 and pond_conservation return as
- *     their status: POND_ENAN while the state holds non-finite values, else
- *     POND_ENONCONV, else POND_ETHETA for conditions that occurred since the previous
- *     report.  ENONCONV and ETHETA are warnings: the call has completed and its
+ *     their status: POND_ETIMEOUT if a bounded device wait ran out, else
+ *     POND_ENAN while the state holds non-finite values, else POND_ENONCONV, else
+ *     POND_ETHETA for conditions that occurred since the previous report.  ENONCONV and ETHETA are warnings: the call has completed and its
  *     outputs are written; the report clears both flags.  There is no CPU fallback: a
  *     missing or unusable GPU is POND_ECUDA.
  *   - A context is not thread safe; distinct contexts may be used concurrently.
@@ -75,8 +75,9 @@ typedef enum {
     POND_ETHETA = 5,    /* warning: the pressure floor was hit since the last
                            report (sticky flag; outputs are still written)         */
     POND_ENAN = 6,      /* a NaN/Inf appeared in the state (see pond_stats)        */
-    POND_ETIMEOUT = 7   /* reserved: no kernel of this library waits on another
-                           block or device, so no call returns it                  */
+    POND_ETIMEOUT = 7   /* a bounded wait of the D2Q9 step for a tile's staging
+                           copies (TMA) ran out: the tile was skipped, the state
+                           is incomplete (sticky, reported at the sync points)     */
 } pond_status;
 
 enum { POND_PERIODIC = 0, POND_ZEROGRAD = 1 };     /* boundary per axis               */
@@ -163,6 +164,13 @@ typedef struct {
     int64_t block_streams; /* streaming passes summed over kernel blocks (a block
                               of 32 nodes streams until all its nodes stop)    */
     int64_t max_streams;   /* largest streaming-pass count of any block        */
+    int64_t timeouts;      /* tiles skipped because a bounded wait for their
+                              staging copies ran out (reported as POND_ETIMEOUT) */
+    int64_t region_nodes;  /* D2Q9: stencil-region nodes carried into the arrival
+                              gauge, summed over streams (the union of a node's
+                              nine 4x4 stencils: 16..64 per stream)              */
+    int64_t pair_streams;  /* D2Q9: streams of regions wider than 8 nodes, which
+                              take the per-direction, per-stencil-node path      */
 } pond_stats_t;
 
 /* Create a context and allocate its device state (two state buffers holding one record

@@ -8,6 +8,7 @@
 #include "pond.h"
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
 
 #include <algorithm>
 #include <cmath>
@@ -55,7 +56,10 @@ struct pond_ctx {
     DevParams dp{};
     // device counters already reported by a sync point's status (sticky flags: a
     // condition is reported once, by the first sync point after it occurred)
-    unsigned long long rep_nonconv = 0, rep_clamped = 0;
+    unsigned long long rep_nonconv = 0, rep_clamped = 0, rep_timeouts = 0;
+    // D2Q9: tensor maps of the two state buffers for the TMA staging of interior tiles
+    CUtensorMap tmap[2];
+    int use_tma = 0;
 };
 
 namespace {
@@ -98,7 +102,55 @@ void dev_free(pond_ctx *c, void *p)
 
 inline unsigned blocks_for(size_t n, unsigned bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// cuTensorMapEncodeTiled from the driver, looked up once (null if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor maps of a D2Q9 context's state buffers: the records as a 3-D tensor
+// [ny][nx][SL] of R, box = the staged slot values x the staged row pitch x the halo'd tile
+// height, so that a box lands in shared memory exactly as the step kernel's staged tile.
+// Leaves use_tma = 0 (every tile copied per chunk) if the maps cannot be made.
+void make_tensor_maps(pond_ctx *c)
+{
+    c->use_tma = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || c->lattice != POND_D2Q9) return;
+    const bool f32 = c->opts.precision == POND_MIXED;
+    const int TS = f32 ? Slot<float>::stride : Slot<double>::stride;
+    const int PT = step_row_pitch(c->dp.tile_x, TS), HT = STEP_NB / c->dp.tile_x + 2 * HALO;
+    if (PT > c->grid.nx || HT > c->grid.ny) return;   // no interior tile
+    const cuuint64_t dims[3] = {(cuuint64_t)SL, (cuuint64_t)c->grid.nx, (cuuint64_t)c->grid.ny};
+    const cuuint64_t strides[2] = {(cuuint64_t)SL * c->esize, (cuuint64_t)SL * c->esize * c->grid.nx};
+    const cuuint32_t box[3] = {(cuuint32_t)TS, (cuuint32_t)PT, (cuuint32_t)HT};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int k = 0; k < 2; ++k)
+        if (enc(&c->tmap[k], f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                c->state[k], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return;
+    c->use_tma = 1;
+}
+
 bool mixed(const pond_ctx *c) { return c->opts.precision == POND_MIXED; }
+
+// Tiles of 16 nodes of the D2Q9 step kernel over the grid.
+int step_tiles(const pond_ctx *c)
+{
+    const int ty = STEP_NB / c->dp.tile_x;
+    return c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty);
+}
 
 // Largest dynamic shared memory of a step block over the tile shapes, for lanes per node.
 template <typename R>
@@ -198,21 +250,21 @@ pond_status launch_step(pond_ctx *c, cudaEvent_t *ev = nullptr)
     if (c->lattice == POND_D3Q27) return launch_step_q27<R>(c, ev);
     const R *in = (const R *)c->state[c->cur];
     R *out = (R *)c->state[1 - c->cur];
-    const int tx = c->dp.tile_x, ty = STEP_NB / tx;
-    const unsigned nb = (unsigned)(c->dp.tiles_x * ((c->grid.ny + ty - 1) / ty));
-    const size_t smem = step_smem_bytes(tx, Slot<R>::stride, (int)sizeof(R), c->lanes);
+    const unsigned nb = (unsigned)step_tiles(c);
+    const size_t smem = step_smem_bytes(c->dp.tile_x, Slot<R>::stride, (int)sizeof(R), c->lanes);
+    const CUtensorMap &tm = c->tmap[c->cur];
     if (ev) cudaEventRecord(ev[0], c->stream);
     const R *nl = in;
     if (c->nonlocal) {
         // pass 1: the lagged step predicts rho, T at t (its counters kept apart); pass 2
         // redoes the step from the same state with the non-local terms of that prediction
         R *pred = (R *)c->pred;
-        if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, pred, c->dstats_pred, in);
-        else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, pred, c->dstats_pred, in);
+        if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, pred, c->dstats_pred, in, tm, c->use_tma);
+        else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, pred, c->dstats_pred, in, tm, c->use_tma);
         nl = pred;
     }
-    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats, nl);
-    else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats, nl);
+    if (c->lanes == 16) k_pond_step<R, 16><<<nb, STEP_NB * 16, smem, c->stream>>>(c->dp, in, out, c->dstats, nl, tm, c->use_tma);
+    else k_pond_step<R, 8><<<nb, STEP_NB * 8, smem, c->stream>>>(c->dp, in, out, c->dstats, nl, tm, c->use_tma);
     if (ev) cudaEventRecord(ev[1], c->stream);
     c->cur = 1 - c->cur;
     return POND_OK;
@@ -295,6 +347,11 @@ pond_status check_ctx(pond_ctx *c)
 // flags (the counts stay readable through pond_stats).
 pond_status report_flags(pond_ctx *c, const DevStats &hs)
 {
+    if (hs.timeouts > c->rep_timeouts) {
+        c->rep_timeouts = hs.timeouts;
+        return fail(c, POND_ETIMEOUT, "a bounded wait for a tile's staging copies ran out (" +
+                                          std::to_string(hs.timeouts) + " tiles skipped; the state is incomplete)");
+    }
     if (hs.nonfinite)
         return fail(c, POND_ENAN, "non-finite values in the state (" + std::to_string(hs.nonfinite) +
                                       " node updates; see pond_stats)");
@@ -333,7 +390,7 @@ pond_status init_common(pond_ctx *c, const double *d_rho, const double *d_ux, co
                                         + std::to_string(hs.bad_init) + " nodes violate it)");
     c->initialised = true;
     c->steps = 0;
-    c->rep_nonconv = c->rep_clamped = 0;
+    c->rep_nonconv = c->rep_clamped = c->rep_timeouts = 0;
     return POND_OK;
 }
 
@@ -580,6 +637,7 @@ pond_status pond_create(const pond_grid *grid, const pond_lattice *lattice, cons
         pond_destroy(c);
         return POND_ECUDA;
     }
+    make_tensor_maps(c);
     *out = c;
     return POND_OK;
 }
@@ -960,7 +1018,7 @@ pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
        "cudaMemcpyAsync D2H");
     if (reset) CK(cudaMemsetAsync(c->dstats, 0, sizeof(DevStats), c->stream), "cudaMemsetAsync");
     CK(cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
-    if (reset) c->rep_nonconv = c->rep_clamped = 0;
+    if (reset) c->rep_nonconv = c->rep_clamped = c->rep_timeouts = 0;
     out->steps = c->steps;
     out->node_updates = c->steps * (int64_t)c->N;
     out->streams = (int64_t)hs.streams;
@@ -970,6 +1028,9 @@ pond_status pond_stats(pond_ctx *c, pond_stats_t *out, int32_t reset)
     out->stalled = (int64_t)hs.stalled;
     out->block_streams = (int64_t)hs.block_streams;
     out->max_streams = (int64_t)hs.max_streams;
+    out->timeouts = (int64_t)hs.timeouts;
+    out->region_nodes = (int64_t)hs.region_nodes;
+    out->pair_streams = (int64_t)hs.pair_streams;
     return hs.nonfinite ? fail(c, POND_ENAN, "non-finite values in the state") : POND_OK;
 }
 

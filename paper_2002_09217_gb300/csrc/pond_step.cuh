@@ -33,6 +33,8 @@
 // the local differences, not to the populations, and does not accumulate as a bias.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor-map type of the TMA tile copies)
+
 #include "pond_kernels.cuh"
 
 namespace pond {
@@ -97,6 +99,56 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// ---- TMA tile copies (cp.async.bulk.tensor) completed on an mbarrier ----------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the async (TMA) proxy
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// One arrival that also expects `bytes` of asynchronous copies on the barrier.
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Copy the box at coordinates (c0, c1, c2) of a 3-D tensor map into shared memory dst
+// (the box lands densely, innermost dimension first), completing on bar.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Wait for phase `parity` of bar to complete, for at most limit_ns nanoseconds of the
+// global timer; returns false if the limit ran out (the caller then gives up the tile
+// instead of hanging).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long limit_ns)
+{
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t0));
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+        if (t - t0 > limit_ns) return false;
+    }
+}
+constexpr unsigned long long TMA_WAIT_LIMIT_NS = 1000000000ull;   // one second
+
 template <typename R>
 struct StepShared {
     R dsum[STEP_NB][4];        // sum dF, sum dF cx, sum dF cy, sum dG of the current stream
@@ -114,6 +166,8 @@ struct StepShared {
     R wt[STEP_NB][2][REGION_MAX][4];
     int active[STEP_NB];
     int any_active;
+    int nreg[STEP_NB];         // region nodes streamed by node j (summed over its streams)
+    int npair[STEP_NB];        // streams of node j that took the per-pair path
 };
 
 // 1-D transfer-map increment E = l_k(c_a + e) - l_k(c_a) for target index k (c = k-1),
@@ -530,17 +584,45 @@ __device__ __forceinline__ void eos_update(const DevParams &p, const float *bhi,
     o.dux = dux.hi; o.duy = duy.hi;
 }
 
+// Issue (without waiting) the 16-byte cp.async copies of tile `tile_idx` and its halo of
+// HALO nodes (the first 24 values of each record) into the staged tile `tile`, one slot per
+// unwrapped coordinate (periodic wrap or zero-gradient clamp applied to the source), and
+// commit them as one group.
+template <typename R>
+__device__ __forceinline__ void stage_issue(const DevParams &p, const R *__restrict__ in, R *tile, int tile_idx)
+{
+    constexpr int TS = Slot<R>::stride, CH = Slot<R>::chunks;
+    const int TX = p.tile_x, TY = STEP_NB / TX;
+    const int X0 = (tile_idx % p.tiles_x) * TX, Y0 = (tile_idx / p.tiles_x) * TY;
+    const int WT = TX + 2 * HALO, HT = TY + 2 * HALO;
+    const int PT = step_row_pitch(TX, TS);
+    const int total = WT * HT * CH;
+    // k / WT through the float reciprocal: exact for k < 2^20 (the quotient's fraction
+    // stays >= 0.5 / WT away from an integer)
+    const float iwt = 1.0f / (float)WT;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int k = idx / CH, ch = idx - k * CH;
+        const int cv = (int)(((float)k + 0.5f) * iwt), cu = k - cv * WT;
+        const int gxw = bc_wrap(X0 - HALO + cu, p.nx, p.bcx);
+        const int gyw = bc_wrap(Y0 - HALO + cv, p.ny, p.bcy);
+        const R *src = in + ((size_t)gyw * p.nx + gxw) * SL + ch * (16 / sizeof(R));
+        cp_async16(tile + (cv * PT + cu) * TS + ch * (16 / sizeof(R)), src);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
 // One time step of one tile (block) of a simulation: the body of both step kernels.
+// tile: the block's staged tile (`staged`: its copies were issued and waited for by the
+// caller, else they are issued here); part: the per-lane partials.
 template <typename R, int LPN>
 __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restrict__ in,
                                           R *__restrict__ out, DevStats *stats, int tile_idx,
-                                          const R *nlsrc)
+                                          const R *nlsrc, R *tile, R *part_base, bool staged,
+                                          const CUtensorMap *tmap = nullptr)
 {
     static_assert(LPN == 8 || LPN == 16, "8 or 16 lanes per node");
     constexpr int PPL = 16 / LPN;   // stencil positions per lane and direction
     __shared__ StepShared<R> sh;
-    extern __shared__ __align__(16) unsigned char step_dyn_smem[];
-    R *tile = reinterpret_cast<R *>(step_dyn_smem);
     constexpr int TS = Slot<R>::stride;
     const TypedParams<R> &q = typed<R>(p);
     const int grp = threadIdx.x / LPN, lane = threadIdx.x % LPN;
@@ -562,21 +644,33 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 
     // ---------------- staging: tile + halo records into shared memory --------------
     {
-        constexpr int CH = Slot<R>::chunks;
-        const int total = WT * HT * CH;
-        // k / WT through the float reciprocal: exact for k < 2^20 (the quotient's fraction
-        // stays >= 0.5 / WT away from an integer)
         const float iwt = 1.0f / (float)WT;
-        for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-            const int k = idx / CH, ch = idx - k * CH;
-            const int cv = (int)(((float)k + 0.5f) * iwt), cu = k - cv * WT;
-            const int gxw = bc_wrap(X0 - HALO + cu, p.nx, p.bcx);
-            const int gyw = bc_wrap(Y0 - HALO + cv, p.ny, p.bcy);
-            const R *src = in + ((size_t)gyw * p.nx + gxw) * SL + ch * (16 / sizeof(R));
-            cp_async16(tile + (cv * PT + cu) * TS + ch * (16 / sizeof(R)), src);
+        // A tile whose halo'd box (PT x HT slots) lies inside the grid is one TMA copy of a
+        // box of the record tensor [ny][nx][SL] (first TS values of each record); tiles at
+        // the grid edges need the periodic wrap or zero-gradient clamp and take the
+        // per-chunk cp.async copies.
+        const bool tma = tmap != nullptr && X0 - HALO >= 0 && X0 - HALO + PT <= p.nx &&
+                         Y0 - HALO >= 0 && Y0 - HALO + HT <= p.ny && (smem_u32(tile) & 127u) == 0;
+        if (tma) {
+            __shared__ __align__(8) unsigned long long tma_bar;
+            __shared__ int tma_ok;
+            if (threadIdx.x == 0) {
+                mbar_init(&tma_bar, 1);
+                mbar_arrive_expect_tx(&tma_bar, (unsigned)(PT * HT * TS * sizeof(R)));
+                tma_load_3d(tile, tmap, 0, X0 - HALO, Y0 - HALO, &tma_bar);
+                tma_ok = mbar_wait_bounded(&tma_bar, 0, TMA_WAIT_LIMIT_NS) ? 1 : 0;
+                if (!tma_ok) atomicAdd(&stats->timeouts, 1ull);
+            }
+            __syncthreads();
+            if (!tma_ok) return;     // the tile is skipped; the sync points report POND_ETIMEOUT
+            // every thread observes the completed phase (returns at once), which orders the
+            // copied data before its reads
+            if (threadIdx.x != 0) mbar_wait_bounded(&tma_bar, 0, TMA_WAIT_LIMIT_NS);
+        } else if (!staged) {
+            stage_issue<R>(p, in, tile, tile_idx);
+            cp_async_wait_all();
+            __syncthreads();
         }
-        cp_async_wait_all();
-        __syncthreads();
         // per staged node, once per step: sqrt(theta) into the slot's spare value, and the
         // vdW pressure and p/rho of the stored rho, T (for the non-local terms) into the
         // slot words past the staged values
@@ -596,7 +690,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
             }
             const R pr = eos_pressure<R>(p.eos_kind, q.a, q.b, q.R, r, t, typed_sp<R>(p));
             sl[S_PR] = pr;
-            sl[S_PRR] = pr / r;
+            sl[S_PRR] = fdiv_(pr, r);
         }
         __syncthreads();
     }
@@ -613,7 +707,10 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         // the grid first (its stencil is that of the boundary node itself)
         const int mx = p.bcx == 0 ? X0 + tx + cx : bc_wrap(X0 + tx + cx, p.nx, 1);
         const int my = p.bcy == 0 ? Y0 + ty + cy : bc_wrap(Y0 + ty + cy, p.ny, 1);
-        const R *c0 = tile + slot_of(mx, my) * TS;
+        // mx + ex, my + ey (|e| <= 1) lie within 2 nodes of the tile, inside the staged
+        // halo: slots by direct offsets from the neighbour's own slot
+        const int s0 = (my - (Y0 - HALO)) * PT + (mx - (X0 - HALO));
+        const R *c0 = tile + s0 * TS;
         const R r0 = c0[P_RHO], t0 = c0[P_T];
         const R pr0 = c0[S_PR], prr0 = c0[S_PRR];
         // gradients from differences to the centre value (sum_i W_i c_i = 0), which keeps
@@ -623,7 +720,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         for (int i = 0; i < 9; ++i) {
             const int ex = i % 3 - 1, ey = i / 3 - 1;
             if (ex == 0 && ey == 0) continue;
-            const R *cm = tile + slot_of(mx + ex, my + ey) * TS;
+            const R *cm = c0 + (ey * PT + ex) * TS;
             const R w = wst<R>(ex, ey);
             const R r = cm[P_RHO], t = cm[P_T];
             const R dr = r - r0, dT = t - t0;
@@ -678,6 +775,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         sh.nl[grp][1] = Fy;
         sh.nl[grp][2] = rEl;
         sh.active[grp] = valid ? 1 : 0;
+        sh.nreg[grp] = 0;
+        sh.npair[grp] = 0;
     }
     if (threadIdx.x < STEP_NB) {
         // exact FP64 sums of node j's stored populations, one node per lane of warp 0
@@ -712,7 +811,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
 
     // ---------------- phase 1: frame search (block lockstep) -----------------------
     // part: this lane's partial increments of the node's 18 populations in the latest stream
-    R *part = tile + step_tile_slots(TX, TS) * TS + grp * step_part_stride(LPN) + lane;
+    R *part = part_base + grp * step_part_stride(LPN) + lane;
     int it = 0;                                   // iterations of this block
     int my_it = 0, my_conv = 0, my_stall = 0;     // warp-0 lane bookkeeping for node threadIdx.x
     float my_res = 3.0e38f;                       // previous residual of that node
@@ -767,38 +866,49 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     }
                 }
                 __syncwarp(gmask);
+                if (lane == 0) sh.nreg[grp] += ncols * nrows;
                 R accf[9], accg[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) accf[i] = accg[i] = R(0);
                 const int x_lo = X + lo_x - 1, y_lo = Y + lo_y - 1;
                 const int nreg = ncols * nrows;
                 const float inc = 1.0f / (float)ncols;
+                // the whole region inside the staged tile (always for |v| dt < 1): slots by
+                // direct indexing from its corner, else per node with a global fallback
+                const int cu0 = x_lo - (X0 - HALO), cv0 = y_lo - (Y0 - HALO);
+                const bool staged_region = cu0 >= 0 && cu0 + ncols <= WT && cv0 >= 0 && cv0 + nrows <= HT;
+                const R *corner = staged_region ? tile + (cv0 * PT + cu0) * TS : tile;
                 // region nodes round-robin over the group's lanes
 #pragma unroll 1
                 for (int r = lane; r < nreg; r += LPN) {
                     const int cy = (int)(((float)r + 0.5f) * inc), cx = r - cy * ncols;
-                    const int sl = slot_of(x_lo + cx, y_lo + cy);
                     R v[24];
-                    if (sl >= 0) {
-                        load_slot24(tile + sl * TS, v);
+                    if (staged_region) {
+                        load_slot24(corner + (cy * PT + cx) * TS, v);
                     } else {
-                        const size_t nd = (size_t)bc_wrap(y_lo + cy, p.ny, p.bcy) * p.nx +
-                                          bc_wrap(x_lo + cx, p.nx, p.bcx);
-                        load_rec24(in + nd * SL, v);
-                        v[P_SQ] = sqrt_(v[P_TH]);
+                        const int sl = slot_of(x_lo + cx, y_lo + cy);
+                        if (sl >= 0) {
+                            load_slot24(tile + sl * TS, v);
+                        } else {
+                            const size_t nd = (size_t)bc_wrap(y_lo + cy, p.ny, p.bcy) * p.nx +
+                                              bc_wrap(x_lo + cx, p.nx, p.bcx);
+                            load_rec24(in + nd * SL, v);
+                            v[P_SQ] = sqrt_(v[P_TH]);
+                        }
                     }
                     const R thn = v[P_TH], sn = v[P_SQ];
                     const R qm1 = sizeof(R) == 8 ? sn * inv_s - R(1) : fdiv_(thn - th, (sn + s) * s);
                     const R wxg = (v[P_UX] - ux) * inv_s, wyg = (v[P_UY] - uy) * inv_s;
+                    // transfer increments per axis from h = e/2 and p = h (2 c_a + e):
+                    // E_0 = p - h, E_1 = -2 p, E_2 = p + h (the three l_k increments)
                     R Ex[3][3], Ey[3][3];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
                         const R ex = qm1 * R(a - 1) + wxg, ey = qm1 * R(a - 1) + wyg;
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            Ex[k][a] = ell_inc<R>(k, a, ex);
-                            Ey[k][a] = ell_inc<R>(k, a, ey);
-                        }
+                        const R hx = R(0.5) * ex, hy = R(0.5) * ey;
+                        const R px = hx * (R(2 * (a - 1)) + ex), py = hy * (R(2 * (a - 1)) + ey);
+                        Ex[0][a] = px - hx; Ex[1][a] = R(-2) * px; Ex[2][a] = px + hx;
+                        Ey[0][a] = py - hy; Ey[1][a] = R(-2) * py; Ey[2][a] = py + hy;
                     }
                     R wx[3], wy[3];
                     {
@@ -809,9 +919,11 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                             wy[j] = py[j];
                         }
                     }
-                    // the node's own populations are read from its staged slot
-                    region_family<R>(v + P_F, own + P_F, Ex, Ey, wx, wy, accf);
-                    region_family<R>(v + P_G, own + P_G, Ex, Ey, wx, wy, accg);
+                    // the node's own populations from its staged slot (16-byte loads)
+                    R ov[24];
+                    load_slot24(own, ov);
+                    region_family<R>(v + P_F, ov + P_F, Ex, Ey, wx, wy, accf);
+                    region_family<R>(v + P_G, ov + P_G, Ex, Ey, wx, wy, accg);
                 }
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
@@ -824,6 +936,7 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     a3 += accg[i];
                 }
             } else {
+            if (lane == 0) sh.npair[grp] += 1;
             // per-pair stream for wide regions (|v| dt of 2 nodes or more): rows of
             // directions (jy) in a rolled loop, the three directions of a row unrolled so
             // that their transfer coefficients are compile-time selections
@@ -1130,6 +1243,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
         const bool v = X0 + j % TX < p.nx && Y0 + j / TX < p.ny;
         const R T = sh.mac[j][6], rr = sh.mac[j][0], pr = sh.mac[j][9];
         warp_add(&stats->streams, v ? my_it : 0);
+        warp_add(&stats->region_nodes, v ? sh.nreg[j] : 0);
+        warp_add(&stats->pair_streams, v ? sh.npair[j] : 0);
         warp_add(&stats->nonconv, (v && !my_conv) ? 1 : 0);
         warp_add(&stats->stalled, (v && my_stall) ? 1 : 0);
         warp_add(&stats->clamped, (v && pr < q.p_floor) ? 1 : 0);
@@ -1142,13 +1257,23 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
     }
 }
 
-// One time step of one simulation: one block per tile.
+// One time step of one simulation: one block per tile.  (A persistent variant that
+// prefetched its next tile into a second staging buffer was slower on GB300: 2.64 against
+// 2.41 ms on the 2048 x 1024 droplet-shock; the block scheduler already overlaps one
+// block's staging with the others' work, and the second buffer takes L1 capacity.)
+// tmap: tensor map of `in` for the TMA staging of interior tiles (use_tma = 0: every tile
+// takes the per-chunk copies).
 template <typename R, int LPN>
 __global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(R, LPN)) k_pond_step(DevParams p, const R *__restrict__ in,
                                                              R *__restrict__ out, DevStats *stats,
-                                                             const R *nlsrc)
+                                                             const R *nlsrc, const __grid_constant__ CUtensorMap tmap,
+                                                             int use_tma)
 {
-    step_tile<R, LPN>(p, in, out, stats, blockIdx.x, nlsrc);
+    extern __shared__ __align__(128) unsigned char step_dyn_smem[];
+    R *tile = reinterpret_cast<R *>(step_dyn_smem);
+    step_tile<R, LPN>(p, in, out, stats, blockIdx.x, nlsrc, tile,
+                      tile + (size_t)step_tile_slots(p.tile_x, Slot<R>::stride) * Slot<R>::stride, false,
+                      use_tma ? &tmap : nullptr);
 }
 
 // A simulation of a batch as one launch sees it: parameters, the buffers this step reads
@@ -1179,7 +1304,10 @@ __global__ void __launch_bounds__(STEP_NB *LPN, STEP_MIN_BLOCKS(R, LPN)) k_pond_
         s_stats = descs[w.x].stats;
     }
     __syncthreads();
-    step_tile<R, LPN>(sp, s_in, s_out, s_stats, w.y, s_in);
+    extern __shared__ __align__(128) unsigned char step_dyn_smem[];
+    R *tile = reinterpret_cast<R *>(step_dyn_smem);
+    step_tile<R, LPN>(sp, s_in, s_out, s_stats, w.y, s_in, tile,
+                      tile + (size_t)step_tile_slots(sp.tile_x, Slot<R>::stride) * Slot<R>::stride, false);
 }
 
 }  // namespace pond

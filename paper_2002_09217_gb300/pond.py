@@ -58,7 +58,8 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("node_updates", C.c_int64), ("streams", C.c_int64),
                 ("nonconverged", C.c_int64), ("clamped", C.c_int64), ("nonfinite", C.c_int64),
-                ("stalled", C.c_int64), ("block_streams", C.c_int64), ("max_streams", C.c_int64)]
+                ("stalled", C.c_int64), ("block_streams", C.c_int64), ("max_streams", C.c_int64),
+                ("timeouts", C.c_int64), ("region_nodes", C.c_int64), ("pair_streams", C.c_int64)]
 
 
 class PondError(RuntimeError):
