@@ -49,6 +49,9 @@ constexpr int HALO = 3;       // staged halo width (stencil reach for |v| dt < 1
 // that the region stream handles: 4 + the spread of the departure points' floors, 5 for
 // |v| dt < 1; wider regions take the per-pair stream.
 constexpr int REGION_MAX = 8;
+// Mixed form: a frame-search residual below this multiple of tol that no longer halves is
+// taken as the FP32 rounding floor (the EoS cancels up to ~200x inside interfaces).
+constexpr float STALL_TOL_FACTOR = 16.0f;
 // resident blocks per SM the register budget is sized for: in FP32 five blocks of 128
 // threads (8 lanes per node, about 96 registers) or two of 256 (16 lanes); in FP64 one,
 // so that its wider values stay in registers
@@ -1023,7 +1026,13 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                 // FP32 form only: the streamed moments carry FP32 rounding that the EoS
                 // cancellation inside interfaces can lift above tol; once a corrector no
                 // longer halves the residual the iteration has reached that floor and stops.
-                const bool stall = sizeof(R) == 4 && it >= 2 && !conv && res > 0.5f * my_res;
+                // Only a residual within STALL_TOL_FACTOR x tol counts as that floor: a larger
+                // one that fails to halve once (the pressure floor's kink in
+                // theta* = max(p, p_floor)/(rho T_L) can do that) keeps iterating, since
+                // stopping there left the gauge up to 8 % off and single steps 3.6e-3 off the
+                // converged result inside a compressed sub-spinodal droplet.
+                const bool stall = sizeof(R) == 4 && it >= 2 && !conv && res > 0.5f * my_res &&
+                                   res < STALL_TOL_FACTOR * p.tol_f;
                 my_res = res;
                 my_it = it;
                 if (conv || bad || stall || it >= p.max_iter) {

@@ -329,7 +329,7 @@ def droplet_shock(nx=2048, ny=1024, Tr=0.8, radius=80.0, xc=600.0, x_shock=300.0
     rho = rv + (rl - rv) * drop + (sh["rho1"] - rv) * post
     ux = sh["u1"] * post
     T = Tr * Tc + (sh["T1"] - Tr * Tc) * post
-    return Workload("dropletshock%dx%d" % (nx, ny), nx, ny, 1, 1, Tr, kappa, tau, sh["dt"], steps,
+    return Workload("dropletshock%dx%d" % (nx, ny), nx, ny, 1, 1, Tr, kappa, tau, sh["dt_droplet"], steps,
                     rho, ux, np.zeros((ny, nx)), T)
 
 

@@ -128,7 +128,12 @@ class Server:
                 for it in [it for it in running[k] if it["left"] == 0]:
                     sim = it["sim"]
                     self.batches[k].remove(sim)
-                    fields = sim.moments() if self.keep_fields else None
+                    try:
+                        fields = sim.moments() if self.keep_fields else None
+                    except pond.PondError as e:
+                        if e.status != 6:
+                            raise
+                        fields = None            # a diverged request: reported, not returned
                     status = sim.stats()
                     status["flags"] = [f for f, _ in sim.flags]
                     if self.keep_state:

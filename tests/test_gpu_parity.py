@@ -2,9 +2,8 @@
 
 Element-by-element parity on seeded inputs at sizes the oracle finishes in
 seconds (several 128-node launch tiles plus a ragged tail), on the full
-128x4 slab for its 2000 steps, and on the other full-size workloads through
-one-step checks at sampled nodes (the oracle steps those nodes from the GPU's
-own previous state).  Bars: FP64 <= 1e-11, mixed FP32/FP64 <= 1e-5 relative
+128x4 slab for its 2000 steps (the other workloads at their own step counts are in
+test_gpu_full_length.py).  Bars: FP64 <= 1e-11, mixed FP32/FP64 <= 1e-5 relative
 L-infinity per field (rho, uhat_x, uhat_y, T, p).
 """
 import dataclasses
@@ -15,7 +14,7 @@ import pytest
 import oracle
 from paper_2002_09217_gb300 import inputs
 
-from parity_util import TOL, oracle_run, params_of, rel_linf, sample_nodes, state_fields
+from parity_util import TOL, oracle_run, rel_linf
 
 pytestmark = pytest.mark.gpu
 
@@ -109,45 +108,6 @@ def test_shocktube_reduced_full_run(pond, precision):
     got, _ = gpu_run(pond, w, precision)
     err = rel_linf(got, ref)
     assert max(err.values()) <= TOL[precision], err
-
-
-def one_step_sampled(pond, w, precision, steps, nsample=64):
-    """Run the GPU to `steps`, then compare its next step at sampled nodes with the
-    oracle stepping those nodes from the GPU's own state."""
-    with pond.from_workload(w, precision=precision) as sim:
-        sim.init_fields(*w.fields())
-        sim.step(steps)
-        prev = sim.get_state()
-        sim.step(1)
-        nxt = sim.get_state().reshape(25, -1)
-        st = sim.stats()
-    P = params_of(w, tol=(1e-12 if precision == "fp64" else 1e-6))
-    nodes = sample_nodes(w.nx, w.ny, nsample)
-    rows = oracle.step_nodes(P, prev, nodes)
-    got = state_fields(P, nxt[:, nodes].T)
-    ref = state_fields(P, rows)
-    return rel_linf(got, ref), st
-
-
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_shocktube2048x4_sampled_at_full_steps(pond, precision):
-    w = inputs.shock_tube()
-    err, st = one_step_sampled(pond, w, precision, w.steps - 1)
-    assert max(err.values()) <= TOL[precision], err
-    assert st["nonfinite"] == 0
-
-
-def test_droplet512_sampled(pond):
-    w = inputs.droplet()
-    err, st = one_step_sampled(pond, w, "mixed", 1000)
-    assert max(err.values()) <= TOL["mixed"], err
-    assert st["nonfinite"] == 0
-
-
-def test_dropletshock2048x1024_sampled(pond):
-    w = inputs.droplet_shock()
-    err, st = one_step_sampled(pond, w, "mixed", 200)
-    assert max(err.values()) <= TOL["mixed"], err
 
 
 def test_conservation_sums_match_oracle_state(pond):
