@@ -361,22 +361,36 @@ def end_to_end(w, pond, torch, stream, precision, shape, n_seg: int, reps: int) 
             "note": "per call: init from pinned host (4 fields), %d steps, 5 fields back to host" % n_seg}
 
 
-def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
-    """Bounded sample of the serving workload: the seeded request mix with sides capped
-    at 256, step counts scaled by 1/10 and two-phase temperatures at or above 0.8 T_cr,
-    arrivals at 200 requests/s, device budget 8 GiB per GPU, served by the batching
-    server; with several ranks each serves its placement share (no data exchange)."""
+def serving_run(torch, rank: int, ws: int, n_req: int = 32, side_cap: int = 256,
+                steps_scale: dict | None = None, tr_min: float = 0.8, rate: float = 200.0,
+                budget: int = 8 << 30, check: int = 0) -> dict:
+    """The seeded serving mix served by the batching server, scaled as stated in the
+    returned `sample` (sides capped at side_cap, step counts times steps_scale per
+    precision, temperatures raised to tr_min; None/1.0 leaves a quantity as specified).
+    With several ranks each serves its placement share (no data exchange).  `check`
+    requests (a seeded subset, half of each precision) keep their final state for the
+    accuracy check (serving_accuracy)."""
     import dataclasses
+    import random
     from paper_2002_09217_gb300 import inputs, placement, serving
-    reqs = inputs.serving_requests(n=n_req, rate=200.0)
-    reqs = [dataclasses.replace(r, side=min(r.side, 256), steps=max(100, r.steps // 10),
-                                T_r=max(r.T_r, 0.8)) for r in reqs]
+    steps_scale = steps_scale or {"mixed": 0.1, "fp64": 0.1}
+    reqs = inputs.serving_requests(n=n_req, rate=rate)
+    reqs = [dataclasses.replace(r, side=min(r.side, side_cap) if side_cap else r.side,
+                                steps=max(100, int(round(r.steps * steps_scale[r.precision]))),
+                                T_r=max(r.T_r, tr_min) if tr_min else r.T_r) for r in reqs]
     mine = placement.my_share(reqs, rank, ws) if ws > 1 else reqs
-    server = serving.Server(hbm_budget=8 << 30, chunk=50, keep_fields=False)
+    keep = set()
+    if check:
+        rng = random.Random(20020921)
+        for prec in ("mixed", "fp64"):
+            ids = [r.rid for r in mine if r.precision == prec]
+            keep |= set(rng.sample(ids, min(len(ids), check // 2)))
+    server = serving.Server(hbm_budget=budget, chunk=50, keep_fields=False, keep_state=keep)
     t0 = time.perf_counter()
     results = server.run(mine)
     wall = time.perf_counter() - t0
     server.close()
+    util = server.used_seconds / max(1e-9, wall) / budget
     if ws > 1:
         import torch.distributed as dist
         gathered = [None] * ws
@@ -385,8 +399,69 @@ def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
         wall = max(w for _, w in gathered)
     summ = serving.summarize(results, wall)
     summ["nonfinite_requests"] = sum(1 for r in results if r.status.get("nonfinite", 0))
-    summ["sample"] = ("%d requests of the seeded mix, side <= 256, steps/10, T_r >= 0.8, "
-                      "mixed and FP64 50/50, Poisson 200/s, 8 GiB budget" % n_req)
+    by_rid = {q.rid: q for q in reqs}
+    summ["nonfinite"] = [{"rid": r.rid, "kind": by_rid[r.rid].kind, "T_r": float(by_rid[r.rid].T_r),
+                          "mach": float(by_rid[r.rid].mach), "side": by_rid[r.rid].side, "steps": r.steps,
+                          "precision": r.precision} for r in results if r.status.get("nonfinite", 0)]
+    summ["budget_bytes"] = budget
+    summ["budget_mean_use"] = util
+    summ["budget_peak_use"] = server.peak_bytes / budget
+    summ["refused_after_create"] = server.refused
+    scaled = ", ".join("%s steps x %g" % (k, v) for k, v in steps_scale.items() if v != 1.0) or "steps as specified"
+    summ["sample"] = ("%d requests of the seeded mix (sides %s, %s, T_r %s), mixed and FP64 "
+                      "as drawn, Poisson %g/s, %.1f GiB budget" % (
+                          n_req, "<= %d" % side_cap if side_cap else "64..1024 as drawn", scaled,
+                          ">= %g" % tr_min if tr_min else "0.70..0.95 as drawn", rate, budget / 2 ** 30))
+    summ["_kept"] = [r for r in results if r.state is not None]
+    return summ
+
+
+def serving_accuracy(pond, kept, nsample: int = 64) -> dict:
+    """One-step check of served results: each kept final state is stepped once more on the
+    GPU (alone, its own precision) and by the FP64 oracle at sampled nodes (half in
+    interfaces and fronts); relative L-infinity per request against the bar of its form."""
+    import numpy as np
+    import oracle
+    bars = {"mixed": 1e-5, "fp64": 1e-11}
+    rows = []
+    for r in kept:
+        w = r.workload
+        P = oracle.Params(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R, delta=w.delta,
+                          kappa=w.kappa, tau=w.tau, dt=w.dt, k_cond=w.k_cond, p_floor=w.p_floor,
+                          tol=1e-12 if r.precision == "fp64" else 1e-6, max_iter=20)
+        st = r.state.reshape(25, -1)
+        if not np.isfinite(st).all():
+            rows.append({"rid": r.rid, "precision": r.precision, "finite": False})
+            continue
+        rho = st[21].reshape(w.ny, w.nx)
+        g = (np.abs(np.roll(rho, -1, 1) - np.roll(rho, 1, 1)) + np.abs(np.roll(rho, -1, 0) - np.roll(rho, 1, 0))).ravel()
+        rng = np.random.default_rng(r.rid)
+        steep = rng.choice(np.argsort(g)[::-1][: 8 * nsample], nsample // 2, replace=False)
+        nodes = np.unique(np.concatenate([steep, rng.choice(w.nodes, nsample // 2, replace=False)]))
+        with pond.from_workload(w, precision=r.precision) as sim:
+            sim.set_state(r.state)
+            sim.step(1)
+            got = sim.get_state().reshape(25, -1)[:, nodes].T
+        ref = oracle.step_nodes(P, r.state, nodes)
+        err = 0.0
+        for k, col in (("rho", 21), ("T", 22)):
+            err = max(err, float(np.abs(got[:, col] - ref[:, col]).max() / np.abs(ref[:, col]).max()))
+        cs = float(np.sqrt(np.max(np.abs(ref[:, 18]) * (1.0 / 3.0))))
+        for col in (23, 24):
+            err = max(err, float(np.abs(got[:, col] - ref[:, col]).max() / max(np.abs(ref[:, col]).max(), cs)))
+        rows.append({"rid": r.rid, "precision": r.precision, "side": w.nx, "steps": r.steps, "T_r": round(w.T_r, 2),
+                     "linf": err, "within_bar": err <= bars[r.precision], "finite": True})
+    return {"checked": len(rows), "within_bar": sum(1 for x in rows if x.get("within_bar")),
+            "max_linf": {p: max([x["linf"] for x in rows if x["precision"] == p and x.get("finite")] or [0.0])
+                         for p in ("mixed", "fp64")},
+            "requests": rows, "nodes_per_request": nsample}
+
+
+def serving_sample(torch, rank: int, ws: int, n_req: int = 32) -> dict:
+    """Bounded sample for the default bench run: sides <= 256, steps / 10, T_r >= 0.8,
+    arrivals at 200 requests/s, 8 GiB budget."""
+    summ = serving_run(torch, rank, ws, n_req=n_req)
+    summ.pop("_kept", None)
     return summ
 
 
@@ -521,6 +596,12 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 form, the other workloads / experiments and the FMA peak")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle sample steps (0 = auto)")
+    ap.add_argument("--serving-config5", action="store_true",
+                    help="serve the 256-request mix (sides, temperatures and mixed step counts as "
+                         "drawn; FP64 step counts / --fp64-steps-div) and print its summary line")
+    ap.add_argument("--fp64-steps-div", type=float, default=10.0)
+    ap.add_argument("--serving-rate", type=float, default=0.5, help="Poisson arrivals per second")
+    ap.add_argument("--serving-budget-gib", type=float, default=8.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = dist_env()
@@ -585,6 +666,26 @@ def main():
 
     from paper_2002_09217_gb300 import autotune, pond
     torch.cuda.set_device(local)
+    if args.serving_config5:
+        # the serving configuration: 256 seeded requests, served by footprint admission and
+        # continuous batching; then a one-step oracle check of a seeded subset of results
+        clocks = ClockSampler(local)
+        with clocks:
+            summ = serving_run(torch, rank, ws, n_req=256, side_cap=0,
+                               steps_scale={"mixed": 1.0, "fp64": 1.0 / args.fp64_steps_div}, tr_min=0.0,
+                               rate=args.serving_rate, budget=int(args.serving_budget_gib * 2 ** 30), check=16)
+        kept = summ.pop("_kept")
+        if rank == 0:
+            line = {"metric": "serving sims/s", "value": summ["sims_per_s"], "unit": "sims/s", "n_gpus": ws,
+                    "higher_is_better": True, "data": "synthetic", "config": {"workload": "serving256"},
+                    "serving": summ, "clocks": clocks.summary()}
+            if not args.no_cpu:
+                line["accuracy"] = serving_accuracy(pond, kept)
+            print(json.dumps(line), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

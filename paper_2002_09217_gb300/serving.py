@@ -70,7 +70,9 @@ class Server:
         self.chunk = int(chunk)
         self.max_resident = int(max_resident)
         self.keep_fields = keep_fields
-        self.keep_state = keep_state   # also return each request's full final state
+        # also return the full final state of every request (True) or of the requests
+        # whose ids are in a given set
+        self.keep_state = keep_state
         self.peak_bytes = 0
         # the mixed stream at higher priority: an FP64 group launch holds tens of thousands
         # of slow blocks, and the block scheduler would otherwise dispatch them ahead of the
@@ -114,8 +116,13 @@ class Server:
         used = 0
         results = []
         t0 = time.perf_counter()
+        self.used_seconds = 0.0        # integral of resident bytes over time (byte-seconds)
+        t_prev = t0
         while pending or waiting or any(running.values()):
-            now = time.perf_counter() - t0
+            t_now = time.perf_counter()
+            self.used_seconds += used * (t_now - t_prev)
+            t_prev = t_now
+            now = t_now - t0
             while pending and pending[0][0] <= now:
                 waiting.append(heapq.heappop(pending)[2])
             busy = False
@@ -136,7 +143,8 @@ class Server:
                         fields = None            # a diverged request: reported, not returned
                     status = sim.stats()
                     status["flags"] = [f for f, _ in sim.flags]
-                    if self.keep_state:
+                    ks = self.keep_state
+                    if ks is True or (ks and it["req"].rid in ks):
                         it["state"] = sim.get_state()
                     sim.close()
                     req = it["req"]

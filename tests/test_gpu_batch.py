@@ -164,3 +164,33 @@ def test_batch_with_d2q16_members_equals_alone(pond):
     batch.close()
     for s in sims:
         s.close()
+
+
+def test_served_states_pass_a_one_step_oracle_check(pond):
+    """Accuracy of served results: the final states the server returns (mixed and FP64
+    requests of the seeded mix, temperatures as drawn, 0.70..0.95) are stepped once more
+    on the GPU and by the oracle at sampled nodes; each stays within its form's bar."""
+    import oracle
+    from parity_util import TOL, params_of, rel_linf, sample_nodes, state_fields
+    from paper_2002_09217_gb300 import serving
+    reqs = inputs.serving_requests(n=8, rate=200.0, seed=91)
+    reqs = [dataclasses.replace(r, side=min(r.side, 64), steps=30 + (r.steps % 50)) for r in reqs]
+    server = serving.Server(hbm_budget=256 << 20, chunk=11, keep_fields=False, keep_state=True)
+    results = server.run(reqs)
+    server.close()
+    assert len(results) == len(reqs)
+    precs = set()
+    for res in results:
+        w = res.workload
+        assert np.isfinite(res.state).all(), res.rid
+        with pond.from_workload(w, precision=res.precision) as sim:
+            sim.set_state(res.state)
+            sim.step(1)
+            nxt = sim.get_state().reshape(25, -1)
+        P = params_of(w, tol=(1e-12 if res.precision == "fp64" else 1e-6))
+        nodes = sample_nodes(w.nx, w.ny, 48)
+        rows = oracle.step_nodes(P, res.state, nodes)
+        err = rel_linf(state_fields(P, nxt[:, nodes].T), state_fields(P, rows))
+        assert max(err.values()) <= TOL[res.precision], (res.rid, res.precision, err)
+        precs.add(res.precision)
+    assert precs == {"mixed", "fp64"}

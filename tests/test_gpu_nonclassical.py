@@ -37,3 +37,34 @@ def test_classical_tube_rarefaction_fan(experiments, precision):
     assert e["left_at"] < h["left_at"]
     assert e["left_peak"] < 0.65 * h["left_peak"], res
     assert e["right_peak"] > 0.85 * h["right_peak"], res
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("name,bar", [("I", 2e-3), ("fig4", 7e-3)])
+def test_tubes_converge_to_the_exact_vdw_riemann_solution(experiments, precision, name, bar):
+    """The GPU's shock tubes at t* against the exact van der Waals Riemann solution
+    (tests/vdw_riemann.py; case I: fan + shock, Fig. 4: rarefaction shock + compression
+    fan): relative L1(rho) below the bar on 2048 nodes and falling from 1024 nodes."""
+    import json
+    import os
+    import numpy as np
+    from oracle import thermo
+    from paper_2002_09217_gb300 import pond
+    import vdw_riemann as vr
+    tab = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "..",
+                                      "paper_2002_09217_gb300", "workloads.json")))["nonclassical"]
+    c = tab["cases"][name]
+    L, R = c["left"], c["right"]
+    rp = vr.Riemann(c["delta"], (L["rho"], 0.0, thermo.pressure(L["rho"], L["T"])),
+                    (R["rho"], 0.0, thermo.pressure(R["rho"], R["T"])))
+    l1 = []
+    for nx in (1024, 2048):
+        w = inputs.nonclassical_tube(name, nx=nx)
+        with pond.from_workload(w, precision=precision) as sim:
+            sim.init_fields(*w.fields())
+            sim.step(w.steps)
+            rho = sim.moments()["rho"][0]
+        re, _, _ = rp.profile(np.arange(nx) + 0.5, w.steps * w.dt, nx / 2)
+        l1.append(float(np.abs(rho - re).mean() / np.abs(re).mean()))
+    print(name, precision, l1)
+    assert l1[1] < bar and l1[1] < 0.8 * l1[0], l1
