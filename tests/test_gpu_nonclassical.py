@@ -40,11 +40,12 @@ def test_classical_tube_rarefaction_fan(experiments, precision):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-@pytest.mark.parametrize("name,bar", [("I", 2e-3), ("fig4", 7e-3)])
+@pytest.mark.parametrize("name,bar", [("I", 2e-3), ("fig4", 7e-3), ("II", 8e-3)])
 def test_tubes_converge_to_the_exact_vdw_riemann_solution(experiments, precision, name, bar):
     """The GPU's shock tubes at t* against the exact van der Waals Riemann solution
     (tests/vdw_riemann.py; case I: fan + shock, Fig. 4: rarefaction shock + compression
-    fan): relative L1(rho) below the bar on 2048 nodes and falling from 1024 nodes."""
+    fan, case II: composite waves on both sides): relative L1(rho) below the bar on 2048
+    nodes and falling from 1024 nodes."""
     import json
     import os
     import numpy as np

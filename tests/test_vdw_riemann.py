@@ -1,7 +1,9 @@
 """The exact van der Waals Riemann solver (tests/vdw_riemann.py) and the oracle's shock
-tubes against it: the SM's case I (delta = 0.329, classical: a fan and a shock) and the
+tubes against it: the SM's case I (delta = 0.329, classical: a fan and a shock), the
 anomalous tube of the main text's Fig. 4 (delta = 0.0125, Gamma < 0: a rarefaction shock
-and a compression fan).
+and a compression fan) and the SM's case II (delta = 0.0125, Gamma changes sign along both
+waves: a fan ended by a shock that is sonic ahead, and a shock sonic behind followed by a
+compression fan).
 
 The solver is pinned by what it does not compute itself: the fundamental derivative of
 its isentropes against the SM's table, lab-frame Rankine-Hugoniot flux balances of every
@@ -37,7 +39,7 @@ def problem(name):
 @pytest.fixture(scope="module")
 def solved():
     out = {}
-    for name in ("I", "fig4"):
+    for name in ("I", "fig4", "II"):
         c, left, right = problem(name)
         out[name] = (c, left, right, vr.Riemann(c["delta"], left, right))
     return out
@@ -69,7 +71,9 @@ def test_wave_structures(solved):
     # the left-moving wave expands the fluid through a shock, the right-moving one
     # compresses it through a fan
     assert d["wave1"] == ["shock"] and d["wave3"] == ["fan"]
-    for name in ("I", "fig4"):
+    d = solved["II"][3].describe()
+    assert d["wave1"] == ["fan", "shock"] and d["wave3"] == ["shock", "fan"]
+    for name in ("I", "fig4", "II"):
         rp = solved[name][3]
         assert rp.mismatch < 1e-12
         assert solved[name][2][2] < rp.ps < solved[name][1][2]
@@ -84,7 +88,7 @@ def _conserved(gas, rho, u, p):
 def test_shocks_balance_the_lab_frame_fluxes(solved):
     """F(U_b) - F(U_a) = sigma (U_b - U_a) for mass, momentum and total energy."""
     n = 0
-    for name in ("I", "fig4"):
+    for name in ("I", "fig4", "II"):
         rp = solved[name][3]
         for fam, waves in ((-1, rp.w1), (+1, rp.w3)):
             for w in waves:
@@ -96,13 +100,13 @@ def test_shocks_balance_the_lab_frame_fluxes(solved):
                 Ub, Fb = _conserved(rp.g, 1.0 / vb, ub, pb)
                 np.testing.assert_allclose(Fb - Fa, sigma * (Ub - Ua), rtol=1e-10, atol=1e-13)
                 n += 1
-    assert n == 2
+    assert n == 4
 
 
 def test_fans_are_self_similar_and_isentropic(solved):
     """Inside a fan of family k at x/t = xi: u + s c = xi, and T (v - b)^delta is that of the
     fan's base state."""
-    for name in ("I", "fig4"):
+    for name in ("I", "fig4", "II"):
         c, left, right, rp = solved[name]
         g = rp.g
         for piece in rp.seg:
@@ -117,7 +121,24 @@ def test_fans_are_self_similar_and_isentropic(solved):
                 assert g.T(v, p) * (v - g.b) ** g.d == pytest.approx(ent0, rel=1e-10)
 
 
-@pytest.mark.parametrize("name,bar", [("I", 3e-3), ("fig4", 6e-3)])
+def test_composite_waves_are_sonic_where_their_pieces_meet(solved):
+    """Case II: the left wave's shock moves at the sound speed of the fan state it starts
+    from (m = C ahead) and leaves a subsonic state; the right wave's shock leaves a state
+    that is exactly sonic (m = C behind), from which the compression fan starts."""
+    rp = solved["II"][3]
+    g = rp.g
+    fan, shock = rp.w1
+    (va, pa, _), (vb, pb, _), m = shock[1], shock[2], shock[3]
+    base = fan[1]
+    assert m == pytest.approx(g.C(va, base[0], base[1]), rel=1e-9)
+    assert m <= g.C(vb, vb, pb) * (1 + 1e-9)
+    shock, fan = rp.w3
+    (va, pa, _), (vb, pb, _), m = shock[1], shock[2], shock[3]
+    assert m == pytest.approx(g.C(vb, vb, pb), rel=1e-9)
+    assert fan[1][0] == vb
+
+
+@pytest.mark.parametrize("name,bar", [("I", 3e-3), ("fig4", 6e-3), ("II", 6e-3)])
 def test_exact_solution_is_the_limit_of_a_finite_volume_solution(solved, name, bar):
     c, left, right, rp = solved[name]
     t = c["t_star"] / TAB["U_ch"]
@@ -129,11 +150,12 @@ def test_exact_solution_is_the_limit_of_a_finite_volume_solution(solved, name, b
     assert l1[1] < bar and l1[1] < 0.8 * l1[0], l1
 
 
-@pytest.mark.parametrize("name,bar", [("I", 3.5e-3), ("fig4", 1.1e-2)])
+@pytest.mark.parametrize("name,bar", [("I", 3.5e-3), ("fig4", 1.1e-2), ("II", 1.2e-2)])
 def test_oracle_tubes_converge_to_the_exact_solution(solved, name, bar):
     """The oracle's shock tubes at t* on 200 and 400 nodes: relative L1(rho) against the
     exact solution below the bar and falling with refinement (measured: case I 4.6e-3,
-    2.7e-3, 1.5e-3 at 200, 400, 800 nodes; Fig. 4 1.4e-2, 8.7e-3, 5.6e-3)."""
+    2.7e-3, 1.5e-3 at 200, 400, 800 nodes; Fig. 4 1.4e-2, 8.7e-3, 5.6e-3; case II 1.5e-2,
+    9.5e-3, 6.7e-3)."""
     rp = solved[name][3]
     l1 = []
     for nx in (200, 400):

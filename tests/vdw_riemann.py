@@ -128,23 +128,43 @@ class Family:
     # -- the wave to pressure p* --------------------------------------------------------
     def to(self, ps):
         """(u*, v*, pieces) of the wave from K to pressure ps.  Pieces run from K outward:
-        ("fan", base (v, p, u), v_a, v_b) or ("shock", (v, p, u) ahead, (v, p, u) behind, m)."""
-        g, vK, pK, uK = self.g, self.vK, self.pK, self.uK
-        if abs(ps - pK) <= 1e-15 * abs(pK):
-            return uK, vK, []
-        expand = ps < pK
-        gK = g.gamma(vK, pK)
-        fan_first = (gK > 0) == expand
-        if fan_first:
-            vs = _v_on(lambda v: g.p_s(v, vK, pK), ps, vK, self._limit_s(expand))
-            if self.fan_ok(vK, pK, vs):
-                return self.fan_u(vK, pK, uK, vs), vs, [("fan", (vK, pK, uK), vK, vs)]
-            return self._fan_shock(ps, expand)
-        vs = _v_on(lambda v: g.p_H(v, vK, pK), ps, vK, self._limit_h(expand))
-        if self.liu_ok(vK, pK, vs):
-            us = self.shock_u(vK, pK, uK, vs, ps)
-            return us, vs, [("shock", (vK, pK, uK), (vs, ps, us), math.sqrt(self.m2(vK, pK, vs, ps)))]
-        return self._shock_fan(ps, expand)
+        ("fan", base (v, p, u), v_a, v_b) or ("shock", (v, p, u) ahead, (v, p, u) behind, m).
+        Built by marching from K: in fan mode (Gamma has the sign that makes this direction
+        a fan) along the isentrope; where an inflection lies before ps the fan ends at M and
+        a shock sonic at M follows, either to ps (if the state behind it is subsonic) or to
+        the point where it is sonic behind as well, after which the march goes on with a
+        fan; in shock mode along the Hugoniot, to ps if Liu's condition holds, else to the
+        point where the state behind becomes sonic, after which a fan follows."""
+        g = self.g
+        v, p, u = self.vK, self.pK, self.uK
+        if abs(ps - p) <= 1e-15 * abs(p):
+            return u, v, []
+        expand = ps < p
+        pieces = []
+        for _ in range(8):
+            fan_mode = (g.gamma(v, p) > 0) == expand
+            if fan_mode:
+                vend = _v_on(lambda x: g.p_s(x, v, p), ps, v, self._limit_s(expand, v))
+                v_inf = self._inflection(v, p, vend)
+                if v_inf is None:
+                    pieces.append(("fan", (v, p, u), v, vend))
+                    return self.fan_u(v, p, u, vend), vend, pieces
+                done, nxt = self._fan_then_shock(v, p, u, ps, v_inf, expand, pieces)
+                if done:
+                    return nxt[2], nxt[0], pieces
+                v, p, u = nxt
+            else:
+                vend = _v_on(lambda x: g.p_H(x, v, p), ps, v, self._limit_h(expand, v))
+                if self.liu_ok(v, p, vend) and self._subsonic_behind(v, p, vend, ps):
+                    ue = self.shock_u(v, p, u, vend, ps)
+                    pieces.append(("shock", (v, p, u), (vend, ps, ue), math.sqrt(self.m2(v, p, vend, ps))))
+                    return ue, vend, pieces
+                vM = self._post_sonic_point(v, p, vend)
+                pM = g.p_H(vM, v, p)
+                uM = self.shock_u(v, p, u, vM, pM)
+                pieces.append(("shock", (v, p, u), (vM, pM, uM), math.sqrt(self.m2(v, p, vM, pM))))
+                v, p, u = vM, pM, uM
+        raise NotImplementedError("wave with more than eight pieces")
 
     def _limit_s(self, expand, vB=None):
         """Far end of a search along the isentrope from vB (default K): large v for
@@ -162,54 +182,101 @@ class Family:
         vmin = (2.0 * g.b / g.d + vB) / (2.0 / g.d + 1.0)
         return vmin + 1e-9 * (vB - vmin)
 
-    def _fan_shock(self, ps, expand):
-        """Fan from K to M, then a shock M -> S that is sonic at M (m(M, S) = C(M))."""
-        g, vK, pK, uK = self.g, self.vK, self.pK, self.uK
-        vend = _v_on(lambda v: g.p_s(v, vK, pK), ps, vK, self._limit_s(expand))
-        # inflection on K's isentrope: the fan can extend at most to it
-        grid = np.linspace(vK, vend, 400)
-        gam = [g.gamma(v, g.p_s(v, vK, pK)) for v in grid]
-        k = next(i for i in range(1, len(grid)) if (gam[i] > 0) != (gam[0] > 0))
-        v_inf = brentq(lambda v: g.gamma(v, g.p_s(v, vK, pK)), grid[k - 1], grid[k], xtol=1e-15)
+    def _inflection(self, vB, pB, vend, n=400):
+        """First v between vB and vend where Gamma on the isentrope of B changes sign."""
+        g = self.g
+        grid = np.linspace(vB, vend, n)
+        gam = [g.gamma(x, g.p_s(x, vB, pB)) for x in grid]
+        for i in range(1, n):
+            if (gam[i] > 0) != (gam[0] > 0):
+                return brentq(lambda x: g.gamma(x, g.p_s(x, vB, pB)), grid[i - 1], grid[i], xtol=1e-15)
+        return None
 
-        def sonic_gap(vM):
-            pM = g.p_s(vM, vK, pK)
-            vS = _v_on(lambda v: g.p_H(v, vM, pM), ps, vM, self._limit_h(expand, vM))
-            return self.m2(vM, pM, vS, ps) - g.C(vM, vK, pK) ** 2, vS
+    def _subsonic_behind(self, va, pa, vb, pb):
+        """Lax bound behind a shock: m <= C at the state behind it."""
+        return self.m2(va, pa, vb, pb) <= self.g.C(vb, vb, pb) ** 2 * (1.0 + 1e-9)
 
-        lo, hi = vK + (v_inf - vK) * 1e-9, v_inf - (v_inf - vK) * 1e-9
-        vM = brentq(lambda x: sonic_gap(x)[0], lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
-        pM = g.p_s(vM, vK, pK)
-        _, vS = sonic_gap(vM)
-        uM = self.fan_u(vK, pK, uK, vM)
-        uS = self.shock_u(vM, pM, uM, vS, ps)
-        return uS, vS, [("fan", (vK, pK, uK), vK, vM),
-                        ("shock", (vM, pM, uM), (vS, ps, uS), math.sqrt(self.m2(vM, pM, vS, ps)))]
+    def _post_sonic_point(self, vA, pA, vend, n=800):
+        """First point M on the Hugoniot of A toward vend where m(A, M) = C(M) (the Rayleigh
+        line tangent to M's isentrope)."""
+        g = self.g
 
-    def _shock_fan(self, ps, expand):
-        """Shock K -> M that is sonic behind (Rayleigh line tangent to M's isentrope), then
-        a fan from M to ps."""
-        g, vK, pK, uK = self.g, self.vK, self.pK, self.uK
+        def gap(x):
+            px = g.p_H(x, vA, pA)
+            return self.m2(vA, pA, x, px) - g.C(x, x, px) ** 2
 
-        def gap(vM):
-            pM = g.p_H(vM, vK, pK)
-            return self.m2(vK, pK, vM, pM) - g.C(vM, vM, pM) ** 2
+        grid = np.linspace(vA, vend, n)[1:]
+        vals = [gap(x) for x in grid]
+        for i in range(1, len(grid)):
+            if (vals[i] > 0) != (vals[0] > 0):
+                return brentq(gap, grid[i - 1], grid[i], xtol=1e-15, rtol=1e-15, maxiter=500)
+        raise NotImplementedError("no sonic point on the Hugoniot before the target")
 
-        vH = _v_on(lambda v: g.p_H(v, vK, pK), ps, vK, self._limit_h(expand))
-        grid = np.linspace(vK, vH, 800)[1:]
-        vals = [gap(v) for v in grid]
-        k = next(i for i in range(1, len(grid)) if (vals[i] > 0) != (vals[0] > 0))
-        vM = brentq(gap, grid[k - 1], grid[k], xtol=1e-15, rtol=1e-15, maxiter=500)
-        pM = g.p_H(vM, vK, pK)
-        if not self.liu_ok(vK, pK, vM):
-            raise NotImplementedError("wave with more than one inflection")
-        uM = self.shock_u(vK, pK, uK, vM, pM)
-        vS = _v_on(lambda v: g.p_s(v, vM, pM), ps, vM, self._limit_s(expand, vM))
-        if not self.fan_ok(vM, pM, vS):
-            raise NotImplementedError("wave with more than one inflection")
-        uS = self.fan_u(vM, pM, uM, vS)
-        return uS, vS, [("shock", (vK, pK, uK), (vM, pM, uM), math.sqrt(self.m2(vK, pK, vM, pM))),
-                        ("fan", (vM, pM, uM), vM, vS)]
+    def _sonic_shock_end(self, vM, pM, CM2, expand, n=600):
+        """The state S (other than M) on the Hugoniot of M where the Rayleigh line of slope
+        -CM2 (a shock sonic at M) meets it again, or None."""
+        g = self.g
+        far = self._limit_h(expand, vM)
+        grid = np.linspace(vM, far, n)[1:]
+        f = lambda x: self.m2(vM, pM, x, g.p_H(x, vM, pM)) - CM2
+        vals = [f(x) for x in grid]
+        for i in range(1, len(grid)):
+            if (vals[i] > 0) != (vals[0] > 0):
+                return brentq(f, grid[i - 1], grid[i], xtol=1e-15, rtol=1e-15, maxiter=500)
+        return None
+
+    def _fan_then_shock(self, vB, pB, uB, ps, v_inf, expand, pieces):
+        """Fan from B to M (before the inflection), then a shock sonic at M.  Appends the
+        pieces; returns (True, (v, p, u) at ps) if the shock reaches ps with a subsonic state
+        behind, else (False, state after a shock that is sonic on both sides)."""
+        g = self.g
+
+        def end_at_ps(vM):
+            pM = g.p_s(vM, vB, pB)
+            vS = _v_on(lambda x: g.p_H(x, vM, pM), ps, vM, self._limit_h(expand, vM))
+            return self.m2(vM, pM, vS, ps) - g.C(vM, vB, pB) ** 2, vS
+
+        lo, hi = vB + (v_inf - vB) * 1e-9, v_inf - (v_inf - vB) * 1e-9
+        try:
+            flo, fhi = end_at_ps(lo)[0], end_at_ps(hi)[0]
+        except ValueError:
+            flo = fhi = 1.0
+        if (flo > 0) != (fhi > 0):
+            vM = brentq(lambda x: end_at_ps(x)[0], lo, hi, xtol=1e-15, rtol=1e-15, maxiter=500)
+            pM = g.p_s(vM, vB, pB)
+            _, vS = end_at_ps(vM)
+            if self._subsonic_behind(vM, pM, vS, ps) and self.liu_ok(vM, pM, vS):
+                uM = self.fan_u(vB, pB, uB, vM)
+                uS = self.shock_u(vM, pM, uM, vS, ps)
+                pieces.append(("fan", (vB, pB, uB), vB, vM))
+                pieces.append(("shock", (vM, pM, uM), (vS, ps, uS), math.sqrt(self.m2(vM, pM, vS, ps))))
+                return True, (vS, ps, uS)
+
+        # the shock stops where it is sonic behind too: C(S) = C(M) = m
+        def double(vM):
+            pM = g.p_s(vM, vB, pB)
+            CM2 = g.C(vM, vB, pB) ** 2
+            vS = self._sonic_shock_end(vM, pM, CM2, expand)
+            if vS is None:
+                return None
+            pS = g.p_H(vS, vM, pM)
+            return g.C(vS, vS, pS) ** 2 - CM2, vS, pS
+
+        grid = np.linspace(lo, hi, 200)
+        vals = [double(x) for x in grid]
+        idx = [i for i in range(1, len(grid)) if vals[i] is not None and vals[i - 1] is not None
+               and (vals[i][0] > 0) != (vals[i - 1][0] > 0)]
+        if not idx:
+            raise NotImplementedError("no double-sonic shock on this isentrope")
+        i = idx[0]
+        vM = brentq(lambda x: double(x)[0], grid[i - 1], grid[i], xtol=1e-15, rtol=1e-15, maxiter=500)
+        pM = g.p_s(vM, vB, pB)
+        _, vS, pS = double(vM)
+        uM = self.fan_u(vB, pB, uB, vM)
+        uS = self.shock_u(vM, pM, uM, vS, pS)
+        pieces.append(("fan", (vB, pB, uB), vB, vM))
+        pieces.append(("shock", (vM, pM, uM), (vS, pS, uS), math.sqrt(self.m2(vM, pM, vS, pS))))
+        return False, (vS, pS, uS)
 
 
 class Riemann:
