@@ -761,6 +761,8 @@ def main():
         "gpu_launches": args.steps * (3 if args.lattice == "d2q16" else 1),
         "roofline": roofline(w, args.precision, its, kms, pk, args.lattice, st, w.nodes * args.steps),
         "region_nodes_per_stream": st["region_nodes"] / max(1, st["streams"] - st["pair_streams"]),
+        # streams a block runs (its nodes search in lockstep) per node's own streams
+        "block_stream_ratio": st["block_streams"] * 16 / max(1, st["streams"]),
         "hbm": {"bytes_per_update": bytes_per_update(args.precision, args.lattice),
                 "achieved_gbs": value / ws * 1e6 * bytes_per_update(args.precision, args.lattice) / 1e9,
                 "peak_gbs": pk["hbm_gbs"], "peak_src": pk["src"]},
