@@ -870,12 +870,19 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                     }
                 }
                 __syncwarp(gmask);
-                if (lane == 0) sh.nreg[grp] += ncols * nrows;
+                if (lane == 0) sh.nreg[grp] += ncols * nrows - ((it == 1 && lo_x <= 1 && 1 - lo_x < ncols &&
+                                                                   lo_y <= 1 && 1 - lo_y < nrows) ? 1 : 0);
                 R accf[9], accg[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) accf[i] = accg[i] = R(0);
                 const int x_lo = X + lo_x - 1, y_lo = Y + lo_y - 1;
-                const int nreg = ncols * nrows;
+                // In the first stream the arrival gauge is the node's own stored gauge, so
+                // its own region entry is carried by the identity and adds exactly nothing
+                // in the FP32 increment form (about 1e-16 in FP64): it is skipped, which
+                // makes the usual 5 x 5 region 24 entries, three full passes of 8 lanes.
+                const int own_r = (1 - lo_y) * ncols + (1 - lo_x);
+                const bool skip_own = it == 1 && lo_x <= 1 && 1 - lo_x < ncols && lo_y <= 1 && 1 - lo_y < nrows;
+                const int nreg = ncols * nrows - (skip_own ? 1 : 0);
                 const float inc = 1.0f / (float)ncols;
                 // the whole region inside the staged tile (always for |v| dt < 1): slots by
                 // direct indexing from its corner, else per node with a global fallback
@@ -884,7 +891,8 @@ __device__ __forceinline__ void step_tile(const DevParams &p, const R *__restric
                 const R *corner = staged_region ? tile + (cv0 * PT + cu0) * TS : tile;
                 // region nodes round-robin over the group's lanes
 #pragma unroll 1
-                for (int r = lane; r < nreg; r += LPN) {
+                for (int rr = lane; rr < nreg; rr += LPN) {
+                    const int r = rr + (skip_own && rr >= own_r ? 1 : 0);
                     const int cy = (int)(((float)r + 0.5f) * inc), cx = r - cy * ncols;
                     R v[24];
                     if (staged_region) {
