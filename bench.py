@@ -238,8 +238,9 @@ def flops_q16(its: float) -> float:
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the bench workload; they hold only for the kernel source they were
 # taken on (sha256 over the two kernel headers), any other source reports null.
-NCU_TRAFFIC = {"kernel_sha256": "cb7987a0ec19027b9e390cdfa7ec7f0feb5e0b4531192ae8db270ec166f19f8b",
-               "bytes": {"dropletshock2048x1024/mixed": 636991232.0}}
+NCU_TRAFFIC = {"kernel_sha256": "804944b3cf14dfdb4985ac6b9233784f0279b3f7c34f8b526fea166cf068bb7f",
+               "bytes": {"dropletshock2048x1024/mixed": 637875968.0,
+                         "dropletshock2048x1024/fp64": 1170719488.0}}
 
 
 def kernel_sha256() -> str:
