@@ -56,6 +56,25 @@ def test_sub_spinodal_interface_at_0_8_on_maxwell(experiments, precision):
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_advected_slab_on_maxwell(experiments, precision):
+    """The advected case of Fig. 2 (0.9 T_cr, the slab moving at U = 5 U_ch): the vapour
+    density's error falls as the inverse box size at a fixed time (measured at t = 1900:
+    -8.5 / -4.4 / -2.3 / -1.3 / -0.6 % on 128 / 256 / 512 / 1024 / 2048 nodes); on 2048
+    nodes both densities are within 1 % of Maxwell's, and halving the box doubles the
+    vapour error."""
+    rv, rl = thermo.maxwell(0.9)
+    err = {}
+    for nx in (1024, 2048):
+        probe = inputs.coexistence_slab(0.9, advected=True, nx=nx)
+        w = inputs.coexistence_slab(0.9, advected=True, nx=nx, steps=int(math.ceil(1900.0 / probe.dt)))
+        res = experiments.coexistence(w, precision)
+        assert res["nonfinite"] == 0
+        err[nx] = (res["rho_v"] / rv - 1.0, res["rho_l"] / rl - 1.0)
+    assert abs(err[2048][0]) < 0.01 and abs(err[2048][1]) < 0.01, err
+    assert 1.6 < err[1024][0] / err[2048][0] < 2.5, err
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("Tr", [0.7, 0.8, 0.9])
 def test_isothermal_dieterici_on_maxwell(experiments, Tr, precision):
     w = inputs.dieterici_slab(Tr, nx=256, steps=3000)
