@@ -18,11 +18,14 @@ Waves of family 1 (left, sign s = -1) and 3 (right, s = +1) from a state K:
                     m = sqrt(-(p - p_K)/(v - v_K)), speed u_K + s m v_K.
 Admissibility (Liu): a shock from the state ahead K to S is admitted when
 m^2(K, M) <= m^2(K, S) for every M on the Hugoniot between them (no intermediate shock is
-faster; at M -> K this is the Lax bound C_K <= m); a fan when the characteristic speed increases across it
-(expansion needs Gamma > 0 along it, compression Gamma < 0).  Where neither holds over the
-whole path the wave is composite: a fan ended by a shock that is sonic at the fan's end
-(m = C there), or a shock that is sonic behind (its Rayleigh line tangent to the isentrope
-of its end state) followed by a fan.  Paths that would need more pieces are refused.
+faster; at M -> K this is the Lax bound C_K <= m); a fan when the characteristic speed
+increases across it (expansion needs Gamma > 0 along it, compression Gamma < 0).  Where
+neither holds over the whole path the wave is composite and is built by marching pieces
+from K: a fan ended by a shock that is sonic at the fan's end (m = C there), which either
+reaches the target with a subsonic state behind it or is sonic behind as well and is
+followed by another fan; or a shock that is sonic behind (its Rayleigh line tangent to the
+isentrope of its end state) followed by a fan.  Waves that would need more than eight
+pieces are refused.
 """
 from __future__ import annotations
 
