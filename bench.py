@@ -257,11 +257,7 @@ def ncu_traffic(w, precision):
     return NCU_TRAFFIC["bytes"].get("%s/%s" % (w.name, precision))
 
 
-def flops_per_stream() -> int:
-    return 9 * (FLOPS_DIR + 16 * FLOPS_PAIR) + FLOPS_STREAM_EXTRA
-
-
-def oracle_mlups(w, steps: int, lattice: str = "d2q9") -> dict:
+def oracle_mlups(w, steps: int, lattice: str = "d2q9", warmup: int = 1) -> dict:
     import oracle
     P = oracle.Params(nx=w.nx, ny=w.ny, bc_x=w.bc_x, bc_y=w.bc_y, a=w.a, b=w.b, R=w.R,
                       delta=w.delta, kappa=w.kappa, tau=w.tau, dt=w.dt, k_cond=w.k_cond,
@@ -269,7 +265,7 @@ def oracle_mlups(w, steps: int, lattice: str = "d2q9") -> dict:
                       eos_params=tuple(w.eos_params),
                       T_iso=float(w.T.flat[0]) if w.isothermal else 0.0, lattice=lattice)
     st = oracle.init_state(P, *w.fields())
-    st = oracle.step(P, st, 1)          # warm-up (page-in, thread pool)
+    st = oracle.step(P, st, max(1, warmup))   # warm-up (page-in, thread pool)
     t0 = time.perf_counter()
     st = oracle.step(P, st, steps)
     dt = time.perf_counter() - t0
@@ -649,9 +645,9 @@ def main():
         if rank == 0:
             # full-grid oracle steps, bounded: a 2048 x 1024 step takes ~10 s on 16 cores
             steps = max(1, min(args.steps, 20 if w.nodes < 100000 else 3))
-            res = oracle_mlups(w, steps, args.lattice)
+            res = oracle_mlups(w, steps, args.lattice, warmup=args.warmup)
             line = {"impl": "reference", "metric": "MLUPS", "value": res["value"], "unit": "MLUPS",
-                    "n_gpus": ws, "steps": steps, "warmup": 1, "higher_is_better": True,
+                    "n_gpus": ws, "steps": steps, "warmup": args.warmup, "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                     "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "dt": w.dt, "precision": "fp64",
                                "launch_shape": "n/a (CPU oracle)", "lattice": args.lattice,
