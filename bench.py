@@ -164,18 +164,34 @@ def flops_d2q9(st: dict, updates: int) -> float:
              + pair_streams * 9 * 16 * FLOPS_PAIR + updates * (FLOPS_NONLOCAL + FLOPS_COLLIDE))
     return total / max(1, updates)
 
-# The same count for the D2Q16 step (k_q16_step), per node update: per stencil pair (16
-# directions x 16 stencil nodes per stream): gauge offsets (9), the eight transfer-map
+# The same count for the D2Q16 step (k_q16_step), per node update.  Region stream, per
+# region node (the union of the sixteen 4 x 4 departure stencils, 5 x 5 for |v| dt < 1):
+# gauge offsets (9), both per-axis increment maps (eight rows of 31 and their offsets 16:
+# 264), for f and g the x-increments (128), the y-increments (144) and the weighted
+# accumulation (80), the weight products (16) => 990; per region stream: departure floors,
+# cubic weights and tables of both axes (220).  Per-pair fallback stream (regions wider
+# than 6): per stencil pair (16 directions x 16 stencil nodes) gauge offsets (9), the eight
 # increments of the pair's row per axis (16 for their offsets, 82 for the entries), the
 # x-increments of the four source rows for f and g (64), the y-increment (24), weight and
-# accumulation (11) => 206; per direction: departure points and cubic weights (40); per
+# accumulation (11) => 206, per direction departure points and cubic weights (40).  Per
 # stream: moments and residual (FP64, 130); per node update: non-local terms (200) and the
 # collision (2300: four per-axis increment maps ~700, three tensor-product applications
 # ~900, forced g equilibrium ~640, mass and energy defect sums ~70).
+FLOPS_Q16_REGION_NODE = 990
+FLOPS_Q16_REGION_STREAM = 220
 FLOPS_Q16_PAIR = 206
 FLOPS_Q16_DIR = 40
 FLOPS_Q16_STREAM_EXTRA = 130
 FLOPS_Q16_COLLIDE = 2300
+
+
+def flops_q16(st: dict, updates: int) -> float:
+    """FLOPs per node update of the D2Q16 step from its counters (pond_stats)."""
+    pair = st.get("pair_streams", 0)
+    total = (st["region_nodes"] * FLOPS_Q16_REGION_NODE + (st["streams"] - pair) * FLOPS_Q16_REGION_STREAM
+             + st["streams"] * FLOPS_Q16_STREAM_EXTRA + pair * 16 * (FLOPS_Q16_DIR + 16 * FLOPS_Q16_PAIR)
+             + updates * (FLOPS_NONLOCAL + FLOPS_Q16_COLLIDE))
+    return total / max(1, updates)
 
 
 # The D3Q27 step (k_q27_step), per node update: per stencil pair (27 directions x 64
@@ -229,10 +245,6 @@ def d3q27_run(pond, torch, stream, precision, steps, warmup, nx=96, ny=96, nz=64
             "roofline": {"bound": "alu", "kernel": "k_q27_step (+ two non-local kernels, timed together)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "flops_per_update": flops_q27(its)}}
-
-
-def flops_q16(its: float) -> float:
-    return its * (16 * (FLOPS_Q16_DIR + 16 * FLOPS_Q16_PAIR) + FLOPS_Q16_STREAM_EXTRA) + FLOPS_NONLOCAL + FLOPS_Q16_COLLIDE
 
 
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from
@@ -317,7 +329,7 @@ def run_form(w, pond, torch, stream, flush, precision, steps, warmup, shape, ws)
 
 def roofline(w, precision, its, kernel_ms, pk, lattice="d2q9", st=None, updates=0):
     if lattice == "d2q16":
-        fl = flops_q16(its)
+        fl = flops_q16(st, updates)
         kernel, traffic = "k_q16_step (+ two non-local kernels, timed together)", None
     else:
         fl = flops_d2q9(st, updates)
@@ -505,13 +517,14 @@ def other_configs(pond, torch, stream, sm_mhz: float = 2070.0, skip: str = "") -
         st = sim.stats()
         sim.close()
         its = st["streams"] / max(1, st["node_updates"])
-        achieved = w.nodes * flops_q16(its) / (ms * 1e-3) / 1e12
+        fl = flops_q16(st, st["node_updates"])
+        achieved = w.nodes * fl / (ms * 1e-3) / 1e12
         peak = alu_peak_tflops(prec, sm_mhz)
         out["%s/d2q16/%s" % (w.name, prec)] = {
             "mlups": w.nodes / ms / 1e3, "ms_per_step": ms, "streams_per_node": its,
             "roofline": {"bound": "alu", "kernel": "k_q16_step (+ two non-local kernels)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "flops_per_update": flops_q16(its)}}
+                         "flops_per_update": fl}}
     # the D3Q27 lattice on a 96 x 96 x 64 liquid sphere
     for prec, steps in (("mixed", 5), ("fp64", 2)):
         out["droplet3d96x96x64/d3q27/%s" % prec] = d3q27_run(pond, torch, stream, prec, steps, 2, sm_mhz=sm_mhz)

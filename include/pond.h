@@ -166,11 +166,14 @@ typedef struct {
     int64_t max_streams;   /* largest streaming-pass count of any block        */
     int64_t timeouts;      /* tiles skipped because a bounded wait for their
                               staging copies ran out (reported as POND_ETIMEOUT) */
-    int64_t region_nodes;  /* D2Q9: stencil-region nodes carried into the arrival
-                              gauge, summed over streams (the union of a node's
-                              nine 4x4 stencils: 16..64 per stream)              */
-    int64_t pair_streams;  /* D2Q9: streams of regions wider than 8 nodes, which
-                              take the per-direction, per-stencil-node path      */
+    int64_t region_nodes;  /* stencil-region nodes carried into the arrival gauge,
+                              summed over streams (the union of a node's 4x4
+                              departure stencils: 16..64 per stream on D2Q9,
+                              16..36 on D2Q16, less the node's own entry in a
+                              first stream)                                    */
+    int64_t pair_streams;  /* streams of regions wider than 8 nodes (D2Q9) or 6
+                              nodes (D2Q16), which take the per-direction,
+                              per-stencil-node path                            */
 } pond_stats_t;
 
 /* Create a context and allocate its device state (two state buffers holding one record

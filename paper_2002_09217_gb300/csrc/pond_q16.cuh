@@ -482,6 +482,185 @@ __device__ __forceinline__ void apply_inc(const A Dx[4][4], const A Dy[4][4], co
 }
 
 // ---------------------------------------------------------------------------
+// Region stream.  On a tensor lattice the union of a node's sixteen 4 x 4 departure
+// stencils is the product of the per-axis unions: W x H nodes with W (H) = 4 + the spread
+// of the four departure floors along the axis, 5 x 5 while |v| dt < 1 in every direction.
+// Each region node is carried into the arrival gauge once for all sixteen directions
+// (G f = f + [(I + Dy) (x) (I + Dx) - I] f), and direction i takes its Lagrange-weighted
+// share of component i.  The arithmetic per (direction, stencil node) pair is that of
+// q16_stream, so the two agree up to the rounding of zero-weight terms; the region form
+// transforms about 25 nodes per stream against 256 pairs.
+
+// Largest region side the region stream takes; wider regions take q16_stream.
+constexpr int Q16_REGION_MAX = 6;
+constexpr int Q16_THREADS = 128;   // threads of a k_q16_step block
+
+// Lagrange weight tables of the region stream, one column of entries per thread (entry e
+// of thread t at w[e][t]: consecutive threads in consecutive banks).  Entry
+// (axis * 4 + k) * Q16_REGION_MAX + c is the weight of region column (row) c in the
+// stencil of axis component k, zero outside that stencil.
+template <typename R>
+struct Q16Weights {
+    R w[2 * 4 * Q16_REGION_MAX][Q16_THREADS];
+};
+
+// Departure floors and Lagrange weights of the four axis components for the gauge
+// velocity u along one axis (as in `departure`), the table entries of that axis, and the
+// region's first coordinate lo (= X + min floor - 1) and side. False, with nothing
+// written, when the side exceeds Q16_REGION_MAX or a floor is not finite or not within
+// 2^20 (the floors are checked as reals before any conversion to int).
+template <typename R>
+__device__ __forceinline__ bool q16_region_axis(const Lat16<R> &L, int X, R s, R u, R dt, R *wt, int &lo,
+                                                int &side)
+{
+    R fl[4], a[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const R d = -(s * L.c[k] + u) * dt;
+        fl[k] = floor(d);
+        cubic_weights<R>(d - fl[k] + R(1), a[k]);
+    }
+    const R flo = fmin(fmin(fl[0], fl[1]), fmin(fl[2], fl[3]));
+    const R fhi = fmax(fmax(fl[0], fl[1]), fmax(fl[2], fl[3]));
+    if (!(fhi - flo <= R(Q16_REGION_MAX - 4)) || !(fabs(flo) <= R(1 << 20)) || !(fabs(fhi) <= R(1 << 20)))
+        return false;
+    lo = X + (int)flo - 1;
+    side = (int)(fhi - flo) + 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = (int)(fl[k] - flo);   // 0 .. side - 4
+#pragma unroll
+        for (int c = 0; c < Q16_REGION_MAX; ++c) {
+            const int j = c - o;
+            wt[(k * Q16_REGION_MAX + c) * Q16_THREADS] =
+                j == 0 ? a[k][0] : (j == 1 ? a[k][1] : (j == 2 ? a[k][2] : (j == 3 ? a[k][3] : R(0))));
+        }
+    }
+    return true;
+}
+
+// One population set (16 values at v) of a region node: x-increments t = (I (x) Dx) h, the
+// y-increment of each component, and acc_i += wx_ix wy_iy ((h_i - ref_i) + t_i + dy_i).
+template <typename R>
+__device__ __forceinline__ void q16_region_pop(const R (&Dx)[4][4], const R (&Dy)[4][4], const R *v,
+                                               const R (&ref)[Q16], const R (&wx)[4], const R (&wy)[4],
+                                               R (&acc)[Q16])
+{
+    R h[Q16], t[Q16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        R q[4];
+        ld4(v + 4 * r, q);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[4 * r + k] = q[k];
+    }
+#pragma unroll
+    for (int jy = 0; jy < 4; ++jy)
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix) {
+            R a = R(0);
+#pragma unroll
+            for (int jx = 0; jx < 4; ++jx) a += Dx[ix][jx] * h[4 * jy + jx];
+            t[4 * jy + ix] = a;
+        }
+#pragma unroll
+    for (int iy = 0; iy < 4; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < 4; ++ix) {
+            R dy = R(0);
+#pragma unroll
+            for (int jy = 0; jy < 4; ++jy) dy += Dy[iy][jy] * (h[4 * jy + ix] + t[4 * jy + ix]);
+            const int i = 4 * iy + ix;
+            acc[i] += (wx[ix] * wy[iy]) * (((h[i] - ref[i]) + t[i]) + dy);
+        }
+}
+
+// The region pass over the W x H region at (xlo, ylo) for the population sets selected
+// (DO_F: f, DO_G: g), skipping region entry `skip` (-1: none); writes the increments of
+// the streamed populations over the node's own (irec) into fi / gi.
+template <typename R, bool DO_F, bool DO_G>
+__device__ __forceinline__ void q16_region_pass(const DevParams &p, const Lat16<R> &L, const R *__restrict__ in,
+                                                const R *irec, int xlo, int ylo, int W, int H, int skip,
+                                                R th, R ux, R uy, const R *wt, R *fi, R *gi)
+{
+    const R s = sqrt_(th), is = R(1) / s;
+    R reff[Q16], refg[Q16], accf[Q16], accg[Q16];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        R q[4];
+        if (DO_F) {
+            ld4(irec + Q_F + 4 * r, q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) reff[4 * r + k] = q[k];
+        }
+        if (DO_G) {
+            ld4(irec + Q_G + 4 * r, q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) refg[4 * r + k] = q[k];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q16; ++i) { accf[i] = R(0); accg[i] = R(0); }
+#pragma unroll 1
+    for (int cy = 0; cy < H; ++cy) {
+        const long long row = (long long)bc_wrap(ylo + cy, p.ny, p.bcy) * p.nx;
+        R wy[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wy[k] = wt[((4 + k) * Q16_REGION_MAX + cy) * Q16_THREADS];
+#pragma unroll 1
+        for (int cx = 0; cx < W; ++cx) {
+            if (cy * W + cx == skip) continue;
+            const R *rec = in + (size_t)(row + bc_wrap(xlo + cx, p.nx, p.bcx)) * SLQ;
+            R wx[4], gv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) wx[k] = wt[(k * Q16_REGION_MAX + cx) * Q16_THREADS];
+            ld4(rec + Q_TH, gv);   // theta, u_x, u_y, rho of the region node
+            const R ds = (gv[0] - th) / (sqrt_(gv[0]) + s) * is;   // (s' - s)/s
+            R Dx[4][4], Dy[4][4];
+            axis_inc<R>(L, ds, (gv[1] - ux) * is, Dx);
+            axis_inc<R>(L, ds, (gv[2] - uy) * is, Dy);
+            if (DO_F) q16_region_pop<R>(Dx, Dy, rec + Q_F, reff, wx, wy, accf);
+            if (DO_G) q16_region_pop<R>(Dx, Dy, rec + Q_G, refg, wx, wy, accg);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q16; ++i) {
+        if (DO_F) fi[i] = accf[i];
+        if (DO_G) gi[i] = accg[i];
+    }
+}
+
+// Streaming of node (X, Y) into gauge (th, ux, uy) by the region stream where the region
+// fits, else by q16_stream; skip_own leaves out the node's own region entry (valid when
+// the gauge is the node's stored gauge: the map is then the identity and the entry adds
+// exactly zero).  Adds the region entries transformed to nreg, or 1 to npair.
+template <typename R>
+__device__ __forceinline__ void q16_stream_any(const DevParams &p, const Lat16<R> &L, const R *__restrict__ in,
+                                               int X, int Y, R th, R ux, R uy, bool skip_own, R *wt, R *fi,
+                                               R *gi, unsigned long long &nreg, unsigned long long &npair)
+{
+    const R s = sqrt_(th), dt = (R)p.dt;
+    int xlo, ylo, W, H;
+    if (q16_region_axis<R>(L, X, s, ux, dt, wt, xlo, W) &&
+        q16_region_axis<R>(L, Y, s, uy, dt, wt + 4 * Q16_REGION_MAX * Q16_THREADS, ylo, H)) {
+        const int cxo = X - xlo, cyo = Y - ylo;
+        const int skip = (skip_own && cxo >= 0 && cxo < W && cyo >= 0 && cyo < H) ? cyo * W + cxo : -1;
+        const R *irec = in + ((size_t)Y * p.nx + X) * SLQ;
+        if (sizeof(R) == 4) {
+            q16_region_pass<R, true, true>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, fi, gi);
+        } else {
+            // FP64: one population set per pass (both at once exceed the register file)
+            q16_region_pass<R, true, false>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, fi, gi);
+            q16_region_pass<R, false, true>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, fi, gi);
+        }
+        nreg += (unsigned long long)(W * H - (skip >= 0 ? 1 : 0));
+    } else {
+        q16_stream<R>(p, L, in, X, Y, th, ux, uy, fi, gi);
+        npair += 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The node step.  in: state at t - dt; nl: non-local terms (F, rho E_lambda, M_0) of the
 // state they are taken from; out: state at t.  Frame search: predictor = the node's
 // stored gauge; corrector = re-stream with (theta*, u) of the streamed moments until the
@@ -489,14 +668,16 @@ __device__ __forceinline__ void apply_inc(const A Dx[4][4], const A Dy[4][4], co
 // the co-moving frame lambda* = (theta*, u) and carried into the streaming gauge (Eqs.
 // f collision with S_i, g collision with gtilde and phi, new geq).
 template <typename R>
-__global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restrict__ in,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_q16_step(DevParams p, const R *__restrict__ in,
                                                   const double *__restrict__ nl, R *__restrict__ out,
                                                   DevStats *stats)
 {
     const int X = blockIdx.x * blockDim.x + threadIdx.x, Y = blockIdx.y * blockDim.y + threadIdx.y;
     const bool valid = X < p.nx && Y < p.ny;
     const long long N = p.N, n = valid ? (long long)Y * p.nx + X : 0;
-    unsigned long long its = 0, nonconv = 0, clamped = 0, nonfinite = 0;
+    unsigned long long its = 0, nonconv = 0, clamped = 0, nonfinite = 0, nreg = 0, npair = 0;
+    __shared__ Q16Weights<R> qw;
+    R *wt = &qw.w[0][threadIdx.y * blockDim.x + threadIdx.x];
     if (valid) {
         const Lat16<R> L = make_lat16<R>();
         const Lat16<double> Ld = make_lat16<double>();
@@ -512,7 +693,8 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         bool conv = false;
         for (;;) {
             ++it;
-            q16_stream<R>(p, L, in, X, Y, th, ux, uy, ft, gt);
+            // the first stream uses the node's stored gauge: its own region entry adds zero
+            q16_stream_any<R>(p, L, in, X, Y, th, ux, uy, it == 1, wt, ft, gt, nreg, npair);
             q16_macro<R>(p, Ld, th, ux, uy, own, ft, gt, Fx, Fy, rEl, mac);
             const double t0 = (double)th, st0 = sqrt(t0);
             const double r0 = fabs(mac[10] - t0) / t0;
@@ -660,10 +842,10 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
     }
     // counters: warp sums (every thread of the block reaches here; the warp's lanes are
     // its linear thread indices, whatever the block's x extent), one atomic per warp
-    unsigned long long v[4] = {its, nonconv, clamped, nonfinite}, mx = its;
+    unsigned long long v[6] = {its, nonconv, clamped, nonfinite, nreg, npair}, mx = its;
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
         const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = m2 > mx ? m2 : mx;
     }
@@ -672,6 +854,8 @@ __global__ void __launch_bounds__(128) k_q16_step(DevParams p, const R *__restri
         if (v[1]) atomicAdd(&stats->nonconv, v[1]);
         if (v[2]) atomicAdd(&stats->clamped, v[2]);
         if (v[3]) atomicAdd(&stats->nonfinite, v[3]);
+        if (v[4]) atomicAdd(&stats->region_nodes, v[4]);
+        if (v[5]) atomicAdd(&stats->pair_streams, v[5]);
         if (mx) atomicMax(&stats->max_streams, mx);
     }
 }

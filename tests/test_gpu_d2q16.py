@@ -52,6 +52,16 @@ def small_cases():
     yield "dieterici_iso_48x3", inputs.dieterici_slab(0.8, nx=48, ny=3, steps=40)
     yield "anomalous_tube_64x2", dataclasses.replace(inputs.nonclassical_tube("fig4", nx=64, ny=2), steps=40)
     yield "double_well_slab_48x3", inputs.simplified_eos("slab", nx=48, ny=3, steps=40)
+    yield "hot_bump24x20_wide_regions", wide_region_droplet()
+
+
+def wide_region_droplet():
+    """The 24 x 20 droplet's density field at 1.7 T_cr (a supercritical density bump) with
+    dt = 1: sqrt(theta) dt up to 0.47, so that the departure floors of about two thirds of
+    the nodes spread over three nodes (regions wider than 6), which take the per-pair
+    stream, and the rest the region stream."""
+    w = inputs.droplet(n=24, ny=20, Tr=0.9, radius=5.0, steps=8)
+    return dataclasses.replace(w, name="hot_bump24x20_dt1", dt=1.0, T=w.T * (1.7 / 0.9))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -66,6 +76,19 @@ def test_small_grids_match_oracle(pond, case, precision):
     assert gstats["nonfinite"] == 0
     if precision == "fp64":
         assert abs(gstats["streams"] - ostats["streams"]) <= 0.01 * ostats["streams"] + 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_region_and_pair_streams_are_both_taken(pond, precision):
+    """Every stream of a usual workload (|v| dt < 1) takes the region stream over at most
+    6 x 6 nodes; the wide-region droplet sends streams down both paths."""
+    w = inputs.droplet(n=24, ny=20, Tr=0.9, radius=5.0, steps=5)
+    _, st = gpu_run(pond, w, precision)
+    assert st["pair_streams"] == 0
+    assert 15 * st["streams"] <= st["region_nodes"] <= 36 * st["streams"], st
+    _, st = gpu_run(pond, wide_region_droplet(), precision)
+    assert 0 < st["pair_streams"] < st["streams"], st
+    assert st["region_nodes"] > 0
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

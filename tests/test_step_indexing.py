@@ -1,4 +1,4 @@
-"""Index safety of the step kernel's region stream, checked on the CPU.
+"""Index safety of the step kernels' region streams (D2Q9 and D2Q16), checked on the CPU.
 
 The kernel computes, per node and axis, the departure offsets d_j = -(s c_j + u) dt of the
 three directions (clamped to +-2^20 nodes, NaN to the lower bound), their floors, the
@@ -65,3 +65,82 @@ def test_region_indices_stay_in_the_tables():
         s = float(np.exp(rng.uniform(-10, 5)))
         u = float(rng.normal(0.0, 3.0))
         check_axis(s, u, float(rng.uniform(0.01, 1.0)))
+
+
+# D2Q16 step (region stream of k_q16_step): per axis the four departure offsets
+# d_k = -(s c_k + u) dt with c_k = -+sqrt(3 -+ sqrt 6), their floors as reals, and the region
+# taken only when max - min <= Q16_REGION_MAX - 4 and both floors lie within 2^20 (NaN fails
+# every comparison); only then are the floors converted to int.
+Q16_REGION_MAX = 6
+Q16_THREADS = 128
+C16 = [np.float32(c) for c in (-np.sqrt(3 + np.sqrt(6)), -np.sqrt(3 - np.sqrt(6)),
+                               np.sqrt(3 - np.sqrt(6)), np.sqrt(3 + np.sqrt(6)))]
+
+
+def cuda_fmin(a, b):
+    """fmin / fmax of CUDA return the other operand when one is NaN."""
+    if np.isnan(a):
+        return b
+    if np.isnan(b):
+        return a
+    return min(a, b)
+
+
+def cuda_fmax(a, b):
+    if np.isnan(a):
+        return b
+    if np.isnan(b):
+        return a
+    return max(a, b)
+
+
+def to_int(x):
+    """float -> int conversion as cvt.rzi.s32: truncation, saturation, NaN to 0."""
+    if np.isnan(x):
+        return 0
+    return int(max(min(np.trunc(x), I32.max), I32.min))
+
+
+def check_axis_q16(s, u, dt, X=7):
+    with np.errstate(all="ignore"):
+        fl = [np.floor(-(np.float32(s) * c + np.float32(u)) * np.float32(dt)) for c in C16]
+        flo = cuda_fmin(cuda_fmin(fl[0], fl[1]), cuda_fmin(fl[2], fl[3]))
+        fhi = cuda_fmax(cuda_fmax(fl[0], fl[1]), cuda_fmax(fl[2], fl[3]))
+        taken = bool(fhi - flo <= np.float32(Q16_REGION_MAX - 4)) and bool(abs(flo) <= 2.0 ** 20) \
+            and bool(abs(fhi) <= 2.0 ** 20)
+    if not taken:
+        return False
+    lo = X + to_int(flo) - 1
+    side = to_int(fhi - flo) + 4
+    assert 4 <= side <= Q16_REGION_MAX
+    assert I32.min < lo - 1 and lo + side < I32.max
+    with np.errstate(all="ignore"):
+        for f in fl:   # a NaN floor (not reachable from a real gauge) converts to 0
+            o = to_int(f - flo)
+            assert 0 <= o <= side - 4
+    for axis in range(2):
+        for k in range(4):
+            for c in range(Q16_REGION_MAX):
+                e = (axis * 4 + k) * Q16_REGION_MAX + c
+                assert 0 <= e < 2 * 4 * Q16_REGION_MAX
+                assert e * Q16_THREADS + Q16_THREADS - 1 < 2 * 4 * Q16_REGION_MAX * Q16_THREADS
+    # the node's own entry, when skipped, is an index of the region
+    cxo = X - lo
+    if 0 <= cxo < side:
+        assert 0 <= cxo * side + cxo < side * side
+    return True
+
+
+def test_d2q16_region_indices_stay_in_the_tables():
+    rng = np.random.default_rng(12)
+    specials = [0.0, 1e-30, 1e-7, 0.05, 0.5, 1.0, 3.0, 1e3, 1e10, 1e38, np.inf, -np.inf, np.nan]
+    taken = 0
+    for s in [abs(x) if not np.isnan(x) else x for x in specials]:
+        for u in specials + [-x for x in specials[1:-1]]:
+            for dt in (0.146, 0.5, 1.0):
+                taken += check_axis_q16(s, u, dt)
+    for _ in range(3000):
+        s = float(np.exp(rng.uniform(-10, 2)))
+        u = float(rng.normal(0.0, 1.0))
+        taken += check_axis_q16(s, u, float(rng.uniform(0.01, 1.0)))
+    assert taken > 1000
