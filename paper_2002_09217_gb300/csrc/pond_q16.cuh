@@ -432,15 +432,16 @@ __device__ __forceinline__ void q16_macro(const DevParams &p, const Lat16<double
     const double jx = s * (own[1] + dx) + (double)ux * rho + own[4];
     const double jy = s * (own[2] + dy) + (double)uy * rho + own[5];
     const double sg = own[3] + dg;
-    const double u_x = jx / rho, u_y = jy / rho;
-    const double uhx = u_x + Fx * p.dt / (2.0 * rho), uhy = u_y + Fy * p.dt / (2.0 * rho);
-    const double E = sg / (2.0 * rho);
-    const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEl / rho;
+    const double irho = 1.0 / rho;   // one FP64 division, the quotients by rho multiply
+    const double u_x = jx * irho, u_y = jy * irho;
+    const double uhx = u_x + (0.5 * p.dt) * Fx * irho, uhy = u_y + (0.5 * p.dt) * Fy * irho;
+    const double E = 0.5 * sg * irho;
+    const double e = E - 0.5 * (uhx * uhx + uhy * uhy) - rEl * irho;
     const double T = p.isothermal ? p.T_iso : (e + p.a * rho) / p.cv;
     const double pr = q16_p(p, rho, T);
     const double P = pr > p.p_floor ? pr : p.p_floor;
     out[0] = rho; out[1] = u_x; out[2] = u_y; out[3] = uhx; out[4] = uhy;
-    out[5] = E; out[6] = e; out[7] = T; out[8] = pr; out[9] = P; out[10] = P / rho;
+    out[5] = E; out[6] = e; out[7] = T; out[8] = pr; out[9] = P; out[10] = P * irho;
 }
 
 // Per-axis transfer map from gauge (s_src, u_src) into (s_dst, u_dst) in increment
@@ -494,6 +495,12 @@ __device__ __forceinline__ void apply_inc(const A Dx[4][4], const A Dy[4][4], co
 // Largest region side the region stream takes; wider regions take q16_stream.
 constexpr int Q16_REGION_MAX = 6;
 constexpr int Q16_THREADS = 128;   // threads of a k_q16_step block
+// FP32: f and g of a region node in one pass (two rolled passes, one population set each,
+// measured 4 % slower on the 2048 x 1024 droplet-shock); FP64 always takes two passes
+// (one pass exceeds the register file).  Three FP32 blocks per SM (168 registers): two
+// (232 registers) and four (128, with spills) measured slower.
+constexpr bool Q16_ONE_PASS = true;
+constexpr int Q16_MIN_BLOCKS = 3;
 
 // Lagrange weight tables of the region stream, one column of entries per thread (entry e
 // of thread t at w[e][t]: consecutive threads in consecutive banks).  Entry
@@ -575,32 +582,31 @@ __device__ __forceinline__ void q16_region_pop(const R (&Dx)[4][4], const R (&Dy
         }
 }
 
-// The region pass over the W x H region at (xlo, ylo) for the population sets selected
-// (DO_F: f, DO_G: g), skipping region entry `skip` (-1: none); writes the increments of
-// the streamed populations over the node's own (irec) into fi / gi.
-template <typename R, bool DO_F, bool DO_G>
+// The region pass over the W x H region at (xlo, ylo), skipping region entry `skip` (-1:
+// none): the increments of the streamed populations over the node's own (irec) for the
+// population set at record offset `off` (Q_F or Q_G) into out0, and with BOTH (off = Q_F)
+// those of g into out1 as well.
+template <typename R, bool BOTH>
 __device__ __forceinline__ void q16_region_pass(const DevParams &p, const Lat16<R> &L, const R *__restrict__ in,
                                                 const R *irec, int xlo, int ylo, int W, int H, int skip,
-                                                R th, R ux, R uy, const R *wt, R *fi, R *gi)
+                                                R th, R ux, R uy, const R *wt, int off, R *out0, R *out1)
 {
     const R s = sqrt_(th), is = R(1) / s;
-    R reff[Q16], refg[Q16], accf[Q16], accg[Q16];
+    R ref0[Q16], ref1[Q16], acc0[Q16], acc1[Q16];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         R q[4];
-        if (DO_F) {
-            ld4(irec + Q_F + 4 * r, q);
+        ld4(irec + off + 4 * r, q);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) reff[4 * r + k] = q[k];
-        }
-        if (DO_G) {
+        for (int k = 0; k < 4; ++k) ref0[4 * r + k] = q[k];
+        if (BOTH) {
             ld4(irec + Q_G + 4 * r, q);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) refg[4 * r + k] = q[k];
+            for (int k = 0; k < 4; ++k) ref1[4 * r + k] = q[k];
         }
     }
 #pragma unroll
-    for (int i = 0; i < Q16; ++i) { accf[i] = R(0); accg[i] = R(0); }
+    for (int i = 0; i < Q16; ++i) { acc0[i] = R(0); acc1[i] = R(0); }
 #pragma unroll 1
     for (int cy = 0; cy < H; ++cy) {
         const long long row = (long long)bc_wrap(ylo + cy, p.ny, p.bcy) * p.nx;
@@ -619,14 +625,14 @@ __device__ __forceinline__ void q16_region_pass(const DevParams &p, const Lat16<
             R Dx[4][4], Dy[4][4];
             axis_inc<R>(L, ds, (gv[1] - ux) * is, Dx);
             axis_inc<R>(L, ds, (gv[2] - uy) * is, Dy);
-            if (DO_F) q16_region_pop<R>(Dx, Dy, rec + Q_F, reff, wx, wy, accf);
-            if (DO_G) q16_region_pop<R>(Dx, Dy, rec + Q_G, refg, wx, wy, accg);
+            q16_region_pop<R>(Dx, Dy, rec + off, ref0, wx, wy, acc0);
+            if (BOTH) q16_region_pop<R>(Dx, Dy, rec + Q_G, ref1, wx, wy, acc1);
         }
     }
 #pragma unroll
     for (int i = 0; i < Q16; ++i) {
-        if (DO_F) fi[i] = accf[i];
-        if (DO_G) gi[i] = accg[i];
+        out0[i] = acc0[i];
+        if (BOTH) out1[i] = acc1[i];
     }
 }
 
@@ -646,12 +652,14 @@ __device__ __forceinline__ void q16_stream_any(const DevParams &p, const Lat16<R
         const int cxo = X - xlo, cyo = Y - ylo;
         const int skip = (skip_own && cxo >= 0 && cxo < W && cyo >= 0 && cyo < H) ? cyo * W + cxo : -1;
         const R *irec = in + ((size_t)Y * p.nx + X) * SLQ;
-        if (sizeof(R) == 4) {
-            q16_region_pass<R, true, true>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, fi, gi);
+        if (Q16_ONE_PASS && sizeof(R) == 4) {
+            q16_region_pass<R, true>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, Q_F, fi, gi);
         } else {
-            // FP64: one population set per pass (both at once exceed the register file)
-            q16_region_pass<R, true, false>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, fi, gi);
-            q16_region_pass<R, false, true>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt, fi, gi);
+            // one population set per pass, the pass's code once (a rolled loop)
+#pragma unroll 1
+            for (int ps = 0; ps < 2; ++ps)
+                q16_region_pass<R, false>(p, L, in, irec, xlo, ylo, W, H, skip, th, ux, uy, wt,
+                                          ps == 0 ? Q_F : Q_G, ps == 0 ? fi : gi, nullptr);
         }
         nreg += (unsigned long long)(W * H - (skip >= 0 ? 1 : 0));
     } else {
@@ -668,7 +676,7 @@ __device__ __forceinline__ void q16_stream_any(const DevParams &p, const Lat16<R
 // the co-moving frame lambda* = (theta*, u) and carried into the streaming gauge (Eqs.
 // f collision with S_i, g collision with gtilde and phi, new geq).
 template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_q16_step(DevParams p, const R *__restrict__ in,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? Q16_MIN_BLOCKS : 1) k_q16_step(DevParams p, const R *__restrict__ in,
                                                   const double *__restrict__ nl, R *__restrict__ out,
                                                   DevStats *stats)
 {
@@ -696,9 +704,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_q16_step(DevPar
             // the first stream uses the node's stored gauge: its own region entry adds zero
             q16_stream_any<R>(p, L, in, X, Y, th, ux, uy, it == 1, wt, ft, gt, nreg, npair);
             q16_macro<R>(p, Ld, th, ux, uy, own, ft, gt, Fx, Fy, rEl, mac);
-            const double t0 = (double)th, st0 = sqrt(t0);
-            const double r0 = fabs(mac[10] - t0) / t0;
-            const double r1 = fabs(mac[1] - (double)ux) / st0, r2 = fabs(mac[2] - (double)uy) / st0;
+            const double ist0 = 1.0 / sqrt((double)th);   // 1/s of the streaming gauge
+            const double r0 = fabs(mac[10] - (double)th) * (ist0 * ist0);
+            const double r1 = fabs(mac[1] - (double)ux) * ist0, r2 = fabs(mac[2] - (double)uy) * ist0;
             const double r = fmax(fmax(r0, r1), r2);
             if (r <= p.tol) { conv = true; break; }
             if (it >= p.max_iter || !(r == r)) break;
@@ -725,8 +733,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_q16_step(DevPar
         const R E = (R)mac[5], Pg = (R)mac[9], ths = (R)mac[10];
         const R fx = (R)Fx, fy = (R)Fy, m0 = (R)M0, dt = q.dt, om = q.omega;
         const double sd = sqrt((double)th), ssd = sqrt(mac[10]);
-        const R is = (R)(1.0 / sd), sst = (R)ssd;
-        const R ds = (R)((mac[10] - (double)th) / (ssd + sd) / sd);   // (s* - s)/s
+        const double isd = 1.0 / sd;
+        const R is = (R)isd, sst = (R)ssd;
+        const R ds = (R)((mac[10] - (double)th) / (ssd + sd) * isd);   // (s* - s)/s
         const R dux = (R)(mac[1] - (double)ux) * is, duy = (R)(mac[2] - (double)uy) * is;
         const R shx = fx * dt / rho * is, shy = fy * dt / rho * is;   // du of the force
         R Dx[4][4], Dy[4][4], Ex[4][4], Ey[4][4];
@@ -762,8 +771,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_q16_step(DevPar
         const R fdef = (R)mdef;
         // W_i s c_i J / theta = W_i c_i J / s (sum_i W_i c_i^2 = T_L = 1); the mass part
         // W_i mdef already carries the momentum mdef u
-        const R jxdef = (R)((mac[0] * mac[1] + Fx * p.dt - sjx - mdef * (double)ux) / sd);
-        const R jydef = (R)((mac[0] * mac[2] + Fy * p.dt - sjy - mdef * (double)uy) / sd);
+        const R jxdef = (R)((mac[0] * mac[1] + Fx * p.dt - sjx - mdef * (double)ux) * isd);
+        const R jydef = (R)((mac[0] * mac[2] + Fy * p.dt - sjy - mdef * (double)uy) * isd);
         R *orec = out + (size_t)n * SLQ;
 #pragma unroll
         for (int i = 0; i < Q16; ++i)
@@ -787,27 +796,31 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 3 : 1) k_q16_step(DevPar
 #pragma unroll
         for (int r = 0; r < 4; ++r) st4(orec + Q_F + 4 * r, fo[4 * r], fo[4 * r + 1], fo[4 * r + 2], fo[4 * r + 3]);
 
-        const R H = E + Pg / rho;
-        const R Ixx = R(2) * uhx * fx + dt * fx * fx * E / (R(2) * Pg);
-        const R Ixy = uhx * fy + fx * uhy + dt * fx * fy * E / (R(2) * Pg);
-        const R Iyy = R(2) * uhy * fy + dt * fy * fy * E / (R(2) * Pg);
-        const R Mx = (dt * rho / Pg) * (fx * H - (Ixx * u_x + Ixy * u_y));
-        const R My = (dt * rho / Pg) * (fy * H - (Ixy * u_x + Iyy * u_y));
-        const R Nxx = rho + (dt * rho / (R(2) * Pg)) * Ixx;
-        const R Nxy = (dt * rho / (R(2) * Pg)) * Ixy;
-        const R Nyy = rho + (dt * rho / (R(2) * Pg)) * Iyy;
+        // the quotients by P and rho as products with two reciprocals
+        const R irh = R(1) / rho, ihP = R(1) / (R(2) * Pg);   // 1/rho, 1/(2P)
+        const R Prh = Pg * irh, k2 = dt * rho * ihP;            // P/rho, dt rho/(2P)
+        const R H = E + Prh;
+        const R Ixx = R(2) * uhx * fx + dt * fx * fx * E * ihP;
+        const R Ixy = uhx * fy + fx * uhy + dt * fx * fy * E * ihP;
+        const R Iyy = R(2) * uhy * fy + dt * fy * fy * E * ihP;
+        const R Mx = (R(2) * k2) * (fx * H - (Ixx * u_x + Ixy * u_y));
+        const R My = (R(2) * k2) * (fy * H - (Ixy * u_x + Iyy * u_y));
+        const R Nxx = rho + k2 * Ixx;
+        const R Nxy = k2 * Ixy;
+        const R Nyy = rho + k2 * Iyy;
         const R phi = R(2) * (uhx * fx + uhy * fy);
+        const R rhP = rho * ihP;                                // rho/(2P)
 #pragma unroll
         for (int i = 0; i < Q16; ++i) {
             const R cx = L.c[i & 3], cy = L.c[i >> 2], W = L.w[i & 3] * L.w[i >> 2];
             const R vx = sst * cx + u_x, vy = sst * cy + u_y;
-            const R Axx = vx * vx - Pg / rho - u_x * u_x;
+            const R Axx = vx * vx - Prh - u_x * u_x;
             const R Axy = vx * vy - u_x * u_y;
-            const R Ayy = vy * vy - Pg / rho - u_y * u_y;
+            const R Ayy = vy * vy - Prh - u_y * u_y;
             const R geq = W * (R(2) * rho * E + Mx * (vx - u_x) + My * (vy - u_y) + Nxx * Axx +
                                R(2) * Nxy * Axy + Nyy * Ayy);
             const R uc = u_x * cx + u_y * cy;
-            const R gc = m0 * W * (R(1) + rho * uc * uc / (R(2) * Pg) - rho * (vx * vx + vy * vy) / (R(2) * Pg) + R(1));
+            const R gc = m0 * W * (R(1) + rhP * (uc * uc) - rhP * (vx * vx + vy * vy) + R(1));
             h[i] = om * geq + dt * (gc + W * phi);
         }
         R ginc[Q16];
