@@ -95,8 +95,8 @@ template <> __device__ __forceinline__ const TypedParams<double> &typed<double>(
 struct DevStats {
     unsigned long long streams, nonconv, clamped, nonfinite, bad_init, stalled, block_streams, max_streams;
     unsigned long long timeouts;   // tiles skipped because a bounded wait for their copies ran out
-    unsigned long long region_nodes;   // D2Q9/D2Q16 step: stencil-region nodes transformed, summed over streams
-    unsigned long long pair_streams;   // D2Q9/D2Q16 step: streams that took the per-pair path (wide regions)
+    unsigned long long region_nodes;   // D2Q9 step: stencil-region nodes transformed, summed over streams
+    unsigned long long pair_streams;   // D2Q9 step: streams that took the per-pair path (wide regions)
 };
 
 // lattice temperature T_L = 1/3 and 1-D weights W_-1, W_0, W_+1 (SM "Equilibrium")

@@ -867,6 +867,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? Q16_MIN_BLOCKS : 1) k_q1
         if (v[1]) atomicAdd(&stats->nonconv, v[1]);
         if (v[2]) atomicAdd(&stats->clamped, v[2]);
         if (v[3]) atomicAdd(&stats->nonfinite, v[3]);
+        // the region-stream counters of the D2Q9 step, filled the same way here
         if (v[4]) atomicAdd(&stats->region_nodes, v[4]);
         if (v[5]) atomicAdd(&stats->pair_streams, v[5]);
         if (mx) atomicMax(&stats->max_streams, mx);
