@@ -29,6 +29,7 @@
 #pragma once
 
 #include "pond_kernels.cuh"
+#include "pond_step.cuh"   // float-float values (ffv) and TwoSum
 
 namespace pond {
 
@@ -377,24 +378,82 @@ __device__ void q16_stream(const DevParams &p, const Lat16<R> &L, const R *__res
     }
 }
 
-// Exact FP64 sums of a node's own stored populations and its kept remainders:
+// The FP32 form's population sums in float-float on the FP32 pipes (GB300 runs FP64 at
+// 1/64 of the FP32 rate, and these sums were most of the step's FP64 work).  C1's outer and
+// inner nodes co = sqrt(3 + sqrt 6), ci = sqrt(3 - sqrt 6) as hi + lo (hi their FP32
+// rounding, lo the FP32 rounding of the rest: together within 2^-48 relative).
+__device__ __forceinline__ ffv q16_co() { return {0x1.2ace16p+1f, -0x1.b3aab0p-26f}; }
+__device__ __forceinline__ ffv q16_ci() { return {0x1.7be2aep-1f, -0x1.4e69e0p-26f}; }
+
+// Moments of 16 FP32 values v (i = 4 jy + jx), returned as doubles: out[0] = sum v and,
+// with WEIGHTED, out[1] = sum v c_jx and out[2] = sum v c_jy, from the column sums C_k and
+// row sums R_r (sum v c_jx = co (C_3 - C_0) + ci (C_2 - C_1), the same over rows for y).
+// Each float-float addition is exact up to ~2^-48 of its result (TwoSum, the error terms
+// added in FP32), far below what the kept remainders resolve (FP32 storage rounding).
+template <bool WEIGHTED>
+__device__ __forceinline__ void q16_ff_moments(const float *v, double *out)
+{
+    ffv C[4], Rw[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        C[k] = {v[k], 0.0f};
+#pragma unroll
+        for (int r = 1; r < 4; ++r) C[k] = ff_add(C[k], v[4 * r + k]);
+    }
+    const ffv s = ff_add(ff_add(C[0], C[1]), ff_add(C[2], C[3]));
+    out[0] = (double)s.hi + (double)s.lo;
+    if (WEIGHTED) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            Rw[r] = {v[4 * r], 0.0f};
+#pragma unroll
+            for (int k = 1; k < 4; ++k) Rw[r] = ff_add(Rw[r], v[4 * r + k]);
+        }
+        const ffv co = q16_co(), ci = q16_ci();
+        const ffv sx = ff_add(ff_mul(ff_add(C[3], ff_neg(C[0])), co), ff_mul(ff_add(C[2], ff_neg(C[1])), ci));
+        const ffv sy = ff_add(ff_mul(ff_add(Rw[3], ff_neg(Rw[0])), co), ff_mul(ff_add(Rw[2], ff_neg(Rw[1])), ci));
+        out[1] = (double)sx.hi + (double)sx.lo;
+        out[2] = (double)sy.hi + (double)sy.lo;
+    }
+}
+
+// Sums of a node's own stored populations and its kept remainders (FP64; float-float in
+// the FP32 form):
 // own[0] = sum f + mass lo, own[1] = sum f c_x, own[2] = sum f c_y, own[3] = sum g +
 // energy lo, own[4], own[5] = the momentum lo (absolute, sum f v units).
 template <typename R>
 __device__ __forceinline__ void q16_own_sums(const Lat16<double> &L, const R *rec, double own[6])
 {
     double s0 = 0.0, sx = 0.0, sy = 0.0, sg = 0.0;
+    if constexpr (sizeof(R) == 4) {
+        float f[Q16], g[Q16];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        R f[4], g[4];
-        ld4(rec + Q_F + 4 * r, f);
-        ld4(rec + Q_G + 4 * r, g);
+        for (int r = 0; r < 4; ++r) {
+            float q[4];
+            ld4(rec + Q_F + 4 * r, q);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            s0 += (double)f[k];
-            sx += (double)f[k] * L.c[k];
-            sy += (double)f[k] * L.c[r];
-            sg += (double)g[k];
+            for (int k = 0; k < 4; ++k) f[4 * r + k] = q[k];
+            ld4(rec + Q_G + 4 * r, q);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) g[4 * r + k] = q[k];
+        }
+        double m[3], mg[1];
+        q16_ff_moments<true>(f, m);
+        q16_ff_moments<false>(g, mg);
+        s0 = m[0]; sx = m[1]; sy = m[2]; sg = mg[0];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            R f[4], g[4];
+            ld4(rec + Q_F + 4 * r, f);
+            ld4(rec + Q_G + 4 * r, g);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                s0 += (double)f[k];
+                sx += (double)f[k] * L.c[k];
+                sy += (double)f[k] * L.c[r];
+                sg += (double)g[k];
+            }
         }
     }
     R lo[4];
@@ -419,13 +478,20 @@ __device__ __forceinline__ void q16_macro(const DevParams &p, const Lat16<double
 {
     const double s = sqrt((double)th);
     double d0 = 0.0, dx = 0.0, dy = 0.0, dg = 0.0;
+    if constexpr (sizeof(R) == 4) {
+        double m[3], mg[1];
+        q16_ff_moments<true>(fi, m);
+        q16_ff_moments<false>(gi, mg);
+        d0 = m[0]; dx = m[1]; dy = m[2]; dg = mg[0];
+    } else {
 #pragma unroll
-    for (int i = 0; i < Q16; ++i) {
-        const double f = (double)fi[i];
-        d0 += f;
-        dx += f * L.c[i & 3];
-        dy += f * L.c[i >> 2];
-        dg += (double)gi[i];
+        for (int i = 0; i < Q16; ++i) {
+            const double f = (double)fi[i];
+            d0 += f;
+            dx += f * L.c[i & 3];
+            dy += f * L.c[i >> 2];
+            dg += (double)gi[i];
+        }
     }
     // sum f v = s sum f c + u sum f, for the stored part and the increments
     const double rho = own[0] + d0;
@@ -757,12 +823,19 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? Q16_MIN_BLOCKS : 1) k_q1
         R fo[Q16];
         double sf = 0.0, sjx = 0.0, sjy = 0.0;
 #pragma unroll
-        for (int i = 0; i < Q16; ++i) {
-            fo[i] = ft[i] + om * ((h[i] - ft[i]) + eqi[i]) + (shi[i] - eqi[i]);
-            const double f = (double)fo[i];
-            sf += f;
-            sjx += f * Ld.c[i & 3];
-            sjy += f * Ld.c[i >> 2];
+        for (int i = 0; i < Q16; ++i) fo[i] = ft[i] + om * ((h[i] - ft[i]) + eqi[i]) + (shi[i] - eqi[i]);
+        if constexpr (sizeof(R) == 4) {
+            double m[3];
+            q16_ff_moments<true>(fo, m);
+            sf = m[0]; sjx = m[1]; sjy = m[2];
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q16; ++i) {
+                const double f = (double)fo[i];
+                sf += f;
+                sjx += f * Ld.c[i & 3];
+                sjy += f * Ld.c[i >> 2];
+            }
         }
         // momentum of the stored values in the streaming gauge: sum f (s c + u)
         sjx = sd * sjx + sf * (double)ux;
@@ -779,15 +852,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? Q16_MIN_BLOCKS : 1) k_q1
             fo[i] += (L.w[i & 3] * L.w[i >> 2]) * (fdef + jxdef * L.c[i & 3] + jydef * L.c[i >> 2]);
         // what the stored values still miss (below their rounding) is kept beside them
         double mlo = 0.0, jxlo = 0.0, jylo = 0.0;
-        if (sizeof(R) == 4) {
-            double s0 = 0.0, cx = 0.0, cy = 0.0;
-#pragma unroll
-            for (int i = 0; i < Q16; ++i) {
-                const double f = (double)fo[i];
-                s0 += f;
-                cx += f * Ld.c[i & 3];
-                cy += f * Ld.c[i >> 2];
-            }
+        if constexpr (sizeof(R) == 4) {
+            double m[3];
+            q16_ff_moments<true>(fo, m);
+            const double s0 = m[0], cx = m[1], cy = m[2];
             mlo = mac[0] - s0;
             // the mass lo carries momentum u mlo in the next step's sums
             jxlo = (mac[0] * mac[1] + Fx * p.dt) - (sd * cx + (double)ux * s0) - mlo * (double)ux;
@@ -830,19 +898,21 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? Q16_MIN_BLOCKS : 1) k_q1
         R go[Q16];
         double sg = 0.0;
 #pragma unroll
-        for (int i = 0; i < Q16; ++i) {
-            go[i] = gt[i] - om * gt[i] + (h[i] + ginc[i]);
-            sg += (double)go[i];
+        for (int i = 0; i < Q16; ++i) go[i] = gt[i] - om * gt[i] + (h[i] + ginc[i]);
+        if constexpr (sizeof(R) == 4) {
+            q16_ff_moments<false>(go, &sg);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q16; ++i) sg += (double)go[i];
         }
         const double g_tot = 2.0 * mac[0] * mac[5] + p.dt * (M0 + 2.0 * (mac[3] * Fx + mac[4] * Fy));
         const R gdef = (R)(g_tot - sg);
 #pragma unroll
         for (int i = 0; i < Q16; ++i) go[i] += gdef * (L.w[i & 3] * L.w[i >> 2]);
         double glo = 0.0;
-        if (sizeof(R) == 4) {
-            double s1 = 0.0;
-#pragma unroll
-            for (int i = 0; i < Q16; ++i) s1 += (double)go[i];
+        if constexpr (sizeof(R) == 4) {
+            double s1;
+            q16_ff_moments<false>(go, &s1);
             glo = g_tot - s1;
         }
 #pragma unroll
