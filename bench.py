@@ -194,13 +194,20 @@ def flops_q16(st: dict, updates: int) -> float:
     return total / max(1, updates)
 
 
-# The D3Q27 step (k_q27_step), per node update: per stencil pair (27 directions x 64
-# stencil nodes per stream): gauge offsets (29), the three per-axis increment rows (60),
-# the x-, y- and z-increments and accumulation for f and g (198), weight (2) => 289; per
-# direction: three departure points and cubic weights (60); per stream: moments and
-# residual (FP64, 260); per node update: non-local terms (600) and the collision (7000:
-# six per-axis increment maps ~360, three three-axis applications ~4800, forced g
-# equilibrium ~1620, defect sums ~300).
+# The D3Q27 step (k_q27_step), per node update.  Region stream, per region node (the
+# union of the 27 departure stencils of 4 x 4 x 4, 5 x 5 x 5 for |v| dt < 1), for each of the
+# two population passes: gauge offsets (11), the three per-axis increment maps (123), the
+# weight products (27), x-, y- and z-increments (3 x 135), the running sums of the
+# increments (135) and the accumulation (81) => 782, 1564 per node; per region stream:
+# departure floors, cubic weights and tables of the three axes (175).  Per-pair fallback
+# stream (regions wider than 6): per stencil pair (27 directions x 64 stencil nodes) gauge
+# offsets (29), the three per-axis increment rows (60), the x-, y- and z-increments and
+# accumulation for f and g (198), weight (2) => 289, per direction three departure points
+# and cubic weights (60).  Per stream: moments and residual (FP64, 260); per node update:
+# non-local terms (600) and the collision (7000: six per-axis increment maps ~360, three
+# three-axis applications ~4800, forced g equilibrium ~1620, defect sums ~300).
+FLOPS_Q27_REGION_NODE = 1564
+FLOPS_Q27_REGION_STREAM = 175
 FLOPS_Q27_PAIR = 289
 FLOPS_Q27_DIR = 60
 FLOPS_Q27_STREAM_EXTRA = 260
@@ -208,8 +215,13 @@ FLOPS_Q27_NONLOCAL = 600
 FLOPS_Q27_COLLIDE = 7000
 
 
-def flops_q27(its: float) -> float:
-    return its * (27 * (FLOPS_Q27_DIR + 64 * FLOPS_Q27_PAIR) + FLOPS_Q27_STREAM_EXTRA) + FLOPS_Q27_NONLOCAL + FLOPS_Q27_COLLIDE
+def flops_q27(st: dict, updates: int) -> float:
+    """FLOPs per node update of the D3Q27 step from its counters (pond_stats)."""
+    pair = st.get("pair_streams", 0)
+    total = (st["region_nodes"] * FLOPS_Q27_REGION_NODE + (st["streams"] - pair) * FLOPS_Q27_REGION_STREAM
+             + st["streams"] * FLOPS_Q27_STREAM_EXTRA + pair * 27 * (FLOPS_Q27_DIR + 64 * FLOPS_Q27_PAIR)
+             + updates * (FLOPS_Q27_NONLOCAL + FLOPS_Q27_COLLIDE))
+    return total / max(1, updates)
 
 
 def d3q27_run(pond, torch, stream, precision, steps, warmup, nx=96, ny=96, nz=64, sm_mhz=2070.0) -> dict:
@@ -238,13 +250,14 @@ def d3q27_run(pond, torch, stream, precision, steps, warmup, nx=96, ny=96, nz=64
     sim.moments()
     e2e = w.nodes * steps / (time.perf_counter() - t0) / 1e6
     sim.close()
-    achieved = w.nodes * flops_q27(its) / (ms * 1e-3) / 1e12
+    fl = flops_q27(st, st["node_updates"])
+    achieved = w.nodes * fl / (ms * 1e-3) / 1e12
     peak = alu_peak_tflops(precision, sm_mhz)
     return {"workload": w.name, "mlups": w.nodes / ms / 1e3, "ms_per_step": ms, "streams_per_node": its,
             "e2e_mlups": e2e,
             "roofline": {"bound": "alu", "kernel": "k_q27_step (+ two non-local kernels, timed together)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "flops_per_update": flops_q27(its)}}
+                         "flops_per_update": fl}}
 
 
 # DRAM bytes per launch of k_pond_step (dram__bytes_read.sum + dram__bytes_write.sum) from

@@ -411,11 +411,213 @@ __device__ __forceinline__ void apply3_inc(const A Dx[3][3], const A Dy[3][3], c
 }
 
 // ---------------------------------------------------------------------------
-// The node step (frame search, then collision), one thread per node.
-// FP32: registers capped for four resident blocks per SM (the stencil gathers are
-// latency-bound; 16 warps hide more of it than 8: +21 % measured); FP64 keeps two.
+// Region stream.  On the tensor lattice the union of a node's 27 departure stencils
+// (4 x 4 x 4 each) is the product of the per-axis unions: W x H x D nodes, each side 4 +
+// the spread of its axis's three departure floors (5 x 5 x 5 while |v| dt < 1).  Each
+// region node is carried into the arrival gauge once for all 27 directions and every
+// direction adds its Lagrange-weighted share, with the per-(direction, node) arithmetic of
+// q27_stream: the region form transforms about 125 nodes per stream against 1,728 pairs.
+
+// Largest region side the region stream takes; wider regions take q27_stream.
+constexpr int Q27_REGION_MAX = 6;
+constexpr int Q27_THREADS = 128;   // threads of a k_q27_step block
+
+// Per-thread Lagrange weight tables in shared memory, one column of entries per thread
+// (entry e of thread t at w[e][t]).  Entries 0..17: x, (k * Q27_REGION_MAX + c) = weight
+// of region column c in the stencil of x component k (c_x = k - 1), zero outside it;
+// entries 18..41: y then z, (18 + (axis - 1) * 12 + k * 4 + j) = cubic weight j of
+// component k, placed by the component's offset in the region (kept in registers).
+constexpr int Q27_WT_ENTRIES = 3 * Q27_REGION_MAX + 2 * 12;
 template <typename R>
-__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_q27_step(DevParams p, Grid3 g3, const R *__restrict__ in,
+struct Q27Weights {
+    R w[Q27_WT_ENTRIES][Q27_THREADS];
+};
+
+// Departure floors and cubic weights of the three components of one axis (as in
+// `depart`) for the gauge velocity u; the region's first coordinate lo = X + min floor - 1,
+// its side, and each component's offset in it.  False, with nothing written, when the side
+// exceeds Q27_REGION_MAX or a floor is not finite or not within 2^20 (checked as reals
+// before any conversion to int).  PADDED: zero-padded table entries (x), else the four
+// weights per component.
+template <typename R, bool PADDED>
+__device__ __forceinline__ bool q27_region_axis(int X, R s, R u, R dt, R *wt, int &lo, int &side, int (&off)[3])
+{
+    R fl[3], a[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const R d = -(s * R(k - 1) + u) * dt;
+        fl[k] = floor(d);
+        cubic_w<R>(d - fl[k] + R(1), a[k]);
+    }
+    const R flo = fmin(fmin(fl[0], fl[1]), fl[2]);
+    const R fhi = fmax(fmax(fl[0], fl[1]), fl[2]);
+    if (!(fhi - flo <= R(Q27_REGION_MAX - 4)) || !(fabs(flo) <= R(1 << 20)) || !(fabs(fhi) <= R(1 << 20)))
+        return false;
+    lo = X + (int)flo - 1;
+    side = (int)(fhi - flo) + 4;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        off[k] = (int)(fl[k] - flo);   // 0 .. side - 4
+        if (PADDED) {
+#pragma unroll
+            for (int c = 0; c < Q27_REGION_MAX; ++c) {
+                const int j = c - off[k];
+                wt[(k * Q27_REGION_MAX + c) * Q27_THREADS] =
+                    j == 0 ? a[k][0] : (j == 1 ? a[k][1] : (j == 2 ? a[k][2] : (j == 3 ? a[k][3] : R(0))));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) wt[(k * 4 + j) * Q27_THREADS] = a[k][j];
+        }
+    }
+    return true;
+}
+
+// weight of region row (plane) c for component k of an unpadded axis table
+template <typename R>
+__device__ __forceinline__ R q27_wt_at(const R *wt, int k, int o, int c)
+{
+    const int j = c - o;
+    return (j >= 0 && j < 4) ? wt[(k * 4 + j) * Q27_THREADS] : R(0);
+}
+
+// One population set (27 values at record offset OFF) of a region node carried by the
+// per-axis increment maps: t1 = x-increments, t2 = y-increments of h + t1, z = the
+// z-increments of h + t1 + t2, and acc_i += w_i (((h_i - ref_i) + t1_i) + t2_i + z_i) with
+// the weight w_i = wx[ix] (wy[iy] wz[iz]) (wyz[3 iz + iy] = wy[iy] wz[iz]).
+template <typename R, int OFF>
+__device__ __forceinline__ void q27_region_pop(const R (&Dx)[3][3], const R (&Dy)[3][3], const R (&Dz)[3][3],
+                                               const R *rec, const R (&ref)[Q27], const R (&wx)[3],
+                                               const R (&wyz)[9], R (&acc)[Q27])
+{
+    constexpr int B = OFF & ~3, SH = OFF - B, NL = (SH + Q27 + 3) / 4;   // 16-byte loads covering the set
+    R h[Q27];
+#pragma unroll
+    for (int c = 0; c < NL; ++c) {
+        R q[4];
+        ld4r(rec + B + 4 * c, q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int i = 4 * c + e - SH;
+            if (i >= 0 && i < Q27) h[i] = q[e];
+        }
+    }
+    R a[Q27], u[Q27];
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        const int ix = i % 3, r = i - ix;
+        const R t1 = Dx[ix][0] * h[r] + Dx[ix][1] * h[r + 1] + Dx[ix][2] * h[r + 2];
+        a[i] = (h[i] - ref[i]) + t1;
+        u[i] = h[i] + t1;
+    }
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        const int iy = (i / 3) % 3, r = i - 3 * iy;
+        // y-increments from h + t1 (held in u before the update below reads it)
+        const R t2 = Dy[iy][0] * u[r] + Dy[iy][1] * u[r + 3] + Dy[iy][2] * u[r + 6];
+        h[i] = t2;
+    }
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        a[i] += h[i];
+        u[i] += h[i];
+    }
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) {
+        const int iz = i / 9, r = i - 9 * iz;
+        const R z = Dz[iz][0] * u[r] + Dz[iz][1] * u[r + 9] + Dz[iz][2] * u[r + 18];
+        acc[i] += (wx[i % 3] * wyz[i / 3]) * (a[i] + z);
+    }
+}
+
+// The region pass for one population set (record offset OFF: R_F or R_G) over the region
+// at (xlo, ylo, zlo) of sides W, H, D, skipping region entry `skip` (-1: none): writes the
+// increments of the streamed populations over the node's own (irec) into out.
+template <typename R, int OFF>
+__device__ __noinline__ void q27_region_pass(const DevParams &p, const Grid3 &g3, const R *__restrict__ in,
+                                             const R *irec, int xlo, int ylo, int zlo, int W, int H, int D,
+                                             const int (&oy)[3], const int (&oz)[3], int skip, R th,
+                                             const R (&u)[3], const R *wt, R *out)
+{
+    const R s = sqrt_(th), is = R(1) / s;
+    R ref[Q27], acc[Q27];
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) { ref[i] = irec[OFF + i]; acc[i] = R(0); }
+    const R *wty = wt + 3 * Q27_REGION_MAX * Q27_THREADS, *wtz = wty + 12 * Q27_THREADS;
+    int e = 0;   // region entry index (z-major, then y, then x)
+#pragma unroll 1
+    for (int cz = 0; cz < D; ++cz) {
+        const int zz = bc_wrap(zlo + cz, g3.nz, g3.bcz);
+        R wz[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) wz[k] = q27_wt_at(wtz, k, oz[k], cz);
+#pragma unroll 1
+        for (int cy = 0; cy < H; ++cy) {
+            const long long row = ((long long)zz * p.ny + bc_wrap(ylo + cy, p.ny, p.bcy)) * p.nx;
+            R wyz[9];   // wy[m] wz[l] at 3 l + m (population i = 9 l + 3 m + k)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const R wy = q27_wt_at(wty, m, oy[m], cy);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) wyz[3 * l + m] = wy * wz[l];
+            }
+#pragma unroll 1
+            for (int cx = 0; cx < W; ++cx, ++e) {
+                if (e == skip) continue;
+                const R *rec = in + (size_t)(row + bc_wrap(xlo + cx, p.nx, p.bcx)) * SL27;
+                R gv[4];
+                ld4r(rec + R_TH, gv);   // theta, u_x, u_y, u_z of the region node
+                const R ds = (gv[0] - th) / (sqrt_(gv[0]) + s) * is;   // (s' - s)/s
+                R Dx[3][3], Dy[3][3], Dz[3][3];
+                axis3<R>(ds, (gv[1] - u[0]) * is, Dx);
+                axis3<R>(ds, (gv[2] - u[1]) * is, Dy);
+                axis3<R>(ds, (gv[3] - u[2]) * is, Dz);
+                R wx[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) wx[k] = wt[(k * Q27_REGION_MAX + cx) * Q27_THREADS];
+                q27_region_pop<R, OFF>(Dx, Dy, Dz, rec, ref, wx, wyz, acc);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q27; ++i) out[i] = acc[i];
+}
+
+// Streaming of node (X, Y, Z) into gauge (th, u) by the region stream where the region
+// fits, else by q27_stream; skip_own leaves out the node's own region entry (valid when
+// the gauge is the node's stored gauge: the map is then the identity and the entry adds
+// exactly zero).  Adds the region entries transformed to nreg, or 1 to npair.
+template <typename R>
+__device__ __forceinline__ void q27_stream_any(const DevParams &p, const Grid3 &g3, const R *__restrict__ in,
+                                               int X, int Y, int Z, R th, const R (&u)[3], bool skip_own, R *wt,
+                                               R *fi, R *gi, unsigned long long &nreg, unsigned long long &npair)
+{
+    const R s = sqrt_(th), dt = (R)p.dt;
+    int xlo, ylo, zlo, W, H, D, ox[3], oy[3], oz[3];
+    R *wty = wt + 3 * Q27_REGION_MAX * Q27_THREADS, *wtz = wty + 12 * Q27_THREADS;
+    if (q27_region_axis<R, true>(X, s, u[0], dt, wt, xlo, W, ox) &&
+        q27_region_axis<R, false>(Y, s, u[1], dt, wty, ylo, H, oy) &&
+        q27_region_axis<R, false>(Z, s, u[2], dt, wtz, zlo, D, oz)) {
+        const int cxo = X - xlo, cyo = Y - ylo, czo = Z - zlo;
+        const int skip = (skip_own && cxo >= 0 && cxo < W && cyo >= 0 && cyo < H && czo >= 0 && czo < D)
+                             ? (czo * H + cyo) * W + cxo : -1;
+        const R *irec = in + (size_t)(((long long)Z * p.ny + Y) * p.nx + X) * SL27;
+        q27_region_pass<R, R_F>(p, g3, in, irec, xlo, ylo, zlo, W, H, D, oy, oz, skip, th, u, wt, fi);
+        q27_region_pass<R, R_G>(p, g3, in, irec, xlo, ylo, zlo, W, H, D, oy, oz, skip, th, u, wt, gi);
+        nreg += (unsigned long long)(W * H * D - (skip >= 0 ? 1 : 0));
+    } else {
+        q27_stream<R>(p, g3, in, X, Y, Z, th, u, fi, gi);
+        npair += 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The node step (frame search, then collision), one thread per node.
+// FP32: registers capped for three resident blocks per SM (168; the region passes then
+// spill 20 bytes; two blocks without spills measured 1.3 % slower); FP64 keeps two.
+constexpr int Q27_MIN_BLOCKS = 3;
+template <typename R>
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? Q27_MIN_BLOCKS : 2) k_q27_step(DevParams p, Grid3 g3, const R *__restrict__ in,
                                                   const double *__restrict__ nl, R *__restrict__ out,
                                                   DevStats *stats)
 {
@@ -423,7 +625,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_q27_step(DevPar
     const int Z = blockIdx.z;
     const bool valid = X < p.nx && Y < p.ny;
     const long long N = p.N, n = valid ? ((long long)Z * p.ny + Y) * p.nx + X : 0;
-    unsigned long long its = 0, nonconv = 0, clamped = 0, nonfinite = 0;
+    unsigned long long its = 0, nonconv = 0, clamped = 0, nonfinite = 0, nreg = 0, npair = 0;
+    __shared__ Q27Weights<R> qw;
+    R *wt = &qw.w[0][threadIdx.y * blockDim.x + threadIdx.x];
     if (valid) {
         const double F[3] = {NL3(nl, N3_F, n, N), NL3(nl, N3_F + 1, n, N), NL3(nl, N3_F + 2, n, N)};
         const double rEl = NL3(nl, N3_REL, n, N), M0 = NL3(nl, N3_M0, n, N);
@@ -438,7 +642,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_q27_step(DevPar
         bool conv = false;
         for (;;) {
             ++it;
-            q27_stream<R>(p, g3, in, X, Y, Z, th, u, ft, gt);
+            // the first stream uses the node's stored gauge: its own region entry adds zero
+            q27_stream_any<R>(p, g3, in, X, Y, Z, th, u, it == 1, wt, ft, gt, nreg, npair);
             q27_macro<R>(p, th, u, own, ft, gt, F, rEl, mac);
             const double t0 = (double)th, st0 = sqrt(t0);
             double r = fabs(mac[12] - t0) / t0;
@@ -566,10 +771,10 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_q27_step(DevPar
         const double chk = mac[0] + mac[9] + (double)ginc[0] + (double)eqi[0];
         nonfinite = (chk - chk == 0.0) ? 0ull : 1ull;
     }
-    unsigned long long v[4] = {its, nonconv, clamped, nonfinite}, mx = its;
+    unsigned long long v[6] = {its, nonconv, clamped, nonfinite, nreg, npair}, mx = its;
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int k = 0; k < 6; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
         const unsigned long long m2 = __shfl_xor_sync(0xffffffffu, mx, o);
         mx = m2 > mx ? m2 : mx;
     }
@@ -578,6 +783,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 2) k_q27_step(DevPar
         if (v[1]) atomicAdd(&stats->nonconv, v[1]);
         if (v[2]) atomicAdd(&stats->clamped, v[2]);
         if (v[3]) atomicAdd(&stats->nonfinite, v[3]);
+        // the region-stream counters of the D2Q9 step, filled the same way here
+        if (v[4]) atomicAdd(&stats->region_nodes, v[4]);
+        if (v[5]) atomicAdd(&stats->pair_streams, v[5]);
         if (mx) atomicMax(&stats->max_streams, mx);
     }
 }

@@ -64,6 +64,15 @@ def cases():
     yield "strip40x2x3_zerograd_z", inputs.droplet3d(n=40, ny=2, nz=3, radius=3.0, bc_z=1, steps=4)
     yield "moving12x10x8", moving(inputs.droplet3d(n=12, ny=10, nz=8, radius=3.0, steps=5))
     yield "single_node", inputs.droplet3d(n=1, radius=0.5, steps=3)
+    yield "hot_bump10x8x6_wide_regions", wide_region_bump()
+
+
+def wide_region_bump():
+    """A 10 x 8 x 6 droplet's density field at three times its temperature (2.55 T_cr) with
+    dt = 1: sqrt(theta / T_L) dt up to 1.11, so that about half of the nodes have departure
+    floors spread over three nodes (regions wider than 6) and take the per-pair stream."""
+    w = inputs.droplet3d(n=10, ny=8, nz=6, radius=3.0, steps=4)
+    return dataclasses.replace(w, name="hot_bump10x8x6_dt1", dt=1.0, T=w.T * 3.0)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -83,6 +92,23 @@ def test_small_grids_match_oracle(pond, case, precision):
     assert st["nonfinite"] == 0
     if precision == "fp64":
         assert abs(st["streams"] - stats["streams"]) <= 0.01 * stats["streams"] + 2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_region_and_pair_streams_are_both_taken(pond, precision):
+    """Every stream of a usual workload (|v| dt < 1) takes the region stream over at most
+    6 x 6 x 6 nodes; the hot bump sends streams down both paths."""
+    for w, both in ((inputs.droplet3d(n=16, radius=4.0, steps=3), False), (wide_region_bump(), True)):
+        with sim_of(pond, w, precision) as sim:
+            sim.init_fields(w.rho, w.ux, w.uy, w.T, uz=w.uz)
+            sim.step(w.steps)
+            st = sim.stats()
+        if both:
+            assert 0 < st["pair_streams"] < st["streams"], st
+            assert st["region_nodes"] > 0
+        else:
+            assert st["pair_streams"] == 0
+            assert 63 * st["streams"] <= st["region_nodes"] <= 216 * st["streams"], st
 
 
 def test_full_state_and_conservation_sums_match_oracle(pond):

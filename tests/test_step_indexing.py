@@ -1,4 +1,4 @@
-"""Index safety of the step kernels' region streams (D2Q9 and D2Q16), checked on the CPU.
+"""Index safety of the step kernels' region streams (D2Q9, D2Q16, D3Q27), checked on the CPU.
 
 The kernel computes, per node and axis, the departure offsets d_j = -(s c_j + u) dt of the
 three directions (clamped to +-2^20 nodes, NaN to the lower bound), their floors, the
@@ -144,3 +144,60 @@ def test_d2q16_region_indices_stay_in_the_tables():
         u = float(rng.normal(0.0, 1.0))
         taken += check_axis_q16(s, u, float(rng.uniform(0.01, 1.0)))
     assert taken > 1000
+
+
+# D3Q27 step (region stream of k_q27_step): per axis the three departure offsets
+# d_k = -(s (k - 1) + u) dt, the same real-valued checks as D2Q16 with Q27_REGION_MAX = 6;
+# the x table is zero-padded (3 x 6 entries), the y and z tables hold the four cubic
+# weights per component (3 x 4 entries each) and are read only at j = c - offset in [0, 4).
+Q27_REGION_MAX = 6
+Q27_ENTRIES = 3 * Q27_REGION_MAX + 2 * 12
+
+
+def check_axis_q27(s, u, dt, X=5):
+    with np.errstate(all="ignore"):
+        fl = [np.floor(-(np.float32(s) * np.float32(k - 1) + np.float32(u)) * np.float32(dt)) for k in range(3)]
+        flo = cuda_fmin(cuda_fmin(fl[0], fl[1]), fl[2])
+        fhi = cuda_fmax(cuda_fmax(fl[0], fl[1]), fl[2])
+        taken = bool(fhi - flo <= np.float32(Q27_REGION_MAX - 4)) and bool(abs(flo) <= 2.0 ** 20) \
+            and bool(abs(fhi) <= 2.0 ** 20)
+    if not taken:
+        return False
+    lo = X + to_int(flo) - 1
+    side = to_int(fhi - flo) + 4
+    assert 4 <= side <= Q27_REGION_MAX
+    assert I32.min < lo - 1 and lo + side < I32.max
+    with np.errstate(all="ignore"):
+        offs = [to_int(f - flo) for f in fl]
+    for o in offs:
+        assert 0 <= o <= side - 4
+    for k in range(3):
+        for c in range(Q27_REGION_MAX):            # padded x entries
+            assert 0 <= k * Q27_REGION_MAX + c < 3 * Q27_REGION_MAX
+        for c in range(side):                      # unpadded y / z entries, read only in range
+            j = c - offs[k]
+            if 0 <= j < 4:
+                for axis in (1, 2):
+                    e = 3 * Q27_REGION_MAX + (axis - 1) * 12 + k * 4 + j
+                    assert 3 * Q27_REGION_MAX <= e < Q27_ENTRIES
+    return True
+
+
+def test_d3q27_region_indices_stay_in_the_tables():
+    rng = np.random.default_rng(13)
+    specials = [0.0, 1e-30, 1e-7, 0.05, 0.5, 1.0, 3.0, 1e3, 1e10, 1e38, np.inf, -np.inf, np.nan]
+    taken = 0
+    for s in [abs(x) if not np.isnan(x) else x for x in specials]:
+        for u in specials + [-x for x in specials[1:-1]]:
+            for dt in (0.228, 0.5, 1.0):
+                taken += check_axis_q27(s, u, dt)
+    for _ in range(3000):
+        s = float(np.exp(rng.uniform(-10, 1)))
+        u = float(rng.normal(0.0, 1.0))
+        taken += check_axis_q27(s, u, float(rng.uniform(0.01, 1.0)))
+    assert taken > 1000
+    # the own-entry index of a region of sides W, H, D stays below W H D
+    for W in range(4, Q27_REGION_MAX + 1):
+        for H in range(4, Q27_REGION_MAX + 1):
+            for D in range(4, Q27_REGION_MAX + 1):
+                assert ((D - 1) * H + (H - 1)) * W + (W - 1) < W * H * D
