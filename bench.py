@@ -598,6 +598,13 @@ def parity_vs_oracle(w, pond, stream, precision, shape, res, steps) -> dict:
         if k in ("ux", "uy"):
             scale = max(scale, cs)
         out[k] = float(np.abs(got[k] - ref[k]).max() / scale)
+    # the velocity figures above are normalised by max(|uhat|, sqrt(max p/rho)); beside them
+    # the plain relative L-infinity |got - ref|max / |ref|max and the ratio of the largest
+    # speed to that scale (the two agree where the ratio is >= 1)
+    for k in ("ux", "uy"):
+        umax = float(np.abs(ref[k]).max())
+        out[k + "_plain"] = float(np.abs(got[k] - ref[k]).max() / umax) if umax > 0 else None
+        out[k + "_max_over_cs"] = umax / cs
     out["steps"] = steps
     return out
 
