@@ -168,11 +168,11 @@ typedef struct {
                               staging copies ran out (reported as POND_ETIMEOUT) */
     int64_t region_nodes;  /* stencil-region nodes carried into the arrival gauge,
                               summed over streams (the union of a node's 4x4
-                              departure stencils: 16..64 per stream on D2Q9,
-                              16..36 on D2Q16, less the node's own entry in a
-                              first stream)                                    */
+                              (4x4x4) departure stencils: 16..64 per stream on
+                              D2Q9, 16..36 on D2Q16, 64..216 on D3Q27, less the
+                              node's own entry in a first stream)              */
     int64_t pair_streams;  /* streams of regions wider than 8 nodes (D2Q9) or 6
-                              nodes (D2Q16), which take the per-direction,
+                              nodes (D2Q16, D3Q27), which take the per-direction,
                               per-stencil-node path                            */
 } pond_stats_t;
 
