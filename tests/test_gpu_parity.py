@@ -54,6 +54,14 @@ def small_cases():
     yield "droplet_isothermal_40x36", dataclasses.replace(
         inputs.droplet(n=40, ny=36, Tr=0.9, radius=8.0, amp=0.0, steps=30), isothermal=True)
     yield "double_well_pulse_80x1", inputs.simplified_eos("pulse", "vapour", nx=80, pulse_width=4.0, steps=40)
+    # near the critical point, where the EoS (float-float in the mixed form) is flattest:
+    # a droplet and a slab at 0.95 T_cr (3.7 streams per node), a 1e-2 pulse at the
+    # critical state, and a supercritical tube at 1.02 T_cr
+    yield "droplet32x28_Tr0.95", inputs.droplet(n=32, ny=28, Tr=0.95, radius=7.0, steps=30)
+    yield "slab48x3_Tr0.95", inputs.slab(nx=48, ny=3, Tr=0.95, steps=40)
+    yield "sound_critical_amp1e-2_64x2", inputs.sound_pulse(phase="critical", nx=64, ny=2, amp=1e-2, width=4.0,
+                                                            steps=40)
+    yield "tube60x3_Tr1.02", inputs.shock_tube(nx=60, ny=3, Tr=1.02, width=2.0, steps=30)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
