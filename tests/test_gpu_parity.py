@@ -79,6 +79,29 @@ def test_small_grids_match_oracle(pond, case, precision):
         assert abs(gstats["streams"] - ostats["streams"]) <= 0.01 * ostats["streams"] + 2
 
 
+FLOWING = ("shock36x10_zerograd", "strong_shock_Tr0.7_Ma3", "tube60x3_zerograd", "tube60x3_Tr1.02")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", FLOWING)
+def test_plain_relative_velocity_error_where_the_fluid_flows(pond, case, precision):
+    """Where the flow speed is a sizeable part of the sound speed, the velocities also meet
+    the bar as plain relative L-infinity errors, |got - ref|max / |ref|max (the other tests
+    normalise by max(|uhat|, sqrt(max p/rho)))."""
+    w = dict(small_cases())[case]
+    P, st, _ = oracle_run(w)
+    ref = oracle.moments(P, st)
+    got, _ = gpu_run(pond, w, precision)
+    cs = float(np.sqrt(np.max(np.abs(ref["p"] / ref["rho"]))))
+    for k in ("ux", "uy"):
+        umax = float(np.abs(ref[k]).max())
+        if umax < 0.1 * cs:
+            continue
+        err = float(np.abs(np.asarray(got[k]) - ref[k]).max() / umax)
+        print("%s %s %s: |u|max/cs %.3f, plain rel. err %.3e" % (case, precision, k, umax / cs, err))
+        assert err <= TOL[precision], (k, umax / cs, err)
+
+
 def test_ideal_gas_limit_matches_oracle(pond):
     nx = 64
     x = np.arange(nx) + 0.5
